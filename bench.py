@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark: converged frequency solves per second of the EWM elastodynamic BEM sweep.
+
+Workload (default ``cavity5120``): spherical cavity of radius 1 in an infinite
+solid (E = 1, nu = 0.25, rho = 1), geodesic sphere with 5,120 flat triangles
+(15,360 unknowns), uniform Heaviside pressure, T = 8, 256 samples (129
+complex frequencies s_k = 5/T + i k 2 pi / T), Hanning window, hierarchical
+operator (leaf 64 elements, ACA tolerance 1e-5), complex64 mixed precision
+with FP64 singular integrals and FP64 true-residual refinement, GMRES to a
+true relative residual of 1e-5, solution extrapolation with K = 4.
+
+One step = the whole hot path on that input: geometry and cluster tree,
+static singular parts, for every frequency the right-hand side, operator
+assembly (near blocks + ACA), initial guess and GMRES, then the windowed
+inverse DFT of the full field (every unknown, 256 time samples).
+
+``value``: solves/s with the inputs already in device memory (CUDA events on
+the library's stream). ``e2e``: the same through the host-pointer API (mesh,
+load and pattern copied in, the full time response copied out, every step).
+``plain``: the same sweep in the plain form (complex128 operator, FP64
+everywhere), timed once. ``--impl reference`` times the CPU oracle instead
+(a bounded sample of the same workload, scaled to solves/s).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # the 5,120-triangle cavity sweep: the metric's configuration
+    "cavity5120": dict(n=16, T=8.0, n_omega=256, eta=5.0 / 8.0, aca_tol=1e-5, leaf=64, tol=1e-5),
+    # small case (320 triangles, 32 samples) for quick runs
+    "cavity320": dict(n=4, T=8.0, n_omega=32, eta=5.0 / 8.0, aca_tol=1e-5, leaf=64, tol=1e-5),
+}
+MAT = dict(E=1.0, nu=0.25, rho=1.0)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(cfg, rows_per_step=48, lu_n=1536):
+    """Times the CPU oracle on a bounded sample of one frequency of the workload.
+
+    Sample: the oracle's dense collocation rows (Eq. Aa_b) for ``rows_per_step``
+    collocation elements at s_1 (static parts already cached), plus a dense
+    complex LU solve of size ``lu_n``. Scaled to one frequency solve:
+    t = t_rows * Ne / rows + t_lu * (N / lu_n)^3; solves/s = 1 / t.
+    """
+    from oracle import bem, kernels
+    from paper_1212_3032_gb300 import inputs
+
+    mesh = inputs.cavity_problem(cfg["n"])
+    mat = kernels.Material(**MAT)
+    g = bem.geometry(mesh.xyz, mesh.tri)
+    ne, N = mesh.ne, 3 * mesh.ne
+    rows = np.linspace(0, ne - 1, rows_per_step).astype(np.int64)
+    s1 = cfg["eta"] + 1j * 2 * math.pi / cfg["T"]
+    known = mesh.pattern.astype(complex)
+    bem.system_rows(g, mesh.bc_type, known, cfg["eta"], mat, rows=rows)  # fills the static cache
+    t0 = time.perf_counter()
+    bem.system_rows(g, mesh.bc_type, known, s1, mat, rows=rows)
+    t_rows = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    A = rng.normal(size=(lu_n, lu_n)) + 1j * rng.normal(size=(lu_n, lu_n)) + lu_n * np.eye(lu_n)
+    b = rng.normal(size=lu_n) + 0j
+    t0 = time.perf_counter()
+    np.linalg.solve(A, b)
+    t_lu = time.perf_counter() - t0
+    t_freq = t_rows * ne / rows_per_step + t_lu * (N / lu_n) ** 3
+    return {"value": 1.0 / t_freq, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one frequency of the {ne}-triangle sweep: oracle rows of {rows_per_step} collocation "
+                       f"elements ({3 * rows_per_step} of {N} rows, numpy single-threaded) scaled by {ne}/"
+                       f"{rows_per_step}, plus a {lu_n}-unknown complex LU (LAPACK, all cores) scaled by "
+                       f"(N/{lu_n})^3"),
+            "sample_seconds": t_rows + t_lu}
+
+
+def run_reference(args, cfg):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_oracle_sample(cfg, rows_per_step=24, lu_n=1024)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append((cb, dt))
+    vals = [c["value"] for c, _ in times]
+    v = statistics.median(vals)
+    cb = dict(times[-1][0])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": "converged frequency solves/s", "value": v, "unit": "solves/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic", "config": {"workload": args.workload, **cfg},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args, cfg):
+    import torch
+
+    from paper_1212_3032_gb300 import binding, build, inputs
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    stream = torch.cuda.current_stream(dev)
+    ctx = binding.Context(local, stream=stream.cuda_stream)
+    ctx.set_material(**MAT)
+    ctx.set_window(cfg["eta"], binding.WIN_HANNING)
+    mesh = inputs.cavity_problem(cfg["n"])
+    N = 3 * mesh.ne
+    n_omega = cfg["n_omega"]
+    nf = n_omega // 2 + 1
+    load = inputs.heaviside_history(n_omega)
+    opts = binding.default_opts(leaf_size=cfg["leaf"], aca_tol=cfg["aca_tol"], tol=cfg["tol"],
+                                precision=binding.PREC_C64_MIXED, guess=binding.GUESS_SEM, sem_k=4)
+    # device-resident inputs
+    xyz_t = torch.tensor(mesh.xyz, dtype=torch.float64, device=dev)
+    tri_t = torch.tensor(mesh.tri, dtype=torch.int32, device=dev)
+    bc_t = torch.tensor(mesh.bc_type, dtype=torch.int8, device=dev)
+    load_t = torch.tensor(load, dtype=torch.float64, device=dev)
+    pat_t = torch.tensor(mesh.pattern, dtype=torch.float64, device=dev)
+    dofs_t = torch.arange(N, dtype=torch.int64, device=dev)
+    out_t = torch.empty((n_omega, N), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    def step(o=opts):
+        ctx.mesh_dev(xyz_t, tri_t, bc_t, o)
+        st = ctx.solve_sweep_dev(cfg["T"], n_omega, load_t, pat_t, o, allow_unconverged=True)
+        ctx.time_response_dev(dofs_t, out_t)
+        return st
+
+    for _ in range(args.warmup):
+        stats = step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ctx.set_profiling(True)
+    total_ms = 0.0
+    unconverged = 0
+    iters = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats = step()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            unconverged += sum(1 for s in stats if not s["converged"])
+            iters += sum(s["iters"] for s in stats)
+        torch.cuda.synchronize()
+    prof = ctx.get_profile()
+    ctx.set_profiling(False)
+    clocks = clk.summary()
+    t_max = total_ms
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        dist.barrier()
+    value = nf * args.steps * ws / (t_max / 1e3)
+
+    # end to end through the host-pointer API
+    h2d = mesh.xyz.nbytes + mesh.tri.astype(np.int32).nbytes + mesh.bc_type.nbytes + load.nbytes + \
+        mesh.pattern.nbytes
+    d2h = n_omega * N * 8
+    dofs = np.arange(N, dtype=np.int64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.mesh(mesh.xyz, mesh.tri, mesh.bc_type, opts)
+        ctx.solve_sweep(cfg["T"], n_omega, load, mesh.pattern, opts, allow_unconverged=True)
+        tr = ctx.time_response(dofs)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = nf * args.steps / e2e_s
+
+    # the plain form (complex128 operator and FP64 everywhere), one timed sweep
+    plain = None
+    if not args.no_plain:
+        popts = binding.default_opts(leaf_size=cfg["leaf"], aca_tol=cfg["aca_tol"], tol=cfg["tol"],
+                                     precision=binding.PREC_C128, guess=binding.GUESS_SEM, sem_k=4)
+        step(popts)
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pst = step(popts)
+        e1.record(stream)
+        e1.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"value": nf / (pms / 1e3), "unit": "solves/s", "ms_per_step": pms,
+                 "iters": sum(s["iters"] for s in pst), "speedup": value / ws / (nf / (pms / 1e3))}
+
+    if rank != 0:
+        return
+    peak, peak_kind = _peaks()
+    hmv_gbs = prof["hmv_bytes"] / (prof["hmv_ms"] / 1e3) / 1e9 if prof["hmv_ms"] > 0 else None
+    out = {
+        "metric": "converged frequency solves/s (GMRES true residual <= 1e-5)",
+        "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 (FP32 kernel evaluation; FP64 singular, Arnoldi, refinement)", "data": "synthetic",
+        "config": {"workload": args.workload, "triangles": mesh.ne, "unknowns": N, "n_omega": n_omega,
+                   "solves_per_step": nf, "T": cfg["T"], "eta": cfg["eta"], "window": "hanning",
+                   "aca_tol": cfg["aca_tol"], "leaf": cfg["leaf"], "gmres_tol": cfg["tol"], "guess": "SEM K=4",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "gmres_iters_per_step": iters / args.steps, "unconverged": unconverged,
+        "roofline": {"kernel": "H-matrix product (k_hmv_t + k_hmv_rows)", "bound": "hbm", "achieved": hmv_gbs,
+                     "peak": peak, "unit": "GB/s", "frac": (hmv_gbs / peak) if hmv_gbs else None,
+                     "peak_source": peak_kind, "traffic": None,
+                     "launches": prof["hmv_launches"], "ms_total": prof["hmv_ms"]},
+        "phases_ms_per_step": {"hmatvec": prof["hmv_ms"] / args.steps, "assembly": prof["assemble_ms"] / args.steps},
+        "gpu_launches": prof["kernel_launches"],
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "plain": plain,
+    }
+    if ws == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_oracle_sample(cfg)
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cavity5120", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    cfg = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * libbem: GB300 (sm_103a) frequency-domain elastodynamic boundary element
+ * method with the exponential window (EWM) and frequency-domain windowing.
+ *
+ * Method: Xiao, Ye, Wen, "Efficiency improvement of the frequency-domain BEM
+ * for rapid transient elastodynamic analysis".
+ *   Sec. 2.1  problem (Eq. governing-pde), BIE (Eq. bie), kernels (Eqs. Uij,
+ *             Tij, Gikj), constant-element collocation T u = U t (Eq. Tu_Ut),
+ *             boundary conditions A a = b (Eq. Aa_b)
+ *   Sec. 2.2  sampling relations T = 2 pi / dw, dt = T / N, solve k = 0..N/2
+ *   Sec. 3    exponential window s_k = eta + i k dw, windows, DFT-MFT and
+ *             IDFT-MFT (Eqs. DFT-MFT, IDFT-MFT)
+ *   Sec. 4    the sequence A_k a_k = b_k (Eq. Aa_b-sequence), solution
+ *             extrapolation (Eqs. a0, lsem, a0-solution)
+ *   Sec. 5    block-diagonal preconditioned GMRES, tolerance 1e-5
+ *
+ * Conventions for every entry point:
+ *   - Returns BEM_OK (0) or a negative BEM_ERR_* code; bem_last_error()
+ *     gives a one-line message. No entry point aborts or exits the process.
+ *   - All pointers without the _dev suffix are HOST pointers owned by the
+ *     caller; the library copies what it needs during the call and keeps no
+ *     caller pointer after returning. *_dev pointers are DEVICE pointers on
+ *     the context's device, borrowed for the duration of the call.
+ *   - Complex arrays are interleaved (re, im) float64 pairs.
+ *   - Unknown/dof numbering: dof = 3 * element + component, in the caller's
+ *     element order.
+ *   - One context = one device and one stream; calls on one context must not
+ *     overlap. Work is enqueued on the context's stream; every call that
+ *     returns host data synchronises that stream.
+ *   - The library allocates the device memory it needs (cudaMalloc) and frees
+ *     it in bem_destroy.
+ */
+#ifndef BEM_H_
+#define BEM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BEM_OK 0
+#define BEM_ERR_INVALID_ARG (-1)
+#define BEM_ERR_NO_MESH (-2)
+#define BEM_ERR_OOM (-3)
+#define BEM_ERR_CUDA (-4)
+#define BEM_ERR_NOT_CONVERGED (-5)
+#define BEM_ERR_TIMEOUT (-6)
+#define BEM_ERR_STATE (-7)
+
+/* element boundary-condition kind (Sec. 2.1: Gamma_sigma / Gamma_u) */
+#define BEM_BC_TRACTION 0     /* traction prescribed, displacement unknown */
+#define BEM_BC_DISPLACEMENT 1 /* displacement prescribed, traction unknown */
+
+/* frequency-domain windows (Sec. 3.2) */
+#define BEM_WIN_NONE 0
+#define BEM_WIN_HANNING 1
+#define BEM_WIN_BLACKMAN 2
+
+/* operator precision */
+#define BEM_PREC_C64_MIXED 0 /* complex64 operator and Krylov basis, FP32 kernel
+                                evaluation; FP64 singular/near-singular
+                                integrals, Arnoldi dots, Givens, true-residual
+                                refinement */
+#define BEM_PREC_C128 1      /* complex128 everywhere (the plain form) */
+
+/* initial guess of each frequency system */
+#define BEM_GUESS_ZERO 0
+#define BEM_GUESS_SEM 1 /* least-squares solution extrapolation (Sec. 4.2) */
+
+typedef struct bem_ctx bem_ctx;
+
+typedef struct bem_opts {
+  double tol;         /* true relative residual ||b - A a|| / ||b|| (Sec. 5: 1e-5) */
+  int32_t restart;    /* GMRES restart length m (paper: unstated; default 50) */
+  int32_t max_iters;  /* Arnoldi steps per frequency before NOT_CONVERGED */
+  double aca_tol;     /* ACA stopping tolerance of far-field blocks */
+  int32_t leaf_size;  /* cluster-tree leaf size in elements (default 64) */
+  double eta_adm;     /* admissibility: min(diam) <= eta_adm * dist */
+  int32_t precision;  /* BEM_PREC_* */
+  int32_t guess;      /* BEM_GUESS_* */
+  int32_t sem_k;      /* K previous solutions for the extrapolation (Sec. 4.2: 3-4) */
+  int32_t dense;      /* 1: every block dense (no ACA); for small meshes and tests */
+} bem_opts;
+
+typedef struct bem_freq_stats {
+  int32_t k;              /* frequency index */
+  int32_t iters;          /* Arnoldi steps used */
+  int32_t cycles;         /* restart cycles (each starts from an FP64 true residual) */
+  int32_t converged;      /* 1 if rel_residual <= tol */
+  double s_re, s_im;      /* s_k = eta + i k dw */
+  double rel_residual;    /* final true relative residual, FP64 accumulation */
+  double guess_residual;  /* ||b - A a0|| / ||b|| of the initial guess */
+  double assemble_ms;     /* operator + right-hand side */
+  double guess_ms;
+  double solve_ms;
+  int64_t near_bytes;     /* bytes of dense near-field blocks */
+  int64_t far_bytes;      /* bytes of low-rank factors actually used */
+  int32_t max_rank;
+  int32_t aca_failures;   /* far blocks that hit the rank cap */
+} bem_freq_stats;
+
+/* Fill *opts with the defaults: tol 1e-5, restart 50, max_iters 5000,
+ * aca_tol 1e-5, leaf 64, eta_adm 1.0, mixed precision, SEM guess, K 4. */
+void bem_default_opts(bem_opts* opts);
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+int bem_create(bem_ctx** out, int device, void* cuda_stream);
+void bem_destroy(bem_ctx* ctx);
+const char* bem_last_error(const bem_ctx* ctx);
+
+/* Surface mesh of the solid (Sec. 2.1, constant triangles, Eq. Tu_Ut).
+ * xyz: nv x 3 vertex coordinates; tri: ne x 3 vertex indices, with
+ * (v1 - v0) x (v2 - v0) pointing OUT of the solid (into cavities);
+ * bc_type: ne values BEM_BC_*. Replaces any previous mesh; builds element
+ * geometry, the cluster tree and the frequency-independent static (Kelvin)
+ * parts of the singular and near-singular integrals.
+ * Errors: INVALID_ARG (sizes, index out of range, degenerate triangle). */
+int bem_mesh(bem_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t ne,
+             const int8_t* bc_type, const bem_opts* opts);
+/* Same with device-resident inputs. */
+int bem_mesh_dev(bem_ctx* ctx, const double* xyz_dev, int64_t nv, const int32_t* tri_dev,
+                 int64_t ne, const int8_t* bc_type_dev, const bem_opts* opts);
+
+/* Isotropic material (Sec. 2.1): E > 0, -1 < nu < 0.5, rho > 0. */
+int bem_set_material(bem_ctx* ctx, double E, double nu, double rho);
+
+/* Exponential-window damping eta >= 0 (Sec. 3.1; Eq. ewm-k gives
+ * eta = kappa ln 10 / T) and frequency window BEM_WIN_* (Sec. 3.2). */
+int bem_set_window(bem_ctx* ctx, double eta, int window);
+
+/* Solve the whole sequence A_k a_k = b_k, k = 0..n_omega/2 (Eq.
+ * Aa_b-sequence) at s_k = eta + i k 2 pi / T. The prescribed data is
+ * separable: value(element, component, t) = bc_pattern[3e+c] * P(t), with
+ * load_hist[n] = P(n T / n_omega), n = 0..n_omega-1, transformed by Eq.
+ * DFT-MFT. bc_pattern: ne x 3 (traction on Gamma_sigma elements,
+ * displacement on Gamma_u elements). stats (optional): n_omega/2 + 1
+ * entries. n_omega must be even and >= 2.
+ * Errors: NO_MESH, STATE (material not set), INVALID_ARG, NOT_CONVERGED
+ * (every frequency is still solved as far as max_iters allows and stored). */
+int bem_solve_sweep(bem_ctx* ctx, double T, int32_t n_omega, const double* load_hist,
+                    const double* bc_pattern, const bem_opts* opts, bem_freq_stats* stats);
+int bem_solve_sweep_dev(bem_ctx* ctx, double T, int32_t n_omega, const double* load_hist_dev,
+                        const double* bc_pattern_dev, const bem_opts* opts,
+                        bem_freq_stats* stats);
+
+/* Solution a_k of frequency k (N = 3 ne complex values; displacement at
+ * Gamma_sigma elements, traction at Gamma_u elements). */
+int bem_get_frequency_solution(bem_ctx* ctx, int32_t k, double* out);
+
+/* Time response R(n dt), n = 0..n_omega-1, at the given dofs by Eq.
+ * IDFT-MFT with the context's window, the spectrum extended by conjugate
+ * symmetry (Sec. 2.2 step 3; the k = 0 and k = n_omega/2 samples enter by
+ * their real parts). out: n_omega x ndof row-major float64. */
+int bem_time_response(bem_ctx* ctx, const int64_t* dofs, int64_t ndof, double* out);
+/* Same, device output (n_omega x ndof float64) and device dof list. */
+int bem_time_response_dev(bem_ctx* ctx, const int64_t* dofs_dev, int64_t ndof, double* out_dev);
+
+/* ---- step-level entry points (each is one step of the sweep) ---------- */
+
+/* Eq. DFT-MFT: out[k], k = 0..n_omega/2 (complex) of P(n dt). */
+int bem_load_dft(bem_ctx* ctx, double T, int32_t n_omega, double eta, const double* load_hist,
+                 double* out);
+
+/* Eq. IDFT-MFT on an arbitrary spectrum: Rk is (n_omega/2+1) x ndof complex,
+ * out is n_omega x ndof float64. */
+int bem_idft(bem_ctx* ctx, double T, int32_t n_omega, double eta, int window, const double* Rk,
+             int64_t ndof, double* out);
+
+/* Build the operator A(s) (near-field blocks, ACA far-field blocks, block
+ * preconditioner) at the complex frequency s. */
+int bem_assemble(bem_ctx* ctx, double s_re, double s_im, const bem_opts* opts);
+
+/* Rows of the assembled operator: out is nrows x N complex (dense rows,
+ * far-field entries reconstructed from the low-rank factors). */
+int bem_operator_rows(bem_ctx* ctx, const int64_t* rows, int64_t nrows, double* out);
+
+/* y = A x with the assembled operator (FP64 accumulation). x, y: N complex. */
+int bem_apply(bem_ctx* ctx, const double* x, double* y);
+
+/* Right-hand side b = p * B(s) pattern of Eq. Aa_b at the assembled s,
+ * where B has the U columns of Gamma_sigma elements and -T (free term
+ * included) columns of Gamma_u elements. pattern: ne x 3 real. */
+int bem_rhs(bem_ctx* ctx, double p_re, double p_im, const double* pattern, double* b);
+
+/* Solve A(s) x = b at the assembled s by block-Jacobi GMRES; x0 may be NULL
+ * (zero guess). */
+int bem_solve_assembled(bem_ctx* ctx, const double* b, const double* x0, double* x,
+                        const bem_opts* opts, bem_freq_stats* stats);
+
+/* Solution extrapolation (Sec. 4.2) at the assembled s: a0 = X s with
+ * s = argmin ||A X s - b||; X is K x N complex (rows = previous solutions). */
+int bem_sem_guess(bem_ctx* ctx, int32_t K, const double* X, const double* b, double* a0);
+
+/* ---- measurement ------------------------------------------------------- */
+
+typedef struct bem_profile {
+  int64_t hmv_launches;     /* H-matrix products (one launch pair each) */
+  double hmv_ms;            /* summed CUDA-event time of those products */
+  double hmv_bytes;         /* algorithmic bytes: operator entries used + x read + y written */
+  int64_t assemble_calls;   /* operator assemblies */
+  double assemble_ms;       /* summed CUDA-event time of assembly (RHS, singular, near, ACA) */
+  int64_t kernel_launches;  /* kernels launched by the library since profiling was (re)enabled */
+} bem_profile;
+
+/* Enable (1) or disable (0) event timing of the H-matrix products and of
+ * assembly on the context's stream, and reset the counters. Timing adds two
+ * event records per timed launch; results are complete after any call that
+ * synchronises the stream. */
+int bem_set_profiling(bem_ctx* ctx, int on);
+int bem_get_profile(bem_ctx* ctx, bem_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_H_ */

@@ -1,0 +1,304 @@
+"""Thin Python binding of the libbem C-ABI (argument marshalling only).
+
+Every step of the method runs in the CUDA library; this module converts numpy
+arrays and torch tensors to pointers and sizes and turns negative return
+codes into ``BemError``. The library must have been built (``build.build()``);
+importing fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbem.so")
+
+BEM_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "NO_MESH", -3: "OOM", -4: "CUDA", -5: "NOT_CONVERGED", -6: "TIMEOUT",
+          -7: "STATE"}
+BC_TRACTION, BC_DISPLACEMENT = 0, 1
+WIN_NONE, WIN_HANNING, WIN_BLACKMAN = 0, 1, 2
+PREC_C64_MIXED, PREC_C128 = 0, 1
+GUESS_ZERO, GUESS_SEM = 0, 1
+
+EXPORTED = [
+    "bem_default_opts", "bem_create", "bem_destroy", "bem_last_error", "bem_mesh", "bem_mesh_dev",
+    "bem_set_material", "bem_set_window", "bem_solve_sweep", "bem_solve_sweep_dev",
+    "bem_get_frequency_solution", "bem_time_response", "bem_time_response_dev", "bem_load_dft", "bem_idft",
+    "bem_assemble", "bem_operator_rows", "bem_apply", "bem_rhs", "bem_solve_assembled", "bem_sem_guess",
+    "bem_set_profiling", "bem_get_profile",
+]
+
+
+class BemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("aca_tol", ctypes.c_double), ("leaf_size", ctypes.c_int32), ("eta_adm", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("guess", ctypes.c_int32), ("sem_k", ctypes.c_int32),
+                ("dense", ctypes.c_int32)]
+
+
+class FreqStats(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("s_re", ctypes.c_double), ("s_im", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("guess_residual", ctypes.c_double),
+                ("assemble_ms", ctypes.c_double), ("guess_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("near_bytes", ctypes.c_int64), ("far_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int32),
+                ("aca_failures", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("hmv_launches", ctypes.c_int64), ("hmv_ms", ctypes.c_double), ("hmv_bytes", ctypes.c_double),
+                ("assemble_calls", ctypes.c_int64), ("assemble_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libbem.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libbem.so not built at {path}; run paper_1212_3032_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "bem_default_opts": (None, [ctypes.POINTER(Opts)]),
+        "bem_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, P]),
+        "bem_destroy": (None, [P]),
+        "bem_last_error": (ctypes.c_char_p, [P]),
+        "bem_mesh": (ctypes.c_int, [P, P, I64, P, I64, P, ctypes.POINTER(Opts)]),
+        "bem_mesh_dev": (ctypes.c_int, [P, P, I64, P, I64, P, ctypes.POINTER(Opts)]),
+        "bem_set_material": (ctypes.c_int, [P, D, D, D]),
+        "bem_set_window": (ctypes.c_int, [P, D, ctypes.c_int]),
+        "bem_solve_sweep": (ctypes.c_int, [P, D, I32, P, P, ctypes.POINTER(Opts), P]),
+        "bem_solve_sweep_dev": (ctypes.c_int, [P, D, I32, P, P, ctypes.POINTER(Opts), P]),
+        "bem_get_frequency_solution": (ctypes.c_int, [P, I32, P]),
+        "bem_time_response": (ctypes.c_int, [P, P, I64, P]),
+        "bem_time_response_dev": (ctypes.c_int, [P, P, I64, P]),
+        "bem_load_dft": (ctypes.c_int, [P, D, I32, D, P, P]),
+        "bem_idft": (ctypes.c_int, [P, D, I32, D, ctypes.c_int, P, I64, P]),
+        "bem_assemble": (ctypes.c_int, [P, D, D, ctypes.POINTER(Opts)]),
+        "bem_operator_rows": (ctypes.c_int, [P, P, I64, P]),
+        "bem_apply": (ctypes.c_int, [P, P, P]),
+        "bem_rhs": (ctypes.c_int, [P, D, D, P, P]),
+        "bem_solve_assembled": (ctypes.c_int, [P, P, P, P, ctypes.POINTER(Opts), P]),
+        "bem_sem_guess": (ctypes.c_int, [P, I32, P, P, P]),
+        "bem_set_profiling": (ctypes.c_int, [P, ctypes.c_int]),
+        "bem_get_profile": (ctypes.c_int, [P, ctypes.POINTER(Profile)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_opts(**kw) -> Opts:
+    lib = load_library()
+    o = Opts()
+    lib.bem_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _tptr(t):
+    return ctypes.c_void_p(int(t.data_ptr()))
+
+
+class Context:
+    """One libbem context on one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load_library()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = 0
+        h = ctypes.c_void_p()
+        rc = self.lib.bem_create(ctypes.byref(h), int(device), ctypes.c_void_p(int(stream)))
+        if rc != BEM_OK:
+            raise BemError(rc, "bem_create failed")
+        self.h = h
+        self.ne = 0
+        self.n_omega = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc, allow=()):
+        if rc != BEM_OK and rc not in allow:
+            raise BemError(rc, self.lib.bem_last_error(self.h).decode())
+        return rc
+
+    # --- problem definition -------------------------------------------------
+    def mesh(self, xyz, tri, bc_type, opts: Opts | None = None):
+        xyz = _f64(xyz)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        bc = np.ascontiguousarray(bc_type, dtype=np.int8)
+        self._check(self.lib.bem_mesh(self.h, _ptr(xyz), xyz.shape[0], _ptr(tri), tri.shape[0], _ptr(bc),
+                                      ctypes.byref(opts) if opts else None))
+        self.ne = tri.shape[0]
+
+    def mesh_dev(self, xyz_t, tri_t, bc_t, opts: Opts | None = None):
+        self._check(self.lib.bem_mesh_dev(self.h, _tptr(xyz_t), xyz_t.shape[0], _tptr(tri_t), tri_t.shape[0],
+                                          _tptr(bc_t), ctypes.byref(opts) if opts else None))
+        self.ne = int(tri_t.shape[0])
+
+    def set_material(self, E, nu, rho):
+        self._check(self.lib.bem_set_material(self.h, float(E), float(nu), float(rho)))
+
+    def set_window(self, eta, window=WIN_NONE):
+        self._check(self.lib.bem_set_window(self.h, float(eta), int(window)))
+
+    # --- sweep ----------------------------------------------------------------
+    def solve_sweep(self, T, n_omega, load_hist, pattern, opts: Opts | None = None, allow_unconverged=False):
+        load = _f64(load_hist)
+        pat = _f64(pattern)
+        stats = (FreqStats * (n_omega // 2 + 1))()
+        rc = self.lib.bem_solve_sweep(self.h, float(T), int(n_omega), _ptr(load), _ptr(pat),
+                                      ctypes.byref(opts) if opts else None, stats)
+        self._check(rc, allow=(-5,) if allow_unconverged else ())
+        self.n_omega = n_omega
+        return [s.as_dict() for s in stats]
+
+    def solve_sweep_dev(self, T, n_omega, load_t, pattern_t, opts: Opts | None = None, allow_unconverged=False):
+        stats = (FreqStats * (n_omega // 2 + 1))()
+        rc = self.lib.bem_solve_sweep_dev(self.h, float(T), int(n_omega), _tptr(load_t), _tptr(pattern_t),
+                                          ctypes.byref(opts) if opts else None, stats)
+        self._check(rc, allow=(-5,) if allow_unconverged else ())
+        self.n_omega = n_omega
+        return [s.as_dict() for s in stats]
+
+    def get_frequency_solution(self, k):
+        out = np.zeros(3 * self.ne, dtype=np.complex128)
+        self._check(self.lib.bem_get_frequency_solution(self.h, int(k), _ptr(out)))
+        return out
+
+    def time_response(self, dofs):
+        dofs = np.ascontiguousarray(dofs, dtype=np.int64)
+        out = np.zeros((self.n_omega, dofs.size), dtype=np.float64)
+        self._check(self.lib.bem_time_response(self.h, _ptr(dofs), dofs.size, _ptr(out)))
+        return out
+
+    def time_response_dev(self, dofs_t, out_t):
+        self._check(self.lib.bem_time_response_dev(self.h, _tptr(dofs_t), dofs_t.numel(), _tptr(out_t)))
+
+    # --- step-level entry points -------------------------------------------
+    def load_dft(self, T, n_omega, eta, load_hist):
+        load = _f64(load_hist)
+        out = np.zeros(n_omega // 2 + 1, dtype=np.complex128)
+        self._check(self.lib.bem_load_dft(self.h, float(T), int(n_omega), float(eta), _ptr(load), _ptr(out)))
+        return out
+
+    def idft(self, T, n_omega, eta, window, Rk):
+        Rk = _c128(Rk)
+        if Rk.ndim == 1:
+            Rk = Rk[:, None]
+        ndof = Rk.shape[1]
+        out = np.zeros((n_omega, ndof), dtype=np.float64)
+        self._check(self.lib.bem_idft(self.h, float(T), int(n_omega), float(eta), int(window), _ptr(Rk), ndof,
+                                      _ptr(out)))
+        return out
+
+    def assemble(self, s, opts: Opts | None = None):
+        s = complex(s)
+        self._check(self.lib.bem_assemble(self.h, s.real, s.imag, ctypes.byref(opts) if opts else None))
+
+    def operator_rows(self, rows):
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        out = np.zeros((rows.size, 3 * self.ne), dtype=np.complex128)
+        self._check(self.lib.bem_operator_rows(self.h, _ptr(rows), rows.size, _ptr(out)))
+        return out
+
+    def apply(self, x):
+        x = _c128(x)
+        y = np.zeros_like(x)
+        self._check(self.lib.bem_apply(self.h, _ptr(x), _ptr(y)))
+        return y
+
+    def rhs(self, p, pattern):
+        p = complex(p)
+        pat = _f64(pattern)
+        b = np.zeros(3 * self.ne, dtype=np.complex128)
+        self._check(self.lib.bem_rhs(self.h, p.real, p.imag, _ptr(pat), _ptr(b)))
+        return b
+
+    def solve_assembled(self, b, x0=None, opts: Opts | None = None, allow_unconverged=False):
+        b = _c128(b)
+        x = np.zeros_like(b)
+        st = FreqStats()
+        x0p = _ptr(_c128(x0)) if x0 is not None else None
+        x0keep = _c128(x0) if x0 is not None else None
+        if x0keep is not None:
+            x0p = _ptr(x0keep)
+        rc = self.lib.bem_solve_assembled(self.h, _ptr(b), x0p, _ptr(x), ctypes.byref(opts) if opts else None,
+                                          ctypes.byref(st))
+        self._check(rc, allow=(-5,) if allow_unconverged else ())
+        return x, st.as_dict()
+
+    def sem_guess(self, X, b):
+        X = _c128(X)
+        if X.ndim == 1:
+            X = X[None, :]
+        b = _c128(b)
+        a0 = np.zeros_like(b)
+        self._check(self.lib.bem_sem_guess(self.h, X.shape[0], _ptr(X) if X.size else None, _ptr(b), _ptr(a0)))
+        return a0
+
+    # --- measurement -------------------------------------------------------
+    def set_profiling(self, on: bool):
+        self._check(self.lib.bem_set_profiling(self.h, 1 if on else 0))
+
+    def get_profile(self):
+        p = Profile()
+        self._check(self.lib.bem_get_profile(self.h, ctypes.byref(p)))
+        return p.as_dict()

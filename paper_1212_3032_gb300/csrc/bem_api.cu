@@ -1,0 +1,1409 @@
+// C-ABI entry points and host orchestration of the frequency sweep.
+//
+// bem_solve_sweep follows Sec. 2.2 with the substitutions of Sec. 3.3:
+//   1. P_k by Eq. DFT-MFT (device kernel)
+//   2. for k = 0..N/2 (Eq. Aa_b-sequence) at s_k = eta + i k dw (Sec. 3.1):
+//        right-hand side b_k (Eq. Aa_b), operator A_k (near blocks + ACA),
+//        initial guess (zero or Sec. 4.2 extrapolation),
+//        block-Jacobi GMRES (Sec. 5) whose restarts start from the true
+//        residual accumulated in FP64 (iterative refinement of the c64 solve)
+//   3. bem_time_response: Eq. IDFT-MFT with the window of Sec. 3.2.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bem_internal.h"
+#include "bem_launch.h"
+
+using bem::c128;
+using bem::c64;
+
+namespace bem {
+
+int fail(bem_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int fail_cuda(bem_ctx* ctx, cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e),
+           what, file, line);
+  if (ctx) ctx->err = buf;
+  return e == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA;
+}
+
+// Gauss-Legendre nodes/weights on [0, 1] by Newton iteration on P_q; series
+// coefficients of the regular radial parts from the exponential series:
+//   Ah_m = (-1)^m [1/m! - 1/(m+1)! + 1/(m+2)!]
+//   Bh_m = (-1)^m [1/(m+2)! - 1/(m+1)!]
+//   Ch_m = (-1)^m [1/m! - 3/(m+1)! + 3/(m+2)!]
+void make_rule_tables(RuleTables& t) {
+  memset(&t, 0, sizeof(t));
+  for (int q = 1; q <= GL_MAX; ++q) {
+    for (int i = 0; i < q; ++i) {
+      long double x = cosl(3.14159265358979323846264338327950288L * (i + 0.75L) / (q + 0.5L));
+      long double dp = 0;
+      for (int it = 0; it < 100; ++it) {
+        long double p0 = 1, p1 = x;
+        for (int k = 2; k <= q; ++k) {
+          long double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = q * (x * p1 - p0) / (x * x - 1);
+        long double dx = p1 / dp;
+        x -= dx;
+        if (fabsl(dx) < 1e-19L) break;
+      }
+      long double p0 = 1, p1 = x;
+      for (int k = 2; k <= q; ++k) {
+        long double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = q * (x * p1 - p0) / (x * x - 1);
+      long double w = 2 / ((1 - x * x) * dp * dp);
+      t.gl_x[q][q - 1 - i] = (double)((x + 1) / 2);
+      t.gl_w[q][q - 1 - i] = (double)(w / 2);
+    }
+    // sort ascending
+    std::vector<std::pair<double, double>> v;
+    for (int i = 0; i < q; ++i) v.push_back({t.gl_x[q][i], t.gl_w[q][i]});
+    std::sort(v.begin(), v.end());
+    for (int i = 0; i < q; ++i) {
+      t.gl_x[q][i] = v[i].first;
+      t.gl_w[q][i] = v[i].second;
+    }
+  }
+  long double fact[SERIES_TERMS + 3];
+  fact[0] = 1;
+  for (int k = 1; k < SERIES_TERMS + 3; ++k) fact[k] = fact[k - 1] * k;
+  long double a[SERIES_TERMS + 1], b[SERIES_TERMS + 1], c[SERIES_TERMS + 1];
+  for (int m = 0; m <= SERIES_TERMS; ++m) {
+    long double sg = (m % 2) ? -1 : 1;
+    a[m] = sg * (1 / fact[m] - 1 / fact[m + 1] + 1 / fact[m + 2]);
+    b[m] = sg * (1 / fact[m + 2] - 1 / fact[m + 1]);
+    c[m] = sg * (1 / fact[m] - 3 / fact[m + 1] + 3 / fact[m + 2]);
+  }
+  for (int m = 0; m < SERIES_TERMS; ++m) {
+    t.ser[0][m] = (double)a[m];
+    t.ser[1][m] = (double)b[m];
+    t.ser[2][m] = (double)c[m];
+    t.ser[3][m] = (double)((m + 1) * a[m + 1]);
+    t.ser[4][m] = (double)((m + 1) * b[m + 1]);
+    t.ser[5][m] = (double)((m + 1) * c[m + 1]);
+  }
+}
+
+template <typename R> KParams<R> make_params(const bem_ctx* ctx, double sre, double sim) {
+  KParams<R> P;
+  std::complex<double> s(sre, sim);
+  std::complex<double> ks = s / ctx->cs, kp = s / ctx->cp;
+  P.s = {R(sre), R(sim)};
+  P.ks = {R(ks.real()), R(ks.imag())};
+  P.kp = {R(kp.real()), R(kp.imag())};
+  P.beta2 = R((ctx->cs / ctx->cp) * (ctx->cs / ctx->cp));
+  P.k2 = R((ctx->cp / ctx->cs) * (ctx->cp / ctx->cs));
+  P.u_scale = R(1.0 / (4.0 * M_PI * ctx->mu));
+  P.t_scale = R(1.0 / (4.0 * M_PI));
+  P.nu = R(ctx->nu);
+  P.kel_u = R(1.0 / (16.0 * M_PI * ctx->mu * (1.0 - ctx->nu)));
+  P.kel_t = R(1.0 / (8.0 * M_PI * (1.0 - ctx->nu)));
+  return P;
+}
+
+}  // namespace bem
+
+using namespace bem;
+
+// ---------------------------------------------------------------------------
+// small kernels local to the orchestration
+// ---------------------------------------------------------------------------
+__global__ void k_permute_pattern(const double* __restrict__ in, const int* __restrict__ perm, int ne,
+                                  double* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ne) return;
+  int e = perm[k];
+  for (int a = 0; a < 3; ++a) out[3 * k + a] = in[3 * e + a];
+}
+
+// deterministic compaction of elements with a nonzero pattern (one CTA)
+__global__ void k_loaded(const double* __restrict__ pat, int ne, int* __restrict__ list, int* __restrict__ count) {
+  __shared__ int wt[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c0 = 0; c0 < ne; c0 += blockDim.x) {
+    int e = c0 + threadIdx.x;
+    bool f = e < ne && (pat[3 * e] != 0.0 || pat[3 * e + 1] != 0.0 || pat[3 * e + 2] != 0.0);
+    unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wt[wid] = __popc(m);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < wid) before += wt[w];
+      tot += wt[w];
+    }
+    if (f) list[base + before + __popc(m & ((1u << lane) - 1))] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) base += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
+__global__ void k_pinv_cast(const c128* __restrict__ a, c64* __restrict__ b, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = c64{(float)a[i].re, (float)a[i].im};
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timer() {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+int check_launch(bem_ctx* ctx, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(ctx, e, what, __FILE__, __LINE__);
+  return BEM_OK;
+}
+
+#define CK(what)                                 \
+  do {                                           \
+    int _r = check_launch(ctx, what);            \
+    if (_r != BEM_OK) return _r;                 \
+  } while (0)
+
+#define TRY(expr)                \
+  do {                           \
+    int _r = (expr);             \
+    if (_r != BEM_OK) return _r; \
+  } while (0)
+
+int set_device(bem_ctx* ctx) {
+  BEM_CUDA_TRY(cudaSetDevice(ctx->device));
+  return BEM_OK;
+}
+
+// Reduce sum conj(a).b over FP64 into host value (synchronises).
+template <typename A, typename B>
+int dot_host(bem_ctx* ctx, const A* a, const B* b, long long n, std::complex<double>& out) {
+  BEM_CUDA_TRY(ctx->red.ensure(64 * 8));
+  c128* part = reinterpret_cast<c128*>(ctx->red.p);
+  int nblk = launch_dots<A, B>(a, n, 1, b, n, part, ctx->stream);
+  launch_dots_final(part, nblk, 1, reinterpret_cast<c128*>(ctx->red.p) + 64 * 2, ctx->stream);
+  CK("dot");
+  c128 h;
+  BEM_CUDA_TRY(cudaMemcpyAsync(&h, reinterpret_cast<c128*>(ctx->red.p) + 64 * 2, sizeof(c128),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  out = {h.re, h.im};
+  return BEM_OK;
+}
+
+int ensure_static(bem_ctx* ctx);
+
+bool is_mixed(const bem_ctx* ctx) { return ctx->prec == BEM_PREC_C64_MIXED; }
+
+cudaEvent_t take_event(bem_ctx* ctx) {
+  if (ctx->event_pool.empty()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  cudaEvent_t e = ctx->event_pool.back();
+  ctx->event_pool.pop_back();
+  return e;
+}
+
+// Records the start of a timed region (returns the event or null).
+cudaEvent_t prof_begin(bem_ctx* ctx) {
+  if (!ctx->profiling) return nullptr;
+  cudaEvent_t a = take_event(ctx);
+  cudaEventRecord(a, ctx->stream);
+  return a;
+}
+void prof_end(bem_ctx* ctx, cudaEvent_t a, int kind, double bytes) {
+  if (!a) return;
+  cudaEvent_t b = take_event(ctx);
+  cudaEventRecord(b, ctx->stream);
+  ctx->pending.push_back({a, b, bytes, kind});
+}
+// Folds completed timings into the counters (call after a stream sync).
+void prof_harvest(bem_ctx* ctx) {
+  for (auto& p : ctx->pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      if (p.kind == 0) {
+        ctx->prof_hmv_ms += ms;
+        ctx->prof_hmv_bytes += p.bytes;
+        ctx->prof_hmv_launches += 1;
+      } else {
+        ctx->prof_asm_ms += ms;
+        ctx->prof_asm_calls += 1;
+      }
+    }
+    ctx->event_pool.push_back(p.a);
+    ctx->event_pool.push_back(p.b);
+  }
+  ctx->pending.clear();
+}
+
+// Algorithmic bytes of one H-matrix product: every stored operator entry in
+// use (near blocks, U and V columns up to the rank), x read once, y written once.
+double hmv_bytes(const bem_ctx* ctx, int op_bytes, int x_bytes, int y_bytes, int nrhs, long long used_lowrank) {
+  return (double)op_bytes * (ctx->near_entries + used_lowrank) + (double)nrhs * ctx->N * (x_bytes + y_bytes);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" void bem_default_opts(bem_opts* o) {
+  if (!o) return;
+  o->tol = 1e-5;
+  o->restart = 50;
+  o->max_iters = 5000;
+  o->aca_tol = 1e-5;
+  o->leaf_size = 64;
+  o->eta_adm = 1.0;
+  o->precision = BEM_PREC_C64_MIXED;
+  o->guess = BEM_GUESS_SEM;
+  o->sem_k = 4;
+  o->dense = 0;
+}
+
+extern "C" int bem_create(bem_ctx** out, int device, void* stream) {
+  if (!out) return BEM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return BEM_ERR_CUDA;
+  bem_ctx* ctx = new bem_ctx();
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  bem_default_opts(&ctx->mesh_opts);
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return BEM_ERR_CUDA;
+  }
+  RuleTables t;
+  make_rule_tables(t);
+  if (upload_rules_assemble(t, ctx->stream) != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    delete ctx;
+    return BEM_ERR_CUDA;
+  }
+  if (cudaMallocHost(&ctx->host_red, 4096 * sizeof(double)) != cudaSuccess) {
+    delete ctx;
+    return BEM_ERR_OOM;
+  }
+  *out = ctx;
+  return BEM_OK;
+}
+
+extern "C" void bem_destroy(bem_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->host_red) cudaFreeHost(ctx->host_red);
+  for (auto& p : ctx->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+extern "C" const char* bem_last_error(const bem_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int bem_set_material(bem_ctx* ctx, double E, double nu, double rho) {
+  if (!ctx) return BEM_ERR_INVALID_ARG;
+  if (!(E > 0) || !(rho > 0) || !(nu > -1.0) || !(nu < 0.5))
+    return fail(ctx, BEM_ERR_INVALID_ARG, "material needs E > 0, rho > 0, -1 < nu < 0.5");
+  bool changed = !ctx->have_mat || E != ctx->E || nu != ctx->nu || rho != ctx->rho;
+  ctx->E = E;
+  ctx->nu = nu;
+  ctx->rho = rho;
+  ctx->mu = E / (2.0 * (1.0 + nu));
+  ctx->lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  ctx->cs = std::sqrt(ctx->mu / rho);
+  ctx->cp = std::sqrt((ctx->lam + 2.0 * ctx->mu) / rho);
+  ctx->have_mat = true;
+  if (changed) ctx->sing_static.release();  // Kelvin parts depend on mu, nu
+  ctx->assembled = false;
+  return BEM_OK;
+}
+
+extern "C" int bem_set_window(bem_ctx* ctx, double eta, int window) {
+  if (!ctx) return BEM_ERR_INVALID_ARG;
+  if (!(eta >= 0) || !std::isfinite(eta)) return fail(ctx, BEM_ERR_INVALID_ARG, "eta must be finite and >= 0");
+  if (window < BEM_WIN_NONE || window > BEM_WIN_BLACKMAN) return fail(ctx, BEM_ERR_INVALID_ARG, "unknown window");
+  ctx->eta = eta;
+  ctx->window = window;
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int* tri_d, int ne,
+                     const signed char* bc_d, const bem_opts* opts) {
+  cudaStream_t st = ctx->stream;
+  bem_opts o;
+  bem_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.leaf_size < 1 || o.leaf_size > 1024) return fail(ctx, BEM_ERR_INVALID_ARG, "leaf_size out of range");
+  if (!(o.eta_adm > 0)) return fail(ctx, BEM_ERR_INVALID_ARG, "eta_adm must be > 0");
+  ctx->have_mesh = false;
+  ctx->assembled = false;
+  ctx->nf = 0;
+  ctx->mesh_opts = o;
+  ctx->ne = ne;
+  ctx->N = 3LL * ne;
+
+  DevBuf<double> cen, hh;
+  DevBuf<int> bad;
+  BEM_CUDA_TRY(cen.alloc(3LL * ne));
+  BEM_CUDA_TRY(hh.alloc(ne));
+  BEM_CUDA_TRY(bad.alloc(1));
+  BEM_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+  launch_centroids(xyz_d, nv, tri_d, ne, cen.p, hh.p, bad.p, st);
+  CK("centroids");
+  std::vector<double> cen_h(3LL * ne), h_h(ne);
+  int bad_h = 0;
+  BEM_CUDA_TRY(cudaMemcpyAsync(cen_h.data(), cen.p, 3LL * ne * sizeof(double), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaMemcpyAsync(h_h.data(), hh.p, ne * sizeof(double), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaMemcpyAsync(&bad_h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (bad_h == 1) return fail(ctx, BEM_ERR_INVALID_ARG, "triangle vertex index out of range");
+  if (bad_h == 2) return fail(ctx, BEM_ERR_INVALID_ARG, "degenerate triangle");
+
+  build_cluster_tree(cen_h.data(), h_h.data(), ne, o.leaf_size, o.eta_adm, RHO2_NEAR, o.dense != 0, ctx->tree);
+  const ClusterTree& tr = ctx->tree;
+  BEM_CUDA_TRY(ctx->perm.alloc(ne));
+  BEM_CUDA_TRY(ctx->iperm.alloc(ne));
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->perm.p, tr.perm.data(), ne * sizeof(int), cudaMemcpyHostToDevice, st));
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->iperm.p, tr.iperm.data(), ne * sizeof(int), cudaMemcpyHostToDevice, st));
+  BEM_CUDA_TRY(ctx->ef.alloc(ne));
+  BEM_CUDA_TRY(ctx->ed.alloc(ne));
+  BEM_CUDA_TRY(ctx->bc.alloc(ne));
+  launch_geometry(xyz_d, tri_d, ctx->perm.p, bc_d, ne, ctx->ef.p, ctx->ed.p, ctx->bc.p, st);
+  CK("geometry");
+  ctx->bc_host.resize(ne);
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->bc_host.data(), ctx->bc.p, ne, cudaMemcpyDeviceToHost, st));
+
+  // near / far block descriptors
+  ctx->near_h.clear();
+  ctx->far_h.clear();
+  long long noff = 0;
+  for (const BlockPair& bp : tr.near) {
+    const Cluster& t = tr.nodes[bp.tau];
+    const Cluster& s = tr.nodes[bp.sigma];
+    NearBlk nb;
+    nb.off = noff;
+    nb.r0 = t.begin;
+    nb.nr = t.size();
+    nb.c0 = s.begin;
+    nb.nc = s.size();
+    noff += 9LL * nb.nr * nb.nc;
+    ctx->near_h.push_back(nb);
+  }
+  ctx->near_entries = noff;
+  long long uoff = 0, voff = 0;
+  int toff = 0;
+  for (const BlockPair& bp : tr.far) {
+    const Cluster& t = tr.nodes[bp.tau];
+    const Cluster& s = tr.nodes[bp.sigma];
+    FarBlk fb;
+    fb.r0 = t.begin;
+    fb.nr = t.size();
+    fb.c0 = s.begin;
+    fb.nc = s.size();
+    int mn = 3 * std::min(fb.nr, fb.nc);
+    fb.rmax = std::min(mn, 128);
+    fb.uoff = uoff;
+    fb.voff = voff;
+    fb.toff = toff;
+    uoff += 3LL * fb.nr * fb.rmax;
+    voff += 3LL * fb.nc * fb.rmax;
+    toff += fb.rmax;
+    ctx->far_h.push_back(fb);
+  }
+  ctx->u_entries = uoff;
+  ctx->v_entries = voff;
+  ctx->t_entries = toff;
+  BEM_CUDA_TRY(ctx->near_d.alloc(std::max<size_t>(1, ctx->near_h.size())));
+  BEM_CUDA_TRY(ctx->far_d.alloc(std::max<size_t>(1, ctx->far_h.size())));
+  if (!ctx->near_h.empty())
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->near_d.p, ctx->near_h.data(), ctx->near_h.size() * sizeof(NearBlk),
+                                 cudaMemcpyHostToDevice, st));
+  if (!ctx->far_h.empty())
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->far_d.p, ctx->far_h.data(), ctx->far_h.size() * sizeof(FarBlk),
+                                 cudaMemcpyHostToDevice, st));
+
+  // leaves and matrix-vector panels (CSR by leaf row)
+  ctx->leaf_nodes.clear();
+  for (int id = 0; id < (int)tr.nodes.size(); ++id)
+    if (tr.nodes[id].leaf()) ctx->leaf_nodes.push_back(id);
+  std::sort(ctx->leaf_nodes.begin(), ctx->leaf_nodes.end(),
+            [&](int a, int b) { return tr.nodes[a].begin < tr.nodes[b].begin; });
+  int L = (int)ctx->leaf_nodes.size();
+  ctx->nleaves = L;
+  std::vector<int> leaf_idx(tr.nodes.size(), -1);
+  std::vector<int> r0(L), nr(L);
+  for (int l = 0; l < L; ++l) {
+    leaf_idx[ctx->leaf_nodes[l]] = l;
+    r0[l] = tr.nodes[ctx->leaf_nodes[l]].begin;
+    nr[l] = tr.nodes[ctx->leaf_nodes[l]].size();
+  }
+  std::vector<std::vector<Panel>> per(L);
+  for (size_t b = 0; b < ctx->near_h.size(); ++b) {
+    const NearBlk& nb = ctx->near_h[b];
+    int l = leaf_idx[tr.near[b].tau];
+    Panel p;
+    p.data = nb.off;
+    p.ld = 3 * nb.nr;
+    p.ncols = 3 * nb.nc;
+    p.xoff = 3 * nb.c0;
+    p.kind = 0;
+    per[l].push_back(p);
+  }
+  for (size_t b = 0; b < ctx->far_h.size(); ++b) {
+    const FarBlk& fb = ctx->far_h[b];
+    // every leaf inside the row cluster gets the matching slice of U_b
+    for (int l = 0; l < L; ++l) {
+      if (r0[l] >= fb.r0 && r0[l] + nr[l] <= fb.r0 + fb.nr) {
+        Panel p;
+        p.data = fb.uoff + 3LL * (r0[l] - fb.r0);
+        p.ld = 3 * fb.nr;
+        p.ncols = 0;
+        p.xoff = (int)b;
+        p.kind = 1;
+        per[l].push_back(p);
+      }
+    }
+  }
+  std::vector<int> pptr(L + 1, 0);
+  std::vector<Panel> pan;
+  for (int l = 0; l < L; ++l) {
+    pptr[l] = (int)pan.size();
+    pan.insert(pan.end(), per[l].begin(), per[l].end());
+  }
+  pptr[L] = (int)pan.size();
+  BEM_CUDA_TRY(ctx->leaf_r0.alloc(L));
+  BEM_CUDA_TRY(ctx->leaf_nr.alloc(L));
+  BEM_CUDA_TRY(ctx->panel_ptr.alloc(L + 1));
+  BEM_CUDA_TRY(ctx->panels.alloc(std::max<size_t>(1, pan.size())));
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->leaf_r0.p, r0.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->leaf_nr.p, nr.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->panel_ptr.p, pptr.data(), (L + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (!pan.empty())
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->panels.p, pan.data(), pan.size() * sizeof(Panel), cudaMemcpyHostToDevice, st));
+
+  // singular and near-singular pairs of the near blocks
+  int nnb = (int)ctx->near_h.size();
+  DevBuf<int> cnt;
+  BEM_CUDA_TRY(cnt.alloc(std::max(1, nnb)));
+  launch_sing_count(ctx->near_d.p, nnb, ctx->ed.p, cnt.p, st);
+  CK("sing_count");
+  std::vector<int> cnt_h(nnb);
+  if (nnb) BEM_CUDA_TRY(cudaMemcpyAsync(cnt_h.data(), cnt.p, nnb * sizeof(int), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<int> offs(nnb + 1, 0);
+  for (int b = 0; b < nnb; ++b) offs[b + 1] = offs[b] + cnt_h[b];
+  ctx->nsing = offs[nnb];
+  BEM_CUDA_TRY(cnt.alloc(nnb + 1));
+  BEM_CUDA_TRY(cudaMemcpyAsync(cnt.p, offs.data(), (nnb + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  BEM_CUDA_TRY(ctx->sing.alloc(std::max(1, ctx->nsing)));
+  launch_sing_fill(ctx->near_d.p, nnb, ctx->ed.p, cnt.p, ctx->sing.p, st);
+  CK("sing_fill");
+  ctx->sing_static.release();
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  ctx->have_mesh = true;
+  return BEM_OK;
+}
+
+extern "C" int bem_mesh_dev(bem_ctx* ctx, const double* xyz_dev, int64_t nv, const int32_t* tri_dev, int64_t ne,
+                            const int8_t* bc_dev, const bem_opts* opts) {
+  if (!ctx) return BEM_ERR_INVALID_ARG;
+  if (!xyz_dev || !tri_dev || !bc_dev || nv < 3 || ne < 1 || ne > (1LL << 28))
+    return fail(ctx, BEM_ERR_INVALID_ARG, "bem_mesh: bad sizes or null pointers");
+  TRY(set_device(ctx));
+  return mesh_impl(ctx, xyz_dev, nv, tri_dev, (int)ne, (const signed char*)bc_dev, opts);
+}
+
+extern "C" int bem_mesh(bem_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t ne,
+                        const int8_t* bc, const bem_opts* opts) {
+  if (!ctx) return BEM_ERR_INVALID_ARG;
+  if (!xyz || !tri || !bc || nv < 3 || ne < 1 || ne > (1LL << 28))
+    return fail(ctx, BEM_ERR_INVALID_ARG, "bem_mesh: bad sizes or null pointers");
+  for (int64_t e = 0; e < ne; ++e)
+    if (bc[e] != BEM_BC_TRACTION && bc[e] != BEM_BC_DISPLACEMENT)
+      return fail(ctx, BEM_ERR_INVALID_ARG, "bem_mesh: bc_type must be 0 or 1");
+  TRY(set_device(ctx));
+  DevBuf<double> x;
+  DevBuf<int> t;
+  DevBuf<signed char> b;
+  BEM_CUDA_TRY(x.alloc(3 * nv));
+  BEM_CUDA_TRY(t.alloc(3 * ne));
+  BEM_CUDA_TRY(b.alloc(ne));
+  BEM_CUDA_TRY(cudaMemcpyAsync(x.p, xyz, 3 * nv * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  BEM_CUDA_TRY(cudaMemcpyAsync(t.p, tri, 3 * ne * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  BEM_CUDA_TRY(cudaMemcpyAsync(b.p, bc, ne, cudaMemcpyHostToDevice, ctx->stream));
+  int r = mesh_impl(ctx, x.p, nv, t.p, (int)ne, b.p, opts);
+  cudaStreamSynchronize(ctx->stream);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// assembly
+// ---------------------------------------------------------------------------
+namespace {
+
+int ensure_static(bem_ctx* ctx) {
+  if (ctx->sing_static.p || ctx->nsing == 0) return BEM_OK;
+  BEM_CUDA_TRY(ctx->sing_static.alloc(18LL * ctx->nsing));
+  KParams<double> P = make_params<double>(ctx, 0.0, 0.0);
+  launch_static(ctx->sing.p, ctx->nsing, ctx->ed.p, P, ctx->sing_static.p, ctx->stream);
+  CK("static");
+  return BEM_OK;
+}
+
+int check_ready(bem_ctx* ctx) {
+  if (!ctx->have_mesh) return fail(ctx, BEM_ERR_NO_MESH, "no mesh");
+  if (!ctx->have_mat) return fail(ctx, BEM_ERR_STATE, "material not set");
+  return BEM_OK;
+}
+
+// Operator at s: right-hand side contributions optional (pattern/b may be null).
+int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const double* pattern_tree,
+                  c128 pk, c128* b) {
+  cudaStream_t st = ctx->stream;
+  TRY(ensure_static(ctx));
+  ctx->prec = o.precision;
+  cudaEvent_t ev = prof_begin(ctx);
+  size_t nf = ctx->far_h.size();
+  BEM_CUDA_TRY(ctx->rank.ensure(std::max<size_t>(1, nf)));
+  BEM_CUDA_TRY(ctx->aca_fail.ensure(1));
+  BEM_CUDA_TRY(ctx->prec_inv.ensure(9LL * ctx->ne));
+  BEM_CUDA_TRY(cudaMemsetAsync(ctx->aca_fail.p, 0, sizeof(int), st));
+  KParams<double> Pd = make_params<double>(ctx, sre, sim);
+  BEM_CUDA_TRY(ctx->status.ensure(1));
+  DevBuf<int>& status = ctx->status;
+  if (b) {
+    if (is_mixed(ctx)) {
+      KParams<float> Pf = make_params<float>(ctx, sre, sim);
+      launch_rhs<float>(ctx->ne, ctx->loaded.p, ctx->nloaded, ctx->ef.p, ctx->ed.p, ctx->bc.p, pattern_tree, Pf,
+                        pk, b, st);
+    } else {
+      launch_rhs<double>(ctx->ne, ctx->loaded.p, ctx->nloaded, ctx->ef.p, ctx->ed.p, ctx->bc.p, pattern_tree, Pd,
+                         pk, b, st);
+    }
+    CK("rhs");
+  }
+  if (is_mixed(ctx)) {
+    BEM_CUDA_TRY(ctx->near32.ensure(std::max<long long>(1, ctx->near_entries)));
+    BEM_CUDA_TRY(ctx->u32.ensure(std::max<long long>(1, ctx->u_entries)));
+    BEM_CUDA_TRY(ctx->v32.ensure(std::max<long long>(1, ctx->v_entries)));
+    BEM_CUDA_TRY(ctx->t32.ensure(4LL * std::max(1, ctx->t_entries)));
+    BEM_CUDA_TRY(ctx->t64.ensure(4LL * std::max(1, ctx->t_entries)));
+    BEM_CUDA_TRY(ctx->prec_inv32.ensure(9LL * ctx->ne));
+    launch_sing<c64>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->bc.p, ctx->sing_static.p, Pd, ctx->near32.p,
+                     ctx->prec_inv.p, pattern_tree, pk, b, status.p, st);
+    CK("sing");
+    KParams<float> Pf = make_params<float>(ctx, sre, sim);
+    launch_near_regular<float, c64>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf,
+                                    ctx->near32.p, st);
+    CK("near_regular");
+    launch_aca<float, c64>(ctx->far_d.p, (int)nf, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, ctx->u32.p, ctx->v32.p,
+                           ctx->rank.p, ctx->aca_fail.p, o.aca_tol, st);
+    CK("aca");
+    long long n9 = 9LL * ctx->ne;
+    count_if(true);
+    k_pinv_cast<<<(unsigned)((n9 + 255) / 256), 256, 0, st>>>(ctx->prec_inv.p, ctx->prec_inv32.p, n9);
+    CK("pinv_cast");
+  } else {
+    BEM_CUDA_TRY(ctx->near64.ensure(std::max<long long>(1, ctx->near_entries)));
+    BEM_CUDA_TRY(ctx->u64.ensure(std::max<long long>(1, ctx->u_entries)));
+    BEM_CUDA_TRY(ctx->v64.ensure(std::max<long long>(1, ctx->v_entries)));
+    BEM_CUDA_TRY(ctx->t64.ensure(4LL * std::max(1, ctx->t_entries)));
+    launch_sing<c128>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->bc.p, ctx->sing_static.p, Pd, ctx->near64.p,
+                      ctx->prec_inv.p, pattern_tree, pk, b, status.p, st);
+    CK("sing");
+    launch_near_regular<double, c128>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd,
+                                      ctx->near64.p, st);
+    CK("near_regular");
+    launch_aca<double, c128>(ctx->far_d.p, (int)nf, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd, ctx->u64.p, ctx->v64.p,
+                             ctx->rank.p, ctx->aca_fail.p, o.aca_tol, st);
+    CK("aca");
+  }
+  prof_end(ctx, ev, 1, 0.0);
+  ctx->assembled = true;
+  ctx->s_re = sre;
+  ctx->s_im = sim;
+  if (ctx->profiling) {
+    std::vector<int> rk(nf);
+    if (nf) BEM_CUDA_TRY(cudaMemcpyAsync(rk.data(), ctx->rank.p, nf * sizeof(int), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA_TRY(cudaStreamSynchronize(st));
+    long long u = 0;
+    for (size_t b = 0; b < nf; ++b) u += (long long)rk[b] * 3 * (ctx->far_h[b].nr + ctx->far_h[b].nc);
+    ctx->used_lowrank = u;
+    prof_harvest(ctx);
+  }
+  return BEM_OK;
+}
+
+// y = A x with FP64 accumulation (x, y c128, nrhs vectors)
+int apply64(bem_ctx* ctx, const c128* x, c128* y, int nrhs) {
+  cudaEvent_t ev = prof_begin(ctx);
+  if (is_mixed(ctx))
+    launch_hmatvec<c64, c128, c128, double>(ctx, ctx->near32.p, ctx->u32.p, ctx->v32.p,
+                                            reinterpret_cast<cplx<double>*>(ctx->t64.p), x, y, nrhs, ctx->stream);
+  else
+    launch_hmatvec<c128, c128, c128, double>(ctx, ctx->near64.p, ctx->u64.p, ctx->v64.p,
+                                             reinterpret_cast<cplx<double>*>(ctx->t64.p), x, y, nrhs, ctx->stream);
+  CK("hmatvec64");
+  prof_end(ctx, ev, 0, hmv_bytes(ctx, is_mixed(ctx) ? 8 : 16, 16, 16, nrhs, ctx->used_lowrank));
+  return BEM_OK;
+}
+
+int prepare_loaded(bem_ctx* ctx, const double* pattern_tree) {
+  BEM_CUDA_TRY(ctx->loaded.ensure(ctx->ne + 1));
+  count_if(true);
+  k_loaded<<<1, 1024, 0, ctx->stream>>>(pattern_tree, ctx->ne, ctx->loaded.p, ctx->loaded.p + ctx->ne);
+  CK("loaded");
+  BEM_CUDA_TRY(cudaMemcpyAsync(&ctx->nloaded, ctx->loaded.p + ctx->ne, sizeof(int), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return BEM_OK;
+}
+
+// pattern in caller order on device -> ctx->pattern in tree order + loaded list
+int set_pattern_dev(bem_ctx* ctx, const double* pat_dev) {
+  BEM_CUDA_TRY(ctx->pattern.ensure(3LL * ctx->ne));
+  count_if(true);
+  k_permute_pattern<<<(ctx->ne + 127) / 128, 128, 0, ctx->stream>>>(pat_dev, ctx->perm.p, ctx->ne, ctx->pattern.p);
+  CK("permute_pattern");
+  return prepare_loaded(ctx, ctx->pattern.p);
+}
+
+int set_pattern_host(bem_ctx* ctx, const double* pat) {
+  std::vector<double> pt(3LL * ctx->ne);
+  for (int k = 0; k < ctx->ne; ++k)
+    for (int a = 0; a < 3; ++a) pt[3LL * k + a] = pat[3LL * ctx->tree.perm[k] + a];
+  BEM_CUDA_TRY(ctx->pattern.ensure(3LL * ctx->ne));
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->pattern.p, pt.data(), pt.size() * sizeof(double), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  return prepare_loaded(ctx, ctx->pattern.p);
+}
+
+// host vector (caller order, interleaved complex) <-> device tree order
+void to_tree(const bem_ctx* ctx, const double* in, std::vector<c128>& out) {
+  out.resize(ctx->N);
+  for (int k = 0; k < ctx->ne; ++k) {
+    long long e = ctx->tree.perm[k];
+    for (int a = 0; a < 3; ++a) out[3LL * k + a] = c128{in[2 * (3 * e + a)], in[2 * (3 * e + a) + 1]};
+  }
+}
+void from_tree(const bem_ctx* ctx, const std::vector<c128>& in, double* out) {
+  for (int k = 0; k < ctx->ne; ++k) {
+    long long e = ctx->tree.perm[k];
+    for (int a = 0; a < 3; ++a) {
+      out[2 * (3 * e + a)] = in[3LL * k + a].re;
+      out[2 * (3 * e + a) + 1] = in[3LL * k + a].im;
+    }
+  }
+}
+
+template <typename Vb> DevBuf<Vb>& basis_buf(bem_ctx* ctx);
+template <> DevBuf<c64>& basis_buf<c64>(bem_ctx* ctx) { return ctx->V32; }
+template <> DevBuf<c128>& basis_buf<c128>(bem_ctx* ctx) { return ctx->V64; }
+template <typename Pm> const Pm* basis_pinv(bem_ctx* ctx);
+template <> const c64* basis_pinv<c64>(bem_ctx* ctx) { return ctx->prec_inv32.p; }
+template <> const c128* basis_pinv<c128>(bem_ctx* ctx) { return ctx->prec_inv.p; }
+
+// ---------------------------------------------------------------------------
+// GMRES (Sec. 5): right block-Jacobi preconditioning; each restart cycle
+// starts from the true residual r = b - A x accumulated in FP64 (x in FP64),
+// so restarts double as iterative refinement of the c64 Krylov solve.
+// ---------------------------------------------------------------------------
+template <typename Vb, typename Pm, typename Acc>
+int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq_stats* stats, double bnorm) {
+  cudaStream_t st = ctx->stream;
+  const long long N = ctx->N;
+  const int m = std::max(1, o.restart);
+  constexpr bool mixed = sizeof(Vb) == sizeof(c64);
+  DevBuf<Vb>& Vbuf = basis_buf<Vb>(ctx);
+  BEM_CUDA_TRY(Vbuf.ensure((m + 1) * N));
+  DevBuf<Vb> wbuf, zbuf;
+  BEM_CUDA_TRY(wbuf.alloc(N));
+  BEM_CUDA_TRY(zbuf.alloc(N));
+  BEM_CUDA_TRY(ctx->r64.ensure(N));
+  BEM_CUDA_TRY(ctx->y64.ensure(N));
+  BEM_CUDA_TRY(ctx->tmp64.ensure(2 * N));
+  BEM_CUDA_TRY(ctx->red.ensure(2LL * 64 * (m + 2) * 2 + 8 * (m + 4)));
+  c128* part = reinterpret_cast<c128*>(ctx->red.p);
+  c128* hdev = part + 64LL * (m + 2);  // [h1 (m+1) | h2 (m+1) | nrm2]
+  const Pm* pinv = basis_pinv<Pm>(ctx);
+  Vb* V = Vbuf.p;
+  int its = 0, cycles = 0;
+  double rel = 1.0;
+  bool converged = false;
+  const double inner_floor = mixed ? 2e-6 : 1e-13;
+  std::vector<std::complex<double>> H((m + 1) * m), cs(m), sn(m), g(m + 1);
+  double* hh = ctx->host_red;
+  while (true) {
+    // true residual (FP64)
+    TRY(apply64(ctx, x, ctx->y64.p, 1));
+    launch_residual(b, ctx->y64.p, ctx->r64.p, N, st);
+    CK("residual");
+    std::complex<double> rr;
+    TRY(dot_host(ctx, ctx->r64.p, ctx->r64.p, N, rr));
+    double rnorm = std::sqrt(std::max(0.0, rr.real()));
+    rel = bnorm > 0 ? rnorm / bnorm : 0.0;
+    if (cycles == 0 && stats) stats->guess_residual = rel;
+    if (rel <= o.tol || rnorm == 0.0) {
+      converged = true;
+      break;
+    }
+    if (its >= o.max_iters) break;
+    // V_0 = r / ||r||
+    if (mixed)
+      launch_copy_cast(ctx->r64.p, reinterpret_cast<c64*>(V), N, 1.0 / rnorm, st);
+    else
+      launch_copy_cast(ctx->r64.p, reinterpret_cast<c128*>(V), N, 1.0 / rnorm, st);
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = rnorm;
+    double target = std::max(0.5 * o.tol * bnorm, inner_floor * rnorm);
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      Vb* vj = V + (long long)j * N;
+      launch_precond<Pm, Vb, Vb>(pinv, vj, zbuf.p, ctx->ne, st);
+      cudaEvent_t ev = prof_begin(ctx);
+      if (mixed)
+        launch_hmatvec<c64, c64, c64, float>(ctx, ctx->near32.p, ctx->u32.p, ctx->v32.p,
+                                             reinterpret_cast<cplx<float>*>(ctx->t32.p),
+                                             reinterpret_cast<const c64*>(zbuf.p), reinterpret_cast<c64*>(wbuf.p), 1,
+                                             st);
+      else
+        launch_hmatvec<c128, c128, c128, double>(ctx, ctx->near64.p, ctx->u64.p, ctx->v64.p,
+                                                 reinterpret_cast<cplx<double>*>(ctx->t64.p),
+                                                 reinterpret_cast<const c128*>(zbuf.p),
+                                                 reinterpret_cast<c128*>(wbuf.p), 1, st);
+      CK("arnoldi matvec");
+      prof_end(ctx, ev, 0, hmv_bytes(ctx, sizeof(Vb), sizeof(Vb), sizeof(Vb), 1, ctx->used_lowrank));
+      for (int pass = 0; pass < 2; ++pass) {
+        int nb = launch_dots<Vb, Vb>(V, N, j + 1, wbuf.p, N, part, st);
+        launch_dots_final(part, nb, j + 1, hdev + pass * (m + 1), st);
+        launch_update<Vb, Vb>(V, N, j + 1, hdev + pass * (m + 1), wbuf.p, N, st);
+      }
+      int nb = launch_dots<Vb, Vb>(wbuf.p, N, 1, wbuf.p, N, part, st);
+      launch_dots_final(part, nb, 1, hdev + 2 * (m + 1), st);
+      launch_scale<Vb, Vb>(wbuf.p, V + (long long)(j + 1) * N, N, reinterpret_cast<const double*>(hdev + 2 * (m + 1)),
+                           st);
+      CK("arnoldi");
+      BEM_CUDA_TRY(cudaMemcpyAsync(hh, hdev, (2 * (m + 1) + 1) * sizeof(c128), cudaMemcpyDeviceToHost, st));
+      BEM_CUDA_TRY(cudaStreamSynchronize(st));
+      prof_harvest(ctx);
+      for (int i = 0; i <= j; ++i)
+        H[i * m + j] = std::complex<double>(hh[2 * i] + hh[2 * (m + 1 + i)], hh[2 * i + 1] + hh[2 * (m + 1 + i) + 1]);
+      double hn = std::sqrt(std::max(0.0, hh[4 * (m + 1)]));
+      H[(j + 1) * m + j] = hn;
+      // Givens (G = [[conj c, conj s], [-s, c]])
+      for (int i = 0; i < j; ++i) {
+        std::complex<double> a = H[i * m + j], c2 = H[(i + 1) * m + j];
+        H[i * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * c2;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c2;
+      }
+      std::complex<double> a = H[j * m + j], c2 = H[(j + 1) * m + j];
+      double den = std::sqrt(std::norm(a) + std::norm(c2));
+      cs[j] = den > 0 ? a / den : 1.0;
+      sn[j] = den > 0 ? c2 / den : 0.0;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = std::conj(cs[j]) * g[j];
+      ++its;
+      jdone = j + 1;
+      if (std::abs(g[j + 1]) <= target || its >= o.max_iters || hn == 0.0) break;
+    }
+    // y = H^{-1} g ; x += M^{-1} V y
+    std::vector<std::complex<double>> y(jdone);
+    for (int i = jdone - 1; i >= 0; --i) {
+      std::complex<double> s = g[i];
+      for (int k2 = i + 1; k2 < jdone; ++k2) s -= H[i * m + k2] * y[k2];
+      y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
+    }
+    for (int i = 0; i < jdone; ++i) {
+      hh[2 * i] = y[i].real();
+      hh[2 * i + 1] = y[i].imag();
+    }
+    BEM_CUDA_TRY(cudaMemcpyAsync(hdev, hh, jdone * sizeof(c128), cudaMemcpyHostToDevice, st));
+    launch_combine<Vb>(V, N, jdone, hdev, ctx->tmp64.p, N, st);
+    launch_precond<c128, c128, c128>(ctx->prec_inv.p, ctx->tmp64.p, ctx->tmp64.p + N, ctx->ne, st);
+    launch_axpy(c128{1.0, 0.0}, ctx->tmp64.p + N, x, N, st);
+    CK("update x");
+    BEM_CUDA_TRY(cudaStreamSynchronize(st));  // hh reused next cycle
+    prof_harvest(ctx);
+    ++cycles;
+  }
+  if (stats) {
+    stats->iters = its;
+    stats->cycles = cycles;
+    stats->rel_residual = rel;
+    stats->converged = converged ? 1 : 0;
+  }
+  return converged ? BEM_OK : BEM_ERR_NOT_CONVERGED;
+}
+
+int gmres(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq_stats* st) {
+  std::complex<double> bb;
+  TRY(dot_host(ctx, b, b, ctx->N, bb));
+  double bnorm = std::sqrt(std::max(0.0, bb.real()));
+  if (bnorm == 0.0) {
+    BEM_CUDA_TRY(cudaMemsetAsync(x, 0, ctx->N * sizeof(c128), ctx->stream));
+    if (st) {
+      st->iters = 0;
+      st->cycles = 0;
+      st->rel_residual = 0;
+      st->converged = 1;
+      st->guess_residual = 0;
+    }
+    return BEM_OK;
+  }
+  if (is_mixed(ctx)) return gmres_impl<c64, c64, float>(ctx, b, x, o, st, bnorm);
+  return gmres_impl<c128, c128, double>(ctx, b, x, o, st, bnorm);
+}
+
+// ---------------------------------------------------------------------------
+// solution extrapolation (Sec. 4.2): a0 = X R^{-1} Q^H b, A X = Q R (CGS2, FP64)
+// X: K vectors (device, stride N), in the order a_{k-1}, a_{k-2}, ...
+// ---------------------------------------------------------------------------
+int sem_impl(bem_ctx* ctx, const c128* const* X, int K, const c128* b, c128* a0) {
+  cudaStream_t st = ctx->stream;
+  const long long N = ctx->N;
+  BEM_CUDA_TRY(cudaMemsetAsync(a0, 0, N * sizeof(c128), st));
+  if (K <= 0) return BEM_OK;
+  DevBuf<c128> Xc, Y, Q;
+  BEM_CUDA_TRY(Xc.alloc(K * N));
+  BEM_CUDA_TRY(Y.alloc(K * N));
+  BEM_CUDA_TRY(Q.alloc(K * N));
+  for (int q = 0; q < K; ++q)
+    BEM_CUDA_TRY(cudaMemcpyAsync(Xc.p + q * N, X[q], N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
+  TRY(apply64(ctx, Xc.p, Y.p, K));
+  BEM_CUDA_TRY(ctx->red.ensure(2LL * 64 * 8 * 2 + 64));
+  c128* part = reinterpret_cast<c128*>(ctx->red.p);
+  c128* hdev = part + 64 * 8;
+  std::vector<std::complex<double>> R(K * K, 0.0);
+  std::vector<int> keep;
+  double r00 = 0;
+  for (int c = 0; c < K; ++c) {
+    c128* qc = Q.p + (long long)keep.size() * N;
+    BEM_CUDA_TRY(cudaMemcpyAsync(qc, Y.p + c * N, N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
+    std::vector<std::complex<double>> col(keep.size(), 0.0);
+    for (int pass = 0; pass < 2 && !keep.empty(); ++pass) {
+      int nb = launch_dots<c128, c128>(Q.p, N, (int)keep.size(), qc, N, part, st);
+      launch_dots_final(part, nb, (int)keep.size(), hdev, st);
+      launch_update<c128, c128>(Q.p, N, (int)keep.size(), hdev, qc, N, st);
+      CK("sem qr");
+      std::vector<c128> h(keep.size());
+      BEM_CUDA_TRY(cudaMemcpyAsync(h.data(), hdev, keep.size() * sizeof(c128), cudaMemcpyDeviceToHost, st));
+      BEM_CUDA_TRY(cudaStreamSynchronize(st));
+      for (size_t i = 0; i < keep.size(); ++i) col[i] += std::complex<double>(h[i].re, h[i].im);
+    }
+    std::complex<double> nn;
+    TRY(dot_host(ctx, qc, qc, N, nn));
+    double nrm = std::sqrt(std::max(0.0, nn.real()));
+    if (keep.empty()) r00 = nrm;
+    if (!(nrm > 1e-12 * r00) || nrm == 0.0) continue;  // numerically dependent column: drop
+    launch_copy_cast(qc, qc, N, 1.0 / nrm, st);
+    int kk = (int)keep.size();
+    for (int i = 0; i < kk; ++i) R[i * K + kk] = col[i];
+    R[kk * K + kk] = nrm;
+    keep.push_back(c);
+  }
+  int kk = (int)keep.size();
+  if (kk == 0) return BEM_OK;
+  int nb = launch_dots<c128, c128>(Q.p, N, kk, b, N, part, st);
+  launch_dots_final(part, nb, kk, hdev, st);
+  CK("sem qhb");
+  std::vector<c128> qb(kk);
+  BEM_CUDA_TRY(cudaMemcpyAsync(qb.data(), hdev, kk * sizeof(c128), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<std::complex<double>> s(kk);
+  for (int i = kk - 1; i >= 0; --i) {
+    std::complex<double> v(qb[i].re, qb[i].im);
+    for (int j = i + 1; j < kk; ++j) v -= R[i * K + j] * s[j];
+    s[i] = v / R[i * K + i];
+  }
+  for (int i = 0; i < kk; ++i) launch_axpy(c128{s[i].real(), s[i].imag()}, X[keep[i]], a0, N, st);
+  CK("sem combine");
+  return BEM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// step-level entry points
+// ---------------------------------------------------------------------------
+extern "C" int bem_assemble(bem_ctx* ctx, double s_re, double s_im, const bem_opts* opts) {
+  if (!ctx) return BEM_ERR_INVALID_ARG;
+  TRY(check_ready(ctx));
+  TRY(set_device(ctx));
+  bem_opts o = ctx->mesh_opts;
+  if (opts) o = *opts;
+  if (!(s_re >= 0) || !std::isfinite(s_im)) return fail(ctx, BEM_ERR_INVALID_ARG, "need Re(s) >= 0");
+  TRY(assemble_impl(ctx, s_re, s_im, o, nullptr, c128{0, 0}, nullptr));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return BEM_OK;
+}
+
+extern "C" int bem_operator_rows(bem_ctx* ctx, const int64_t* rows, int64_t nrows, double* out) {
+  if (!ctx || (!rows && nrows) || (!out && nrows) || nrows < 0) return BEM_ERR_INVALID_ARG;
+  if (!ctx->assembled) return fail(ctx, BEM_ERR_STATE, "operator not assembled");
+  TRY(set_device(ctx));
+  const long long N = ctx->N;
+  for (int64_t r = 0; r < nrows; ++r)
+    if (rows[r] < 0 || rows[r] >= N) return fail(ctx, BEM_ERR_INVALID_ARG, "row index out of range");
+  // download operator storage and reconstruct rows on the host
+  std::vector<c128> nearv(ctx->near_entries), Uv(ctx->u_entries), Vv(ctx->v_entries);
+  std::vector<int> rk(ctx->far_h.size());
+  cudaStream_t st = ctx->stream;
+  if (is_mixed(ctx)) {
+    std::vector<c64> a(ctx->near_entries), u(ctx->u_entries), v(ctx->v_entries);
+    if (!a.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(a.data(), ctx->near32.p, a.size() * sizeof(c64), cudaMemcpyDeviceToHost, st));
+    if (!u.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(u.data(), ctx->u32.p, u.size() * sizeof(c64), cudaMemcpyDeviceToHost, st));
+    if (!v.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(v.data(), ctx->v32.p, v.size() * sizeof(c64), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < a.size(); ++i) nearv[i] = c128{a[i].re, a[i].im};
+    for (size_t i = 0; i < u.size(); ++i) Uv[i] = c128{u[i].re, u[i].im};
+    for (size_t i = 0; i < v.size(); ++i) Vv[i] = c128{v[i].re, v[i].im};
+  } else {
+    if (!nearv.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(nearv.data(), ctx->near64.p, nearv.size() * sizeof(c128), cudaMemcpyDeviceToHost, st));
+    if (!Uv.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(Uv.data(), ctx->u64.p, Uv.size() * sizeof(c128), cudaMemcpyDeviceToHost, st));
+    if (!Vv.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(Vv.data(), ctx->v64.p, Vv.size() * sizeof(c128), cudaMemcpyDeviceToHost, st));
+  }
+  if (!rk.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(rk.data(), ctx->rank.p, rk.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  const auto& perm = ctx->tree.perm;
+  const auto& ip = ctx->tree.iperm;
+  for (int64_t q = 0; q < nrows; ++q) {
+    long long rc = rows[q];            // caller dof
+    int ec = (int)(rc / 3), a = (int)(rc % 3);
+    int et = ip[ec];                   // tree element
+    long long rt = 3LL * et + a;       // tree row
+    std::vector<c128> rowt(N, c128{0, 0});
+    for (const NearBlk& nb : ctx->near_h) {
+      if (et < nb.r0 || et >= nb.r0 + nb.nr) continue;
+      long long ld = 3LL * nb.nr, lr = rt - 3LL * nb.r0;
+      for (int c = 0; c < 3 * nb.nc; ++c) rowt[3LL * nb.c0 + c] = nearv[nb.off + c * ld + lr];
+    }
+    for (size_t b = 0; b < ctx->far_h.size(); ++b) {
+      const FarBlk& fb = ctx->far_h[b];
+      if (et < fb.r0 || et >= fb.r0 + fb.nr) continue;
+      long long m = 3LL * fb.nr, n = 3LL * fb.nc, lr = rt - 3LL * fb.r0;
+      for (long long c = 0; c < n; ++c) {
+        std::complex<double> s = 0;
+        for (int l = 0; l < rk[b]; ++l) {
+          c128 u = Uv[fb.uoff + l * m + lr], v = Vv[fb.voff + l * n + c];
+          s += std::complex<double>(u.re, u.im) * std::complex<double>(v.re, v.im);
+        }
+        rowt[3LL * fb.c0 + c] = c128{s.real(), s.imag()};
+      }
+    }
+    double* o = out + 2 * q * N;
+    for (int k = 0; k < ctx->ne; ++k)
+      for (int c = 0; c < 3; ++c) {
+        long long dc = 3LL * perm[k] + c;
+        o[2 * dc] = rowt[3LL * k + c].re;
+        o[2 * dc + 1] = rowt[3LL * k + c].im;
+      }
+  }
+  return BEM_OK;
+}
+
+extern "C" int bem_apply(bem_ctx* ctx, const double* x, double* y) {
+  if (!ctx || !x || !y) return BEM_ERR_INVALID_ARG;
+  if (!ctx->assembled) return fail(ctx, BEM_ERR_STATE, "operator not assembled");
+  TRY(set_device(ctx));
+  std::vector<c128> xt;
+  to_tree(ctx, x, xt);
+  DevBuf<c128> xd, yd;
+  BEM_CUDA_TRY(xd.alloc(ctx->N));
+  BEM_CUDA_TRY(yd.alloc(ctx->N));
+  BEM_CUDA_TRY(cudaMemcpyAsync(xd.p, xt.data(), ctx->N * sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+  TRY(apply64(ctx, xd.p, yd.p, 1));
+  BEM_CUDA_TRY(cudaMemcpyAsync(xt.data(), yd.p, ctx->N * sizeof(c128), cudaMemcpyDeviceToHost, ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  from_tree(ctx, xt, y);
+  return BEM_OK;
+}
+
+extern "C" int bem_rhs(bem_ctx* ctx, double p_re, double p_im, const double* pattern, double* b) {
+  if (!ctx || !pattern || !b) return BEM_ERR_INVALID_ARG;
+  if (!ctx->assembled) return fail(ctx, BEM_ERR_STATE, "operator not assembled");
+  TRY(set_device(ctx));
+  TRY(set_pattern_host(ctx, pattern));
+  DevBuf<c128> bd;
+  BEM_CUDA_TRY(bd.alloc(ctx->N));
+  c128 pk{p_re, p_im};
+  KParams<double> Pd = make_params<double>(ctx, ctx->s_re, ctx->s_im);
+  if (is_mixed(ctx)) {
+    KParams<float> Pf = make_params<float>(ctx, ctx->s_re, ctx->s_im);
+    launch_rhs<float>(ctx->ne, ctx->loaded.p, ctx->nloaded, ctx->ef.p, ctx->ed.p, ctx->bc.p, ctx->pattern.p, Pf, pk,
+                      bd.p, ctx->stream);
+    launch_sing<c64>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->bc.p, ctx->sing_static.p, Pd, nullptr, nullptr,
+                     ctx->pattern.p, pk, bd.p, ctx->status.p, ctx->stream);
+  } else {
+    launch_rhs<double>(ctx->ne, ctx->loaded.p, ctx->nloaded, ctx->ef.p, ctx->ed.p, ctx->bc.p, ctx->pattern.p, Pd, pk,
+                       bd.p, ctx->stream);
+    launch_sing<c128>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->bc.p, ctx->sing_static.p, Pd, nullptr, nullptr,
+                      ctx->pattern.p, pk, bd.p, ctx->status.p, ctx->stream);
+  }
+  CK("rhs");
+  std::vector<c128> bt(ctx->N);
+  BEM_CUDA_TRY(cudaMemcpyAsync(bt.data(), bd.p, ctx->N * sizeof(c128), cudaMemcpyDeviceToHost, ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  from_tree(ctx, bt, b);
+  return BEM_OK;
+}
+
+extern "C" int bem_solve_assembled(bem_ctx* ctx, const double* b, const double* x0, double* x, const bem_opts* opts,
+                                   bem_freq_stats* stats) {
+  if (!ctx || !b || !x) return BEM_ERR_INVALID_ARG;
+  if (!ctx->assembled) return fail(ctx, BEM_ERR_STATE, "operator not assembled");
+  TRY(set_device(ctx));
+  bem_opts o = ctx->mesh_opts;
+  if (opts) o = *opts;
+  if (!(o.tol > 0) || o.restart < 1 || o.max_iters < 0) return fail(ctx, BEM_ERR_INVALID_ARG, "bad solver options");
+  if (o.precision != ctx->prec) return fail(ctx, BEM_ERR_STATE, "precision differs from the assembled operator");
+  std::vector<c128> bt, xt;
+  to_tree(ctx, b, bt);
+  if (x0) to_tree(ctx, x0, xt);
+  else xt.assign(ctx->N, c128{0, 0});
+  BEM_CUDA_TRY(ctx->b64.ensure(ctx->N));
+  BEM_CUDA_TRY(ctx->x64.ensure(ctx->N));
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->b64.p, bt.data(), ctx->N * sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->x64.p, xt.data(), ctx->N * sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+  bem_freq_stats s{};
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = gmres(ctx, ctx->b64.p, ctx->x64.p, o, &s);
+  if (rc != BEM_OK && rc != BEM_ERR_NOT_CONVERGED) return rc;
+  BEM_CUDA_TRY(cudaMemcpyAsync(xt.data(), ctx->x64.p, ctx->N * sizeof(c128), cudaMemcpyDeviceToHost, ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  s.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  s.s_re = ctx->s_re;
+  s.s_im = ctx->s_im;
+  from_tree(ctx, xt, x);
+  if (stats) *stats = s;
+  if (rc == BEM_ERR_NOT_CONVERGED) fail(ctx, rc, "GMRES did not reach the tolerance");
+  return rc;
+}
+
+extern "C" int bem_sem_guess(bem_ctx* ctx, int32_t K, const double* X, const double* b, double* a0) {
+  if (!ctx || !b || !a0 || K < 0 || (K > 0 && !X)) return BEM_ERR_INVALID_ARG;
+  if (!ctx->assembled) return fail(ctx, BEM_ERR_STATE, "operator not assembled");
+  if (K > 4) return fail(ctx, BEM_ERR_INVALID_ARG, "K must be <= 4");
+  TRY(set_device(ctx));
+  const long long N = ctx->N;
+  DevBuf<c128> Xd, bd, ad;
+  BEM_CUDA_TRY(Xd.alloc(std::max<long long>(1, K * N)));
+  BEM_CUDA_TRY(bd.alloc(N));
+  BEM_CUDA_TRY(ad.alloc(N));
+  std::vector<c128> t;
+  std::vector<const c128*> ptrs;
+  for (int q = 0; q < K; ++q) {
+    to_tree(ctx, X + 2 * q * N, t);
+    BEM_CUDA_TRY(cudaMemcpyAsync(Xd.p + q * N, t.data(), N * sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+    BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    ptrs.push_back(Xd.p + q * N);
+  }
+  to_tree(ctx, b, t);
+  BEM_CUDA_TRY(cudaMemcpyAsync(bd.p, t.data(), N * sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+  TRY(sem_impl(ctx, ptrs.data(), K, bd.p, ad.p));
+  BEM_CUDA_TRY(cudaMemcpyAsync(t.data(), ad.p, N * sizeof(c128), cudaMemcpyDeviceToHost, ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  from_tree(ctx, t, a0);
+  return BEM_OK;
+}
+
+extern "C" int bem_load_dft(bem_ctx* ctx, double T, int32_t n_omega, double eta, const double* load_hist, double* out) {
+  if (!ctx || !load_hist || !out || n_omega < 2 || (n_omega & 1) || !(T > 0) || !(eta >= 0))
+    return BEM_ERR_INVALID_ARG;
+  TRY(set_device(ctx));
+  int nf = n_omega / 2 + 1;
+  DevBuf<double> P;
+  DevBuf<c128> o;
+  BEM_CUDA_TRY(P.alloc(n_omega));
+  BEM_CUDA_TRY(o.alloc(nf));
+  BEM_CUDA_TRY(cudaMemcpyAsync(P.p, load_hist, n_omega * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  launch_load_dft(P.p, n_omega, T, eta, o.p, ctx->stream);
+  CK("load_dft");
+  BEM_CUDA_TRY(cudaMemcpyAsync(out, o.p, nf * sizeof(c128), cudaMemcpyDeviceToHost, ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return BEM_OK;
+}
+
+static int idft_checks(bem_ctx* ctx, int n_omega) {
+  if (n_omega < 2 || (n_omega & 1) || n_omega > 6000)
+    return fail(ctx, BEM_ERR_INVALID_ARG, "n_omega must be even, 2..6000");
+  return BEM_OK;
+}
+
+extern "C" int bem_idft(bem_ctx* ctx, double T, int32_t n_omega, double eta, int window, const double* Rk,
+                        int64_t ndof, double* out) {
+  if (!ctx || !Rk || !out || ndof < 0 || !(T > 0) || !(eta >= 0)) return BEM_ERR_INVALID_ARG;
+  if (window < 0 || window > 2) return fail(ctx, BEM_ERR_INVALID_ARG, "unknown window");
+  TRY(idft_checks(ctx, n_omega));
+  TRY(set_device(ctx));
+  if (ndof == 0) return BEM_OK;
+  int nf = n_omega / 2 + 1;
+  DevBuf<c128> s;
+  DevBuf<double> o;
+  BEM_CUDA_TRY(s.alloc(nf * ndof));
+  BEM_CUDA_TRY(o.alloc(n_omega * ndof));
+  BEM_CUDA_TRY(cudaMemcpyAsync(s.p, Rk, nf * ndof * sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+  launch_idft(s.p, ndof, nullptr, ndof, n_omega, T, eta, window, o.p, ctx->stream);
+  CK("idft");
+  BEM_CUDA_TRY(cudaMemcpyAsync(out, o.p, n_omega * ndof * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the sweep
+// ---------------------------------------------------------------------------
+static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_dev, const bem_opts& o,
+                      bem_freq_stats* stats) {
+  cudaStream_t st = ctx->stream;
+  const long long N = ctx->N;
+  int nf = n_omega / 2 + 1;
+  ctx->T = T;
+  ctx->n_omega = n_omega;
+  ctx->nf = 0;
+  BEM_CUDA_TRY(ctx->Pk.ensure(nf));
+  launch_load_dft(load_dev, n_omega, T, ctx->eta, ctx->Pk.p, st);
+  CK("load_dft");
+  ctx->Pk_host.resize(nf);
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->Pk_host.data(), ctx->Pk.p, nf * sizeof(c128), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(ctx->sol.ensure((long long)nf * N));
+  BEM_CUDA_TRY(ctx->b64.ensure(N));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  const double dw = 2.0 * M_PI / T;
+  int worst = BEM_OK;
+  Timer t0, t1, t2;
+  for (int k = 0; k < nf; ++k) {
+    bem_freq_stats s{};
+    s.k = k;
+    s.s_re = ctx->eta;
+    s.s_im = k * dw;
+    c128* xk = ctx->sol.p + (long long)k * N;
+    cudaEventRecord(t0.a, st);
+    TRY(assemble_impl(ctx, s.s_re, s.s_im, o, ctx->pattern.p, ctx->Pk_host[k], ctx->b64.p));
+    cudaEventRecord(t0.b, st);
+    cudaEventRecord(t1.a, st);
+    int K = (o.guess == BEM_GUESS_SEM) ? std::min(k, std::max(0, std::min(o.sem_k, 4))) : 0;
+    if (K > 0) {
+      std::vector<const c128*> X;
+      for (int q = 1; q <= K; ++q) X.push_back(ctx->sol.p + (long long)(k - q) * N);
+      TRY(sem_impl(ctx, X.data(), K, ctx->b64.p, xk));
+    } else {
+      BEM_CUDA_TRY(cudaMemsetAsync(xk, 0, N * sizeof(c128), st));
+    }
+    cudaEventRecord(t1.b, st);
+    cudaEventRecord(t2.a, st);
+    int rc = gmres(ctx, ctx->b64.p, xk, o, &s);
+    cudaEventRecord(t2.b, st);
+    if (rc != BEM_OK && rc != BEM_ERR_NOT_CONVERGED) return rc;
+    if (rc == BEM_ERR_NOT_CONVERGED) worst = rc;
+    int fails = 0;
+    BEM_CUDA_TRY(cudaMemcpyAsync(&fails, ctx->aca_fail.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA_TRY(cudaStreamSynchronize(st));
+    float ms;
+    cudaEventElapsedTime(&ms, t0.a, t0.b);
+    s.assemble_ms = ms;
+    cudaEventElapsedTime(&ms, t1.a, t1.b);
+    s.guess_ms = ms;
+    cudaEventElapsedTime(&ms, t2.a, t2.b);
+    s.solve_ms = ms;
+    s.aca_failures = fails;
+    s.near_bytes = ctx->near_entries * (is_mixed(ctx) ? 8 : 16);
+    if (stats) stats[k] = s;
+    ctx->nf = k + 1;
+  }
+  if (stats && !ctx->far_h.empty()) {
+    std::vector<int> rk(ctx->far_h.size());
+    BEM_CUDA_TRY(cudaMemcpy(rk.data(), ctx->rank.p, rk.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    long long fb = 0;
+    int mr = 0;
+    for (size_t b = 0; b < rk.size(); ++b) {
+      fb += (long long)rk[b] * 3 * (ctx->far_h[b].nr + ctx->far_h[b].nc);
+      mr = std::max(mr, rk[b]);
+    }
+    stats[nf - 1].far_bytes = fb * (is_mixed(ctx) ? 8 : 16);
+    stats[nf - 1].max_rank = mr;
+  }
+  if (worst != BEM_OK) fail(ctx, worst, "at least one frequency did not reach the tolerance");
+  return worst;
+}
+
+static int sweep_checks(bem_ctx* ctx, double T, int32_t n_omega, const bem_opts& o) {
+  TRY(check_ready(ctx));
+  if (!(T > 0) || n_omega < 2 || (n_omega & 1) || n_omega > 6000)
+    return fail(ctx, BEM_ERR_INVALID_ARG, "need T > 0 and even n_omega in 2..6000");
+  if (!(o.tol > 0) || o.restart < 1 || o.max_iters < 0 || !(o.aca_tol > 0))
+    return fail(ctx, BEM_ERR_INVALID_ARG, "bad solver options");
+  if (o.precision != BEM_PREC_C64_MIXED && o.precision != BEM_PREC_C128)
+    return fail(ctx, BEM_ERR_INVALID_ARG, "unknown precision");
+  return BEM_OK;
+}
+
+extern "C" int bem_solve_sweep(bem_ctx* ctx, double T, int32_t n_omega, const double* load_hist,
+                               const double* bc_pattern, const bem_opts* opts, bem_freq_stats* stats) {
+  if (!ctx || !load_hist || !bc_pattern) return BEM_ERR_INVALID_ARG;
+  bem_opts o = ctx->mesh_opts;
+  if (opts) o = *opts;
+  TRY(sweep_checks(ctx, T, n_omega, o));
+  TRY(set_device(ctx));
+  TRY(set_pattern_host(ctx, bc_pattern));
+  DevBuf<double> P;
+  BEM_CUDA_TRY(P.alloc(n_omega));
+  BEM_CUDA_TRY(cudaMemcpyAsync(P.p, load_hist, n_omega * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  return sweep_impl(ctx, T, n_omega, P.p, o, stats);
+}
+
+extern "C" int bem_solve_sweep_dev(bem_ctx* ctx, double T, int32_t n_omega, const double* load_dev,
+                                   const double* pattern_dev, const bem_opts* opts, bem_freq_stats* stats) {
+  if (!ctx || !load_dev || !pattern_dev) return BEM_ERR_INVALID_ARG;
+  bem_opts o = ctx->mesh_opts;
+  if (opts) o = *opts;
+  TRY(sweep_checks(ctx, T, n_omega, o));
+  TRY(set_device(ctx));
+  TRY(set_pattern_dev(ctx, pattern_dev));
+  return sweep_impl(ctx, T, n_omega, load_dev, o, stats);
+}
+
+extern "C" int bem_get_frequency_solution(bem_ctx* ctx, int32_t k, double* out) {
+  if (!ctx || !out) return BEM_ERR_INVALID_ARG;
+  if (k < 0 || k >= ctx->nf) return fail(ctx, BEM_ERR_INVALID_ARG, "frequency index not solved");
+  TRY(set_device(ctx));
+  std::vector<c128> t(ctx->N);
+  BEM_CUDA_TRY(cudaMemcpyAsync(t.data(), ctx->sol.p + (long long)k * ctx->N, ctx->N * sizeof(c128),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  from_tree(ctx, t, out);
+  return BEM_OK;
+}
+
+static int time_response_impl(bem_ctx* ctx, const long long* idx_dev, long long ndof, double* out_dev) {
+  if (ctx->nf != ctx->n_omega / 2 + 1 || ctx->nf == 0)
+    return fail(ctx, BEM_ERR_STATE, "the sweep has not been solved");
+  TRY(idft_checks(ctx, ctx->n_omega));
+  launch_idft(ctx->sol.p, ctx->N, idx_dev, ndof, ctx->n_omega, ctx->T, ctx->eta, ctx->window, out_dev, ctx->stream);
+  CK("idft");
+  return BEM_OK;
+}
+
+extern "C" int bem_time_response(bem_ctx* ctx, const int64_t* dofs, int64_t ndof, double* out) {
+  if (!ctx || (ndof > 0 && (!dofs || !out)) || ndof < 0) return BEM_ERR_INVALID_ARG;
+  TRY(set_device(ctx));
+  if (ndof == 0) return BEM_OK;
+  std::vector<long long> idx(ndof);
+  for (int64_t d = 0; d < ndof; ++d) {
+    if (dofs[d] < 0 || dofs[d] >= ctx->N) return fail(ctx, BEM_ERR_INVALID_ARG, "dof out of range");
+    long long e = dofs[d] / 3, a = dofs[d] % 3;
+    idx[d] = 3LL * ctx->tree.iperm[e] + a;
+  }
+  DevBuf<long long> id;
+  DevBuf<double> o;
+  BEM_CUDA_TRY(id.alloc(ndof));
+  BEM_CUDA_TRY(o.alloc((long long)ctx->n_omega * ndof));
+  BEM_CUDA_TRY(cudaMemcpyAsync(id.p, idx.data(), ndof * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+  TRY(time_response_impl(ctx, id.p, ndof, o.p));
+  BEM_CUDA_TRY(cudaMemcpyAsync(out, o.p, (long long)ctx->n_omega * ndof * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return BEM_OK;
+}
+
+__global__ void k_map_dofs(const long long* __restrict__ in, const int* __restrict__ iperm, long long n,
+                           long long ndofs, long long* __restrict__ out, int* __restrict__ bad) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long d = in[i];
+  if (d < 0 || d >= ndofs) {
+    atomicExch(bad, 1);
+    out[i] = 0;
+    return;
+  }
+  out[i] = 3LL * iperm[d / 3] + d % 3;
+}
+
+extern "C" int bem_time_response_dev(bem_ctx* ctx, const int64_t* dofs_dev, int64_t ndof, double* out_dev) {
+  if (!ctx || (ndof > 0 && (!dofs_dev || !out_dev)) || ndof < 0) return BEM_ERR_INVALID_ARG;
+  TRY(set_device(ctx));
+  if (ndof == 0) return BEM_OK;
+  if (ctx->nf == 0) return fail(ctx, BEM_ERR_STATE, "the sweep has not been solved");
+  DevBuf<long long> id;
+  DevBuf<int> bad;
+  BEM_CUDA_TRY(id.alloc(ndof));
+  BEM_CUDA_TRY(bad.alloc(1));
+  BEM_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), ctx->stream));
+  count_if(true);
+  k_map_dofs<<<(unsigned)((ndof + 255) / 256), 256, 0, ctx->stream>>>((const long long*)dofs_dev, ctx->iperm.p,
+                                                                      ndof, ctx->N, id.p, bad.p);
+  CK("map_dofs");
+  int bad_h = 0;
+  BEM_CUDA_TRY(cudaMemcpyAsync(&bad_h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (bad_h) return fail(ctx, BEM_ERR_INVALID_ARG, "dof out of range");
+  TRY(time_response_impl(ctx, id.p, ndof, out_dev));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return BEM_OK;
+}
+
+extern "C" int bem_set_profiling(bem_ctx* ctx, int on) {
+  if (!ctx) return BEM_ERR_INVALID_ARG;
+  TRY(set_device(ctx));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  prof_harvest(ctx);
+  ctx->profiling = on != 0;
+  ctx->prof_hmv_launches = ctx->prof_asm_calls = 0;
+  ctx->prof_hmv_ms = ctx->prof_hmv_bytes = ctx->prof_asm_ms = 0;
+  ctx->launches_at_reset = launch_count();
+  return BEM_OK;
+}
+
+extern "C" int bem_get_profile(bem_ctx* ctx, bem_profile* out) {
+  if (!ctx || !out) return BEM_ERR_INVALID_ARG;
+  TRY(set_device(ctx));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  prof_harvest(ctx);
+  out->hmv_launches = ctx->prof_hmv_launches;
+  out->hmv_ms = ctx->prof_hmv_ms;
+  out->hmv_bytes = ctx->prof_hmv_bytes;
+  out->assemble_calls = ctx->prof_asm_calls;
+  out->assemble_ms = ctx->prof_asm_ms;
+  out->kernel_launches = launch_count() - ctx->launches_at_reset;
+  return BEM_OK;
+}

@@ -1,0 +1,875 @@
+// Operator assembly kernels (Sec. 2.1: collocation with constant triangles,
+// Eqs. Uij, Tij, Gikj, Tu_Ut, Aa_b).
+//
+//   k_centroids      element centroids and sizes (caller order)
+//   k_geometry       tree-ordered FP32/FP64 element records
+//   k_sing_count /
+//   k_sing_fill      singular (self) and near-singular pairs of near blocks
+//   k_static         frequency-independent Kelvin parts of those pairs (FP64)
+//   k_near_regular   regular near-field entries (FP32 mixed / FP64 plain)
+//   k_sing           singular + near-singular entries: FP64 remainder plus
+//                    static part, block-Jacobi inverses, their RHS share
+//   k_rhs            b = B(s) pattern over regular pairs, on the fly
+//   k_aca            adaptive cross approximation of admissible blocks
+#include "bem_internal.h"
+#include "bem_kernels.cuh"
+#include "bem_launch.h"
+
+namespace bem {
+
+cudaError_t upload_rules_assemble(const RuleTables& t, cudaStream_t st) {
+  return cudaMemcpyToSymbolAsync(c_rules, &t, sizeof(RuleTables), 0, cudaMemcpyHostToDevice, st);
+}
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+__global__ void k_centroids(const double* __restrict__ xyz, long long nv, const int* __restrict__ tri,
+                            int ne, double* __restrict__ cen, double* __restrict__ h,
+                            int* __restrict__ bad) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  int v[3] = {tri[3 * e], tri[3 * e + 1], tri[3 * e + 2]};
+  for (int k = 0; k < 3; ++k)
+    if (v[k] < 0 || v[k] >= nv) {
+      atomicExch(bad, 1);
+      return;
+    }
+  double p[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) p[k][a] = xyz[3 * (long long)v[k] + a];
+  double e1[3], e2[3], e3[3];
+  for (int a = 0; a < 3; ++a) {
+    e1[a] = p[1][a] - p[0][a];
+    e2[a] = p[2][a] - p[0][a];
+    e3[a] = p[2][a] - p[1][a];
+  }
+  double cx = e1[1] * e2[2] - e1[2] * e2[1];
+  double cy = e1[2] * e2[0] - e1[0] * e2[2];
+  double cz = e1[0] * e2[1] - e1[1] * e2[0];
+  double a2 = sqrt(cx * cx + cy * cy + cz * cz);
+  double l1 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+  double l2 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+  double l3 = e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2];
+  double hm = sqrt(fmax(l1, fmax(l2, l3)));
+  if (!(a2 > 1e-12 * hm * hm) || !(hm > 0)) atomicExch(bad, 2);
+  for (int a = 0; a < 3; ++a) cen[3 * e + a] = (p[0][a] + p[1][a] + p[2][a]) / 3.0;
+  h[e] = hm;
+}
+
+__global__ void k_geometry(const double* __restrict__ xyz, const int* __restrict__ tri,
+                           const int* __restrict__ perm, const signed char* __restrict__ bc_in,
+                           int ne, ElemF* __restrict__ ef, ElemD* __restrict__ ed,
+                           signed char* __restrict__ bc) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ne) return;
+  int e = perm[k];
+  double p[3][3];
+  for (int v = 0; v < 3; ++v)
+    for (int a = 0; a < 3; ++a) p[v][a] = xyz[3 * (long long)tri[3 * e + v] + a];
+  ElemD D;
+  ElemF F;
+  double e1[3], e2[3], e3[3];
+  for (int a = 0; a < 3; ++a) {
+    D.c[a] = (p[0][a] + p[1][a] + p[2][a]) / 3.0;
+    D.p0[a] = p[0][a];
+    D.p1[a] = p[1][a];
+    D.p2[a] = p[2][a];
+    e1[a] = p[1][a] - p[0][a];
+    e2[a] = p[2][a] - p[0][a];
+    e3[a] = p[2][a] - p[1][a];
+  }
+  double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                  e1[0] * e2[1] - e1[1] * e2[0]};
+  double a2 = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+  double l1 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+  double l2 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+  double l3 = e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2];
+  D.area2 = a2;
+  D.h2 = fmax(l1, fmax(l2, l3));
+  for (int a = 0; a < 3; ++a) {
+    D.n[a] = cr[a] / a2;
+    float hi = (float)D.c[a];
+    F.c_hi[a] = hi;
+    F.c_lo[a] = (float)(D.c[a] - (double)hi);
+    F.o0[a] = (float)(p[0][a] - D.c[a]);
+    F.e1[a] = (float)e1[a];
+    F.e2[a] = (float)e2[a];
+    F.n[a] = (float)D.n[a];
+  }
+  F.area2 = (float)a2;
+  F.h2 = (float)D.h2;
+  ed[k] = D;
+  ef[k] = F;
+  bc[k] = bc_in[e];
+}
+
+// ---------------------------------------------------------------------------
+// pair geometry helpers: d = c_e - c_i, o0 = p0_e - c_i (offsets of the
+// integration element relative to the collocation point)
+// ---------------------------------------------------------------------------
+template <typename R> struct PairGeo {
+  R d[3], o0[3], e1[3], e2[3], n[3];
+  R area2, he2, d2;
+};
+
+__device__ __forceinline__ void pair_geo(const ElemF* ef, const ElemD* ed, int i, int e,
+                                         PairGeo<float>& g, int& band) {
+  const ElemF& I = ef[i];
+  const ElemF& E = ef[e];
+  float d2 = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g.d[a] = (E.c_hi[a] - I.c_hi[a]) + (E.c_lo[a] - I.c_lo[a]);
+    d2 += g.d[a] * g.d[a];
+    g.o0[a] = g.d[a] + E.o0[a];
+    g.e1[a] = E.e1[a];
+    g.e2[a] = E.e2[a];
+    g.n[a] = E.n[a];
+  }
+  g.area2 = E.area2;
+  g.he2 = E.h2;
+  g.d2 = d2;
+  if (i == e) {
+    band = BAND_SELF;
+    return;
+  }
+  // exact-consistent band: FP64 decision near a threshold
+  const float thr[3] = {float(RHO2_NEAR), float(RHO2_Q4), float(RHO2_Q2)};
+  bool close = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float t = thr[k] * g.he2;
+    close |= fabsf(d2 - t) <= 1e-4f * t;
+  }
+  if (close) {
+    const ElemD& Id = ed[i];
+    const ElemD& Ed = ed[e];
+    double dd = 0;
+    for (int a = 0; a < 3; ++a) dd += (Ed.c[a] - Id.c[a]) * (Ed.c[a] - Id.c[a]);
+    band = band_of<double>(dd, Ed.h2);
+  } else {
+    band = band_of<float>(d2, g.he2);
+  }
+}
+
+__device__ __forceinline__ void pair_geo(const ElemF* ef, const ElemD* ed, int i, int e,
+                                         PairGeo<double>& g, int& band) {
+  const ElemD& I = ed[i];
+  const ElemD& E = ed[e];
+  double d2 = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g.d[a] = E.c[a] - I.c[a];
+    d2 += g.d[a] * g.d[a];
+    g.o0[a] = E.p0[a] - I.c[a];
+    g.e1[a] = E.p1[a] - E.p0[a];
+    g.e2[a] = E.p2[a] - E.p0[a];
+    g.n[a] = E.n[a];
+  }
+  g.area2 = E.area2;
+  g.he2 = E.h2;
+  g.d2 = d2;
+  band = (i == e) ? BAND_SELF : band_of<double>(d2, E.h2);
+}
+
+// Regular-band integral of a pair (bands Q4, Q2, Q1).
+template <typename R>
+__device__ __forceinline__ void regular_pair(UTAcc<R>& acc, const PairGeo<R>& g, int band,
+                                             const KParams<R>& P) {
+  acc.zero();
+  if (band == BAND_Q4) {
+    integrate_collapsed<R, 4>(acc, g.o0, g.e1, g.e2, g.area2, g.n, P);
+  } else if (band == BAND_Q2) {
+    integrate_collapsed<R, 2>(acc, g.o0, g.e1, g.e2, g.area2, g.n, P);
+  } else {
+    accumulate_point<R>(acc, g.d[0], g.d[1], g.d[2], g.n[0], g.n[1], g.n[2], R(0.5) * g.area2, P);
+  }
+}
+
+template <typename Op, typename R> __device__ __forceinline__ Op to_op(cplx<R> v) {
+  Op o;
+  o.re = decltype(o.re)(v.re);
+  o.im = decltype(o.im)(v.im);
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// singular pair detection (two passes for a deterministic list)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_sing(const ElemD* ed, int i, int e) {
+  if (i == e) return true;
+  const ElemD& I = ed[i];
+  const ElemD& E = ed[e];
+  double dd = 0;
+  for (int a = 0; a < 3; ++a) dd += (E.c[a] - I.c[a]) * (E.c[a] - I.c[a]);
+  return dd < RHO2_NEAR * E.h2;
+}
+
+__global__ void k_sing_count(const NearBlk* __restrict__ blks, const ElemD* __restrict__ ed,
+                             int* __restrict__ count) {
+  NearBlk B = blks[blockIdx.x];
+  int np = B.nr * B.nc;
+  int c = 0;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    int i = B.r0 + p % B.nr, e = B.c0 + p / B.nr;
+    c += is_sing(ed, i, e) ? 1 : 0;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  __shared__ int s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    count[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sing_fill(const NearBlk* __restrict__ blks, const ElemD* __restrict__ ed,
+                            const int* __restrict__ offs, SingPair* __restrict__ out) {
+  NearBlk B = blks[blockIdx.x];
+  int np = B.nr * B.nc;
+  int ld = 3 * B.nr;
+  __shared__ int warp_tot[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = offs[blockIdx.x];
+  __syncthreads();
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int p0 = 0; p0 < np; p0 += blockDim.x) {
+    int p = p0 + threadIdx.x;
+    bool f = false;
+    int i = 0, e = 0;
+    if (p < np) {
+      i = B.r0 + p % B.nr;
+      e = B.c0 + p / B.nr;
+      f = is_sing(ed, i, e);
+    }
+    unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_tot[wid] = __popc(m);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < wid) before += warp_tot[w];
+      tot += warp_tot[w];
+    }
+    if (f) {
+      int pos = base + before + __popc(m & ((1u << lane) - 1));
+      SingPair sp;
+      sp.i = i;
+      sp.e = e;
+      sp.entry = B.off + (long long)(3 * (e - B.c0)) * ld + 3 * (i - B.r0);
+      sp.ld = ld;
+      sp.self = (i == e);
+      out[pos] = sp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += tot;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// static Kelvin parts (FP64, once per mesh): one warp per pair
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Polar parameters of the triangle (c, pa, pb) about c (normal n).
+struct PolarSub {
+  double d, fh[3], gh[3], tha, dth;
+};
+__device__ __forceinline__ PolarSub polar_sub(const double* c, const double* pa, const double* pb,
+                                              const double* n) {
+  PolarSub S;
+  double t[3], cpa[3];
+  for (int a = 0; a < 3; ++a) {
+    t[a] = pb[a] - pa[a];
+    cpa[a] = c[a] - pa[a];
+  }
+  double lam = (cpa[0] * t[0] + cpa[1] * t[1] + cpa[2] * t[2]) / (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+  double fv[3];
+  for (int a = 0; a < 3; ++a) fv[a] = pa[a] + lam * t[a] - c[a];
+  S.d = sqrt(fv[0] * fv[0] + fv[1] * fv[1] + fv[2] * fv[2]);
+  for (int a = 0; a < 3; ++a) S.fh[a] = fv[a] / S.d;
+  S.gh[0] = n[1] * S.fh[2] - n[2] * S.fh[1];
+  S.gh[1] = n[2] * S.fh[0] - n[0] * S.fh[2];
+  S.gh[2] = n[0] * S.fh[1] - n[1] * S.fh[0];
+  double va[3], vb[3];
+  for (int a = 0; a < 3; ++a) {
+    va[a] = pa[a] - c[a];
+    vb[a] = pb[a] - c[a];
+  }
+  double tha = atan2(va[0] * S.gh[0] + va[1] * S.gh[1] + va[2] * S.gh[2],
+                     va[0] * S.fh[0] + va[1] * S.fh[1] + va[2] * S.fh[2]);
+  double thb = atan2(vb[0] * S.gh[0] + vb[1] * S.gh[1] + vb[2] * S.gh[2],
+                     vb[0] * S.fh[0] + vb[1] * S.fh[1] + vb[2] * S.fh[2]);
+  S.tha = tha;
+  S.dth = thb - tha;
+  return S;
+}
+
+__device__ __forceinline__ const double* vtx(const ElemD& E, int k) {
+  return k == 0 ? E.p0 : (k == 1 ? E.p1 : E.p2);
+}
+
+__global__ void k_static(const SingPair* __restrict__ pairs, int npairs, const ElemD* __restrict__ ed,
+                         KParams<double> P, double* __restrict__ out) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= npairs) return;
+  SingPair sp = pairs[warp];
+  const ElemD& E = ed[sp.e];
+  const ElemD& I = ed[sp.i];
+  double us[9], ts[9];
+  for (int k = 0; k < 9; ++k) us[k] = ts[k] = 0.0;
+  if (sp.self) {
+    // 3 triangles x 16 angles; closed-form ray integrals
+    double nu = P.nu;
+    double a34 = 3.0 - 4.0 * nu, a12 = 1.0 - 2.0 * nu;
+    for (int q = lane; q < 3 * SELF_NT_STATIC; q += 32) {
+      int sub = q / SELF_NT_STATIC, m = q % SELF_NT_STATIC;
+      PolarSub S = polar_sub(E.c, vtx(E, sub), vtx(E, (sub + 1) % 3), E.n);
+      double th = S.tha + S.dth * gl_x<double>(SELF_NT_STATIC, m);
+      double wth = S.dth * gl_w<double>(SELF_NT_STATIC, m);
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      double R = S.d / cs;
+      double dir[3];
+      for (int a = 0; a < 3; ++a) dir[a] = cs * S.fh[a] + sn * S.gh[a];
+      double lr = log(R);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          us[3 * i + j] += wth * R * P.kel_u * ((i == j ? a34 : 0.0) + dir[i] * dir[j]);
+          ts[3 * i + j] += wth * lr * a12 * P.kel_t * (dir[i] * E.n[j] - dir[j] * E.n[i]);
+        }
+    }
+  } else {
+    // 64 children (3 midpoint-subdivision levels) x collapsed 4x4
+    for (int q = lane; q < 64 * NEAR_Q * NEAR_Q; q += 32) {
+      int child = q / (NEAR_Q * NEAR_Q), pt = q % (NEAR_Q * NEAR_Q);
+      double a[3], b[3], c[3];
+      for (int k = 0; k < 3; ++k) {
+        a[k] = E.p0[k];
+        b[k] = E.p1[k];
+        c[k] = E.p2[k];
+      }
+      int digits = child;
+      int dig[NEAR_LEVELS];
+      for (int l = NEAR_LEVELS - 1; l >= 0; --l) {
+        dig[l] = digits & 3;
+        digits >>= 2;
+      }
+      for (int l = 0; l < NEAR_LEVELS; ++l) {
+        double mab[3], mbc[3], mca[3];
+        for (int k = 0; k < 3; ++k) {
+          mab[k] = 0.5 * (a[k] + b[k]);
+          mbc[k] = 0.5 * (b[k] + c[k]);
+          mca[k] = 0.5 * (c[k] + a[k]);
+        }
+        for (int k = 0; k < 3; ++k) {
+          double na, nb, nc;
+          switch (dig[l]) {
+            case 0: na = a[k]; nb = mab[k]; nc = mca[k]; break;
+            case 1: na = mab[k]; nb = b[k]; nc = mbc[k]; break;
+            case 2: na = mca[k]; nb = mbc[k]; nc = c[k]; break;
+            default: na = mbc[k]; nb = mca[k]; nc = mab[k]; break;
+          }
+          a[k] = na;
+          b[k] = nb;
+          c[k] = nc;
+        }
+      }
+      double e1[3], e2[3];
+      for (int k = 0; k < 3; ++k) {
+        e1[k] = b[k] - a[k];
+        e2[k] = c[k] - a[k];
+      }
+      double cr0 = e1[1] * e2[2] - e1[2] * e2[1], cr1 = e1[2] * e2[0] - e1[0] * e2[2],
+             cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+      double area2 = sqrt(cr0 * cr0 + cr1 * cr1 + cr2 * cr2);
+      int ia = pt / NEAR_Q, ib = pt % NEAR_Q;
+      double u = gl_x<double>(NEAR_Q, ia), v = (1.0 - u) * gl_x<double>(NEAR_Q, ib);
+      double w = area2 * gl_w<double>(NEAR_Q, ia) * gl_w<double>(NEAR_Q, ib) * (1.0 - u);
+      double rv[3];
+      for (int k = 0; k < 3; ++k) rv[k] = a[k] + u * e1[k] + v * e2[k] - I.c[k];
+      add_kelvin(us, ts, rv[0], rv[1], rv[2], E.n[0], E.n[1], E.n[2], w, P);
+    }
+  }
+  for (int k = 0; k < 9; ++k) {
+    us[k] = warp_sum(us[k]);
+    ts[k] = warp_sum(ts[k]);
+  }
+  if (lane == 0) {
+    double* o = out + 18 * (long long)warp;
+    for (int k = 0; k < 9; ++k) {
+      o[k] = us[k];
+      o[9 + k] = ts[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// regular near-field entries: one CTA per near block
+// ---------------------------------------------------------------------------
+template <typename R, typename Op>
+__global__ void __launch_bounds__(256) k_near_regular(const NearBlk* __restrict__ blks,
+                                                      const ElemF* __restrict__ ef,
+                                                      const ElemD* __restrict__ ed,
+                                                      const signed char* __restrict__ bc,
+                                                      KParams<R> P, Op* __restrict__ near) {
+  NearBlk B = blks[blockIdx.x];
+  int np = B.nr * B.nc;
+  long long ld = 3 * B.nr;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    int il = p % B.nr, el = p / B.nr;
+    int i = B.r0 + il, e = B.c0 + el;
+    PairGeo<R> g;
+    int band;
+    pair_geo(ef, ed, i, e, g, band);
+    if (band == BAND_SELF || band == BAND_NEAR) continue;
+    UTAcc<R> acc;
+    regular_pair<R>(acc, g, band, P);
+    bool trac = bc[e] == BEM_BC_TRACTION;
+    Op* dst = near + B.off + (3 * el) * ld + 3 * il;
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        cplx<R> v = trac ? acc.t[3 * a + b] : -acc.U(a, b);
+        dst[b * ld + a] = to_op<Op>(v);
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// singular + near-singular entries (FP64): one warp per pair
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool inv3(const c128* A, c128* Ai) {
+  // cofactor inverse of a complex 3x3 (row-major)
+  c128 c00 = A[4] * A[8] - A[5] * A[7];
+  c128 c01 = A[5] * A[6] - A[3] * A[8];
+  c128 c02 = A[3] * A[7] - A[4] * A[6];
+  c128 det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+  if (abs2(det) == 0.0) return false;
+  c128 id = inv(det);
+  Ai[0] = c00 * id;
+  Ai[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+  Ai[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+  Ai[3] = c01 * id;
+  Ai[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+  Ai[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+  Ai[6] = c02 * id;
+  Ai[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+  Ai[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+  return true;
+}
+
+template <typename Op>
+__global__ void k_sing(const SingPair* __restrict__ pairs, int npairs, const ElemD* __restrict__ ed,
+                       const signed char* __restrict__ bc, const double* __restrict__ stat,
+                       KParams<double> P, Op* __restrict__ near, c128* __restrict__ pinv,
+                       const double* __restrict__ pattern, c128 pk, c128* __restrict__ b,
+                       int* __restrict__ status) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= npairs) return;
+  SingPair sp = pairs[warp];
+  const ElemD& E = ed[sp.e];
+  const ElemD& I = ed[sp.i];
+  UTAcc<double> acc;
+  acc.zero();
+  if (sp.self) {
+    for (int q = lane; q < 3 * SELF_NT * SELF_NR; q += 32) {
+      int sub = q / (SELF_NT * SELF_NR);
+      int m = (q / SELF_NR) % SELF_NT, l = q % SELF_NR;
+      PolarSub S = polar_sub(E.c, vtx(E, sub), vtx(E, (sub + 1) % 3), E.n);
+      double th = S.tha + S.dth * gl_x<double>(SELF_NT, m);
+      double wth = S.dth * gl_w<double>(SELF_NT, m);
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      double R = S.d / cs;
+      double r = R * gl_x<double>(SELF_NR, l);
+      double w = wth * R * gl_w<double>(SELF_NR, l) * r;
+      double rv[3];
+      for (int a = 0; a < 3; ++a) rv[a] = r * (cs * S.fh[a] + sn * S.gh[a]);
+      accumulate_point<double>(acc, rv[0], rv[1], rv[2], E.n[0], E.n[1], E.n[2], w, P);
+      subtract_kelvin(acc, rv[0], rv[1], rv[2], E.n[0], E.n[1], E.n[2], w, P);
+    }
+  } else if (lane < NEAR_Q_REM * NEAR_Q_REM) {
+    int ia = lane / NEAR_Q_REM, ib = lane % NEAR_Q_REM;
+    double u = gl_x<double>(NEAR_Q_REM, ia), v = (1.0 - u) * gl_x<double>(NEAR_Q_REM, ib);
+    double w = E.area2 * gl_w<double>(NEAR_Q_REM, ia) * gl_w<double>(NEAR_Q_REM, ib) * (1.0 - u);
+    double rv[3];
+    for (int k = 0; k < 3; ++k)
+      rv[k] = E.p0[k] + u * (E.p1[k] - E.p0[k]) + v * (E.p2[k] - E.p0[k]) - I.c[k];
+    accumulate_point<double>(acc, rv[0], rv[1], rv[2], E.n[0], E.n[1], E.n[2], w, P);
+    subtract_kelvin(acc, rv[0], rv[1], rv[2], E.n[0], E.n[1], E.n[2], w, P);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    acc.u[k].re = warp_sum(acc.u[k].re);
+    acc.u[k].im = warp_sum(acc.u[k].im);
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    acc.t[k].re = warp_sum(acc.t[k].re);
+    acc.t[k].im = warp_sum(acc.t[k].im);
+  }
+  if (lane != 0) return;
+  const double* st = stat + 18 * (long long)warp;
+  c128 U[9], T[9];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      U[3 * a + c] = acc.U(a, c);
+      U[3 * a + c].re += st[3 * a + c];
+      T[3 * a + c] = acc.t[3 * a + c];
+      T[3 * a + c].re += st[9 + 3 * a + c];
+    }
+  if (sp.self)
+    for (int a = 0; a < 3; ++a) T[4 * a].re += 0.5;  // free term c_ij = delta_ij / 2
+  bool trac = bc[sp.e] == BEM_BC_TRACTION;
+  c128 Ablk[9];
+  for (int k = 0; k < 9; ++k) Ablk[k] = trac ? T[k] : -U[k];
+  if (near) {
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) near[sp.entry + (long long)c * sp.ld + a] = to_op<Op>(Ablk[3 * a + c]);
+  }
+  if (sp.self && pinv) {
+    c128 Ai[9];
+    if (!inv3(Ablk, Ai)) atomicExch(status, 3);
+    for (int k = 0; k < 9; ++k) pinv[9 * (long long)sp.i + k] = Ai[k];
+  }
+  if (b) {
+    const double* pt = pattern + 3 * (long long)sp.e;
+    if (pt[0] != 0.0 || pt[1] != 0.0 || pt[2] != 0.0) {
+      for (int a = 0; a < 3; ++a) {
+        c128 s = mk<double>(0, 0);
+        for (int c = 0; c < 3; ++c) {
+          c128 Bv = trac ? U[3 * a + c] : -T[3 * a + c];
+          cfmr(s, Bv, pt[c]);
+        }
+        s = s * pk;
+        atomicAdd(&b[3 * (long long)sp.i + a].re, s.re);
+        atomicAdd(&b[3 * (long long)sp.i + a].im, s.im);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// right-hand side over regular pairs, on the fly: one warp per row element
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_rhs(int ne, const int* __restrict__ loaded, int nloaded, const ElemF* __restrict__ ef,
+                      const ElemD* __restrict__ ed, const signed char* __restrict__ bc,
+                      const double* __restrict__ pattern, KParams<R> P, c128 pk, c128* __restrict__ b) {
+  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= ne) return;
+  cplx<R> s[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+  for (int j = lane; j < nloaded; j += 32) {
+    int e = loaded[j];
+    PairGeo<R> g;
+    int band;
+    pair_geo(ef, ed, i, e, g, band);
+    if (band == BAND_SELF || band == BAND_NEAR) continue;
+    UTAcc<R> acc;
+    regular_pair<R>(acc, g, band, P);
+    bool trac = bc[e] == BEM_BC_TRACTION;
+    const double* pt = pattern + 3 * (long long)e;
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) {
+        cplx<R> Bv = trac ? acc.U(a, c) : -acc.t[3 * a + c];
+        cfmr(s[a], Bv, R(pt[c]));
+      }
+  }
+  for (int a = 0; a < 3; ++a) {
+    double re = warp_sum((double)s[a].re), im = warp_sum((double)s[a].im);
+    if (lane == 0) b[3 * (long long)i + a] = mk<double>(re, im) * pk;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// ACA with partial pivoting: one CTA per admissible block
+// ---------------------------------------------------------------------------
+template <typename R> struct BlockRed {
+  double v[32];
+  int idx[32];
+};
+
+// block-wide max |value| with index (ties -> smaller index)
+__device__ __forceinline__ void block_argmax(double& v, int& idx, BlockRed<double>& sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh.v[wid] = v;
+    sh.idx[wid] = idx;
+  }
+  __syncthreads();
+  v = sh.v[0];
+  idx = sh.idx[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+    if (sh.v[w] > v || (sh.v[w] == v && sh.idx[w] < idx)) {
+      v = sh.v[w];
+      idx = sh.idx[w];
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, BlockRed<double>& sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh.v[wid] = v;
+  __syncthreads();
+  double t = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh.v[w];
+  return t;
+}
+
+template <typename R, typename Op>
+__global__ void __launch_bounds__(256) k_aca(const FarBlk* __restrict__ blks, const ElemF* __restrict__ ef,
+                                             const ElemD* __restrict__ ed,
+                                             const signed char* __restrict__ bc, KParams<R> P,
+                                             Op* __restrict__ Ustore, Op* __restrict__ Vstore,
+                                             int* __restrict__ rank, int* __restrict__ fails,
+                                             double eps) {
+  using T = decltype(Op{}.re);
+  FarBlk B = blks[blockIdx.x];
+  const int m = 3 * B.nr, n = 3 * B.nc;
+  Op* Ub = Ustore + B.uoff;
+  Op* Vb = Vstore + B.voff;
+  __shared__ BlockRed<double> red;
+  __shared__ Op sU[256];   // U[i*, l] for l < k  (rmax <= 256)
+  __shared__ Op sV[256];   // V[j*, l]
+  __shared__ int rows_used[256];
+  const int rmax = min(B.rmax, 256);
+  int k = 0;
+  int istar = 0;
+  double normS2 = 0.0;
+  bool converged = false;
+  while (k < rmax) {
+    // --- residual row istar -> V[:, k]
+    for (int l = threadIdx.x; l < k; l += blockDim.x) sU[l] = Ub[(long long)l * m + istar];
+    __syncthreads();
+    int ie = B.r0 + istar / 3, ia = istar % 3;
+    for (int el = threadIdx.x; el < B.nc; el += blockDim.x) {
+      int e = B.c0 + el;
+      PairGeo<R> g;
+      int band;
+      pair_geo(ef, ed, ie, e, g, band);
+      UTAcc<R> acc;
+      regular_pair<R>(acc, g, band, P);
+      bool trac = bc[e] == BEM_BC_TRACTION;
+      for (int c = 0; c < 3; ++c) {
+        cplx<R> v = trac ? acc.t[3 * ia + c] : -acc.U(ia, c);
+        int j = 3 * el + c;
+        cplx<T> vv = mk<T>(T(v.re), T(v.im));
+        for (int l = 0; l < k; ++l) {
+          Op ul = sU[l], vl = Vb[(long long)l * n + j];
+          vv = vv - mk<T>(ul.re, ul.im) * mk<T>(vl.re, vl.im);
+        }
+        Vb[(long long)k * n + j] = to_op<Op>(vv);
+      }
+    }
+    __syncthreads();
+    double best = -1.0;
+    int jstar = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      Op v = Vb[(long long)k * n + j];
+      double a = (double)v.re * v.re + (double)v.im * v.im;
+      if (a > best) {
+        best = a;
+        jstar = j;
+      }
+    }
+    block_argmax(best, jstar, red);
+    if (!(best > 0.0)) {
+      converged = true;  // zero residual row: the block is represented exactly
+      break;
+    }
+    Op pv = Vb[(long long)k * n + jstar];
+    cplx<T> ipiv = inv(mk<T>(pv.re, pv.im));
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      Op v = Vb[(long long)k * n + j];
+      Vb[(long long)k * n + j] = to_op<Op>(mk<T>(v.re, v.im) * ipiv);
+    }
+    // --- residual column jstar -> U[:, k]
+    for (int l = threadIdx.x; l < k; l += blockDim.x) sV[l] = Vb[(long long)l * n + jstar];
+    __syncthreads();
+    int je = B.c0 + jstar / 3, jc = jstar % 3;
+    bool trac = bc[je] == BEM_BC_TRACTION;
+    for (int il = threadIdx.x; il < B.nr; il += blockDim.x) {
+      int i = B.r0 + il;
+      PairGeo<R> g;
+      int band;
+      pair_geo(ef, ed, i, je, g, band);
+      UTAcc<R> acc;
+      regular_pair<R>(acc, g, band, P);
+      for (int a = 0; a < 3; ++a) {
+        cplx<R> v = trac ? acc.t[3 * a + jc] : -acc.U(a, jc);
+        int ii = 3 * il + a;
+        cplx<T> vv = mk<T>(T(v.re), T(v.im));
+        for (int l = 0; l < k; ++l) {
+          Op ul = Ub[(long long)l * m + ii], vl = sV[l];
+          vv = vv - mk<T>(ul.re, ul.im) * mk<T>(vl.re, vl.im);
+        }
+        Ub[(long long)k * m + ii] = to_op<Op>(vv);
+      }
+    }
+    if (threadIdx.x == 0) rows_used[k] = istar;
+    __syncthreads();
+    // earlier pivot rows are exactly represented already: their residual is zero
+    for (int l = threadIdx.x; l < k; l += blockDim.x) Ub[(long long)k * m + rows_used[l]] = Op{};
+    __syncthreads();
+    // --- norms: ||S_k||^2 = ||S_{k-1}||^2 + 2 Re sum_l (u_l^H u_k)(v_l^H v_k) + |u_k|^2 |v_k|^2
+    double nu2 = 0, nv2 = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      Op u = Ub[(long long)k * m + i];
+      nu2 += (double)u.re * u.re + (double)u.im * u.im;
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      Op v = Vb[(long long)k * n + j];
+      nv2 += (double)v.re * v.re + (double)v.im * v.im;
+    }
+    nu2 = block_sum(nu2, red);
+    nv2 = block_sum(nv2, red);
+    double cross = 0.0;
+    for (int l = 0; l < k; ++l) {
+      double ur = 0, ui = 0, vr = 0, vi = 0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        Op a = Ub[(long long)l * m + i], b2 = Ub[(long long)k * m + i];
+        ur += (double)a.re * b2.re + (double)a.im * b2.im;
+        ui += (double)a.re * b2.im - (double)a.im * b2.re;
+      }
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        Op a = Vb[(long long)l * n + j], b2 = Vb[(long long)k * n + j];
+        vr += (double)a.re * b2.re + (double)a.im * b2.im;
+        vi += (double)a.re * b2.im - (double)a.im * b2.re;
+      }
+      ur = block_sum(ur, red);
+      ui = block_sum(ui, red);
+      vr = block_sum(vr, red);
+      vi = block_sum(vi, red);
+      cross += ur * vr - ui * vi;
+    }
+    normS2 += 2.0 * cross + nu2 * nv2;
+    ++k;
+    if (nu2 * nv2 <= eps * eps * normS2) {
+      converged = true;
+      break;
+    }
+    // --- next pivot row: largest entry of u_k outside the rows used so far
+    double bu = -1.0;
+    int inext = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      if (i == istar) continue;
+      Op u = Ub[(long long)(k - 1) * m + i];
+      double a = (double)u.re * u.re + (double)u.im * u.im;
+      if (a > bu) {
+        bu = a;
+        inext = i;
+      }
+    }
+    block_argmax(bu, inext, red);
+    if (!(bu > 0.0)) {
+      converged = true;
+      break;
+    }
+    istar = inext;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    rank[blockIdx.x] = k;
+    if (!converged) atomicAdd(fails, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_centroids(const double* xyz, long long nv, const int* tri, int ne, double* cen, double* h,
+                      int* bad, cudaStream_t st) {
+  count_if(true);
+  k_centroids<<<(ne + 127) / 128, 128, 0, st>>>(xyz, nv, tri, ne, cen, h, bad);
+}
+void launch_geometry(const double* xyz, const int* tri, const int* perm, const signed char* bc_in, int ne,
+                     ElemF* ef, ElemD* ed, signed char* bc, cudaStream_t st) {
+  count_if(true);
+  k_geometry<<<(ne + 127) / 128, 128, 0, st>>>(xyz, tri, perm, bc_in, ne, ef, ed, bc);
+}
+void launch_sing_count(const NearBlk* blks, int nblk, const ElemD* ed, int* count, cudaStream_t st) {
+  if (count_if(nblk)) k_sing_count<<<nblk, 256, 0, st>>>(blks, ed, count);
+}
+void launch_sing_fill(const NearBlk* blks, int nblk, const ElemD* ed, const int* offs, SingPair* out,
+                      cudaStream_t st) {
+  if (count_if(nblk)) k_sing_fill<<<nblk, 256, 0, st>>>(blks, ed, offs, out);
+}
+void launch_static(const SingPair* pairs, int n, const ElemD* ed, const KParams<double>& P, double* out,
+                   cudaStream_t st) {
+  if (count_if(n)) k_static<<<(n + 3) / 4, 128, 0, st>>>(pairs, n, ed, P, out);
+}
+template <typename R, typename Op>
+void launch_near_regular(const NearBlk* blks, int nblk, const ElemF* ef, const ElemD* ed,
+                         const signed char* bc, const KParams<R>& P, Op* near, cudaStream_t st) {
+  if (count_if(nblk)) k_near_regular<R, Op><<<nblk, 256, 0, st>>>(blks, ef, ed, bc, P, near);
+}
+template <typename Op>
+void launch_sing(const SingPair* pairs, int n, const ElemD* ed, const signed char* bc, const double* stat,
+                 const KParams<double>& P, Op* near, c128* pinv, const double* pattern, c128 pk, c128* b,
+                 int* status, cudaStream_t st) {
+  if (count_if(n)) k_sing<Op><<<(n + 3) / 4, 128, 0, st>>>(pairs, n, ed, bc, stat, P, near, pinv, pattern, pk, b, status);
+}
+template <typename R>
+void launch_rhs(int ne, const int* loaded, int nloaded, const ElemF* ef, const ElemD* ed,
+                const signed char* bc, const double* pattern, const KParams<R>& P, c128 pk, c128* b,
+                cudaStream_t st) {
+  count_if(true);
+  k_rhs<R><<<(ne + 7) / 8, 256, 0, st>>>(ne, loaded, nloaded, ef, ed, bc, pattern, P, pk, b);
+}
+template <typename R, typename Op>
+void launch_aca(const FarBlk* blks, int nblk, const ElemF* ef, const ElemD* ed, const signed char* bc,
+                const KParams<R>& P, Op* U, Op* V, int* rank, int* fails, double eps, cudaStream_t st) {
+  if (count_if(nblk)) k_aca<R, Op><<<nblk, 256, 0, st>>>(blks, ef, ed, bc, P, U, V, rank, fails, eps);
+}
+
+template void launch_near_regular<float, c64>(const NearBlk*, int, const ElemF*, const ElemD*,
+                                              const signed char*, const KParams<float>&, c64*, cudaStream_t);
+template void launch_near_regular<double, c128>(const NearBlk*, int, const ElemF*, const ElemD*,
+                                                const signed char*, const KParams<double>&, c128*,
+                                                cudaStream_t);
+template void launch_sing<c64>(const SingPair*, int, const ElemD*, const signed char*, const double*,
+                               const KParams<double>&, c64*, c128*, const double*, c128, c128*, int*,
+                               cudaStream_t);
+template void launch_sing<c128>(const SingPair*, int, const ElemD*, const signed char*, const double*,
+                                const KParams<double>&, c128*, c128*, const double*, c128, c128*, int*,
+                                cudaStream_t);
+template void launch_rhs<float>(int, const int*, int, const ElemF*, const ElemD*, const signed char*,
+                                const double*, const KParams<float>&, c128, c128*, cudaStream_t);
+template void launch_rhs<double>(int, const int*, int, const ElemF*, const ElemD*, const signed char*,
+                                 const double*, const KParams<double>&, c128, c128*, cudaStream_t);
+template void launch_aca<float, c64>(const FarBlk*, int, const ElemF*, const ElemD*, const signed char*,
+                                     const KParams<float>&, c64*, c64*, int*, int*, double, cudaStream_t);
+template void launch_aca<double, c128>(const FarBlk*, int, const ElemF*, const ElemD*, const signed char*,
+                                       const KParams<double>&, c128*, c128*, int*, int*, double,
+                                       cudaStream_t);
+
+}  // namespace bem

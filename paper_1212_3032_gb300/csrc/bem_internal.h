@@ -1,0 +1,196 @@
+// Internal declarations shared by the library's translation units: device
+// data layouts of the mesh and of the hierarchical operator, the context,
+// and the kernel launchers each unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "bem_common.cuh"
+#include "bem_tree.h"
+
+namespace bem {
+
+// ---- device element geometry (tree order) --------------------------------
+// FP32 view: centroid split into hi + lo floats (so centroid differences are
+// accurate in FP32), vertex p0 relative to the centroid, edges, normal.
+struct ElemF {
+  float c_hi[3], c_lo[3];
+  float o0[3], e1[3], e2[3];
+  float n[3];
+  float area2;  // 2 * area
+  float h2;     // (longest edge)^2
+};
+// FP64 view for the singular / near-singular rules.
+struct ElemD {
+  double c[3];
+  double p0[3], p1[3], p2[3];
+  double n[3];
+  double area2;
+  double h2;
+};
+
+// Dense near-field block (tau rows x sigma cols), column-major, ld = 3 * nr.
+struct NearBlk {
+  long long off;  // offset in the near-field array (entries)
+  int r0, nr;     // row cluster: first tree element, element count
+  int c0, nc;     // column cluster
+};
+
+// Low-rank far-field block A ~ U V^T; U: (3 nr) x rmax column-major,
+// V: (3 nc) x rmax column-major; rank[b] <= rmax set by ACA.
+struct FarBlk {
+  long long uoff, voff;
+  int r0, nr, c0, nc;
+  int rmax;
+  int toff;  // offset of this block's t = V^T x in the t buffer
+};
+
+// One column panel of a leaf row of the matrix-vector product:
+// y[rows of leaf] += P x_panel, P column-major with leading dimension ld.
+struct Panel {
+  long long data;  // offset into the near array (kind 0) or U array (kind 1)
+  int ld;          // leading dimension of the stored block
+  int ncols;       // kind 0: columns; kind 1: ignored (rank read at run time)
+  int xoff;        // kind 0: first x index; kind 1: far block index
+  int kind;
+};
+
+// Singular (SELF) and near-singular (NEAR) element pairs, FP64 path.
+struct SingPair {
+  int i, e;         // collocation element, integration element (tree order)
+  long long entry;  // near-array offset of entry (row 3 i', col 3 e')
+  int ld;           // leading dimension of that block
+  int self;         // 1 for i == e
+};
+
+template <typename T> struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t alloc(size_t count) {
+    release();
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e == cudaSuccess) n = count;
+    else p = nullptr;
+    return e;
+  }
+  cudaError_t ensure(size_t count) { return count <= n ? cudaSuccess : alloc(count); }
+};
+
+// Process-wide count of kernel launches issued by the library (for the
+// launch count reported by measurements). count_if(c) adds one when c holds.
+bool count_if(bool c);
+long long launch_count();
+
+// Host-side rule tables (Gauss-Legendre on [0,1], series coefficients).
+void make_rule_tables(RuleTables& t);
+
+// Translation-unit uploads of the constant tables.
+cudaError_t upload_rules_assemble(const RuleTables& t, cudaStream_t st);
+
+}  // namespace bem
+
+struct bem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // material (Sec. 2.1)
+  bool have_mat = false;
+  double E = 0, nu = 0, rho = 0, mu = 0, lam = 0, cs = 0, cp = 0;
+  // window (Sec. 3)
+  double eta = 0;
+  int window = BEM_WIN_NONE;
+
+  // mesh
+  bool have_mesh = false;
+  int ne = 0;
+  long long N = 0;
+  bem_opts mesh_opts{};
+  bem::ClusterTree tree;
+  std::vector<signed char> bc_host;  // tree order
+  bem::DevBuf<bem::ElemF> ef;
+  bem::DevBuf<bem::ElemD> ed;
+  bem::DevBuf<signed char> bc;       // tree order
+  bem::DevBuf<int> perm;             // tree -> caller
+  bem::DevBuf<int> iperm;            // caller -> tree
+
+  // operator structure (frequency independent)
+  std::vector<bem::NearBlk> near_h;
+  std::vector<bem::FarBlk> far_h;
+  bem::DevBuf<bem::NearBlk> near_d;
+  bem::DevBuf<bem::FarBlk> far_d;
+  long long near_entries = 0, u_entries = 0, v_entries = 0;
+  int t_entries = 0;
+  int nleaves = 0;
+  std::vector<int> leaf_nodes;        // node index per leaf (row order)
+  bem::DevBuf<int> leaf_r0, leaf_nr;  // per leaf
+  bem::DevBuf<int> panel_ptr;         // CSR over leaves
+  bem::DevBuf<bem::Panel> panels;
+  // singular pairs and their static parts
+  int nsing = 0;
+  bem::DevBuf<bem::SingPair> sing;
+  bem::DevBuf<double> sing_static;    // nsing x 18 (U* 9, T* 9)
+  bem::DevBuf<int> loaded;            // tree elements with nonzero prescribed pattern
+  int nloaded = 0;
+
+  // operator values at the current frequency
+  int prec = BEM_PREC_C64_MIXED;
+  bool assembled = false;
+  double s_re = 0, s_im = 0;
+  bem::DevBuf<bem::c64> near32, u32, v32, t32;
+  bem::DevBuf<bem::c128> near64, u64, v64, t64;
+  bem::DevBuf<int> rank;
+  bem::DevBuf<int> aca_fail;
+  bem::DevBuf<int> status;             // singular 3x3 diagonal block flag
+  bem::DevBuf<bem::c128> prec_inv;     // ne x 9 inverse diagonal blocks
+  bem::DevBuf<bem::c64> prec_inv32;
+
+  // solver workspace
+  bem::DevBuf<bem::c64> V32;           // Krylov basis (m+1) x N
+  bem::DevBuf<bem::c128> V64;
+  bem::DevBuf<bem::c64> w32;
+  bem::DevBuf<bem::c128> w64, x64, r64, b64, y64, tmp64;
+  bem::DevBuf<double> red;             // reduction scratch
+  bem::DevBuf<double> pattern;         // tree order ne x 3
+  double* host_red = nullptr;          // pinned
+
+  // event timing (bem_set_profiling)
+  bool profiling = false;
+  struct Pending {
+    cudaEvent_t a, b;
+    double bytes;
+    int kind;  // 0 H-matrix product, 1 assembly
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  long long prof_hmv_launches = 0, prof_asm_calls = 0;
+  long long used_lowrank = 0;
+  long long launches_at_reset = 0;  // sum_b rank_b (3 nr_b + 3 nc_b) after the last ACA
+  double prof_hmv_ms = 0, prof_hmv_bytes = 0, prof_asm_ms = 0;
+
+  // sweep results
+  int n_omega = 0;
+  double T = 0;
+  int nf = 0;
+  bem::DevBuf<bem::c128> sol;          // nf x N (tree order)
+  bem::DevBuf<bem::c128> Pk;           // nf
+  std::vector<bem::c128> Pk_host;
+};
+
+namespace bem {
+int fail(bem_ctx* ctx, int code, const std::string& msg);
+int fail_cuda(bem_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
+}

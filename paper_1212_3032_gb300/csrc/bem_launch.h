@@ -1,0 +1,72 @@
+// Kernel launchers provided by the assembly and solver translation units.
+#pragma once
+
+#include "bem_internal.h"
+
+namespace bem {
+
+// ---- assembly (bem_assemble.cu) ----
+void launch_centroids(const double* xyz, long long nv, const int* tri, int ne, double* cen, double* h,
+                      int* bad, cudaStream_t st);
+void launch_geometry(const double* xyz, const int* tri, const int* perm, const signed char* bc_in, int ne,
+                     ElemF* ef, ElemD* ed, signed char* bc, cudaStream_t st);
+void launch_sing_count(const NearBlk* blks, int nblk, const ElemD* ed, int* count, cudaStream_t st);
+void launch_sing_fill(const NearBlk* blks, int nblk, const ElemD* ed, const int* offs, SingPair* out,
+                      cudaStream_t st);
+void launch_static(const SingPair* pairs, int n, const ElemD* ed, const KParams<double>& P, double* out,
+                   cudaStream_t st);
+template <typename R, typename Op>
+void launch_near_regular(const NearBlk* blks, int nblk, const ElemF* ef, const ElemD* ed,
+                         const signed char* bc, const KParams<R>& P, Op* near, cudaStream_t st);
+template <typename Op>
+void launch_sing(const SingPair* pairs, int n, const ElemD* ed, const signed char* bc, const double* stat,
+                 const KParams<double>& P, Op* near, c128* pinv, const double* pattern, c128 pk, c128* b,
+                 int* status, cudaStream_t st);
+template <typename R>
+void launch_rhs(int ne, const int* loaded, int nloaded, const ElemF* ef, const ElemD* ed,
+                const signed char* bc, const double* pattern, const KParams<R>& P, c128 pk, c128* b,
+                cudaStream_t st);
+template <typename R, typename Op>
+void launch_aca(const FarBlk* blks, int nblk, const ElemF* ef, const ElemD* ed, const signed char* bc,
+                const KParams<R>& P, Op* U, Op* V, int* rank, int* fails, double eps, cudaStream_t st);
+
+// ---- solver (bem_solve.cu) ----
+// H-matrix product y = A x for nrhs right-hand sides (x, y: nrhs vectors of
+// length N, stride N). Op: operator storage; X: input vectors; Y: output;
+// accumulation in Acc (float or double).
+template <typename Op, typename X, typename Y, typename Acc>
+void launch_hmatvec(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V, cplx<Acc>* t,
+                    const X* x, Y* y, int nrhs, cudaStream_t st);
+
+// z = M^{-1} v per element (3x3 inverse diagonal blocks)
+template <typename Pm, typename V, typename Z>
+void launch_precond(const Pm* pinv, const V* v, Z* z, int ne, cudaStream_t st);
+
+// Partial dot products part[l * nblk + blk] of conj(V_l) . w, l < nvec (FP64)
+template <typename Vb, typename W>
+int launch_dots(const Vb* V, long long ldv, int nvec, const W* w, long long n, c128* part, cudaStream_t st);
+// out[l] = sum_blk part[l * nblk + blk]
+void launch_dots_final(const c128* part, int nblk, int nvec, c128* out, cudaStream_t st);
+// w -= sum_l V_l h_l
+template <typename Vb, typename W>
+void launch_update(const Vb* V, long long ldv, int nvec, const c128* h, W* w, long long n, cudaStream_t st);
+// v = w * scale (complex scale given on device as 1/||w|| in h[0].re)
+template <typename W, typename Vb>
+void launch_scale(const W* w, Vb* v, long long n, const double* inv_norm, cudaStream_t st);
+// r = b - y ; both c128
+void launch_residual(const c128* b, const c128* y, c128* r, long long n, cudaStream_t st);
+// x += sum_l V_l y_l (x c128) after preconditioning: caller passes z = M^{-1} V y
+template <typename Vb>
+void launch_combine(const Vb* V, long long ldv, int nvec, const c128* y, c128* out, long long n,
+                    cudaStream_t st);
+void launch_axpy(c128 a, const c128* x, c128* y, long long n, cudaStream_t st);
+void launch_copy_cast(const c128* x, c64* y, long long n, double scale, cudaStream_t st);
+void launch_copy_cast(const c128* x, c128* y, long long n, double scale, cudaStream_t st);
+
+// Eq. DFT-MFT for k = 0..n_omega/2
+void launch_load_dft(const double* P, int n_omega, double T, double eta, c128* out, cudaStream_t st);
+// Eq. IDFT-MFT: spec (nf x ldspec, columns at dof indices idx or 0..ndof-1)
+void launch_idft(const c128* spec, long long ldspec, const long long* idx, long long ndof, int n_omega,
+                 double T, double eta, int window, double* out, cudaStream_t st);
+
+}  // namespace bem

@@ -1,0 +1,465 @@
+// Solver kernels: hierarchical matrix-vector product, block-Jacobi
+// preconditioner, Arnoldi pieces with FP64 accumulation, and the modified
+// Fourier transforms (Sec. 3.3, Eqs. DFT-MFT and IDFT-MFT).
+//
+// H-matrix product (HBM-bound): y = D_near x + sum_b U_b (V_b^T x)
+//   k_hmv_t     t_b = V_b^T x for every admissible block (one CTA per block,
+//               one warp per factor column, coalesced column reads)
+//   k_hmv_rows  one CTA per leaf row cluster: streams its dense near blocks
+//               and its slices of the U_b factors once, column-major, each
+//               thread owning one row of the leaf (coalesced 8/16-byte loads),
+//               G column groups reduced through shared memory; no atomics.
+#include <algorithm>
+
+#include "bem_internal.h"
+#include "bem_launch.h"
+
+namespace bem {
+
+template <typename A, typename B> struct Promote;
+template <> struct Promote<float, float> { using type = float; };
+template <> struct Promote<float, double> { using type = double; };
+template <> struct Promote<double, float> { using type = double; };
+template <> struct Promote<double, double> { using type = double; };
+
+template <typename Acc, typename T> __device__ __forceinline__ cplx<Acc> up(const cplx<T>& v) {
+  return cplx<Acc>{Acc(v.re), Acc(v.im)};
+}
+
+template <typename Acc>
+__device__ __forceinline__ void cmac(cplx<Acc>& acc, const cplx<Acc>& a, const cplx<Acc>& b) {
+  acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(a.im, b.re, acc.im));
+}
+
+template <typename Acc> __device__ __forceinline__ Acc wsum(Acc v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// phase 1: t_b = V_b^T x_sigma
+// ---------------------------------------------------------------------------
+template <typename Op, typename X, typename Acc, int NRHS>
+__global__ void __launch_bounds__(256) k_hmv_t(const FarBlk* __restrict__ blks, const int* __restrict__ rank,
+                                               const Op* __restrict__ V, const X* __restrict__ x, long long N,
+                                               cplx<Acc>* __restrict__ t, int tstride) {
+  FarBlk B = blks[blockIdx.x];
+  int r = rank[blockIdx.x];
+  int n = 3 * B.nc;
+  const X* xs = x + 3LL * B.c0;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int l = warp; l < r; l += nw) {
+    const Op* col = V + B.voff + (long long)l * n;
+    cplx<Acc> acc[NRHS];
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) acc[q] = cplx<Acc>{0, 0};
+    for (int j = lane; j < n; j += 32) {
+      cplx<Acc> v = up<Acc>(col[j]);
+#pragma unroll
+      for (int q = 0; q < NRHS; ++q) cmac(acc[q], v, up<Acc>(xs[q * N + j]));
+    }
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      Acc re = wsum(acc[q].re), im = wsum(acc[q].im);
+      if (lane == 0) t[(long long)q * tstride + B.toff + l] = cplx<Acc>{re, im};
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// phase 2: rows of one leaf cluster
+// ---------------------------------------------------------------------------
+template <typename Op, typename X, typename Y, typename Acc, int NRHS>
+__global__ void __launch_bounds__(256) k_hmv_rows(const int* __restrict__ leaf_r0, const int* __restrict__ leaf_nr,
+                                                  const int* __restrict__ pptr, const Panel* __restrict__ panels,
+                                                  const FarBlk* __restrict__ far, const int* __restrict__ rank,
+                                                  const Op* __restrict__ near, const Op* __restrict__ U,
+                                                  const cplx<Acc>* __restrict__ t, int tstride,
+                                                  const X* __restrict__ x, long long N, Y* __restrict__ y) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<Acc>* red = reinterpret_cast<cplx<Acc>*>(smem_raw);
+  const int leaf = blockIdx.x;
+  const int rows = 3 * leaf_nr[leaf];
+  const long long row0 = 3LL * leaf_r0[leaf];
+  const int p0 = pptr[leaf], p1 = pptr[leaf + 1];
+  for (int rbase = 0; rbase < rows; rbase += blockDim.x) {
+    const int rcount = min(rows - rbase, (int)blockDim.x);
+    const int G = max(1, (int)blockDim.x / rcount);
+    const int g = threadIdx.x / rcount;
+    const int r = threadIdx.x % rcount + rbase;
+    const bool active = g < G;
+    cplx<Acc> acc[NRHS];
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) acc[q] = cplx<Acc>{0, 0};
+    if (active) {
+      for (int p = p0; p < p1; ++p) {
+        const Panel P = panels[p];
+        const long long ld = P.ld;
+        if (P.kind == 0) {
+          const Op* d = near + P.data + r;
+          const X* xs = x + P.xoff;
+          const int nc = P.ncols;
+          int j = g;
+          for (; j + 3 * G < nc; j += 4 * G) {
+            cplx<Acc> a0 = up<Acc>(d[(long long)j * ld]);
+            cplx<Acc> a1 = up<Acc>(d[(long long)(j + G) * ld]);
+            cplx<Acc> a2 = up<Acc>(d[(long long)(j + 2 * G) * ld]);
+            cplx<Acc> a3 = up<Acc>(d[(long long)(j + 3 * G) * ld]);
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q) {
+              const X* xq = xs + q * N;
+              cmac(acc[q], a0, up<Acc>(xq[j]));
+              cmac(acc[q], a1, up<Acc>(xq[j + G]));
+              cmac(acc[q], a2, up<Acc>(xq[j + 2 * G]));
+              cmac(acc[q], a3, up<Acc>(xq[j + 3 * G]));
+            }
+          }
+          for (; j < nc; j += G) {
+            cplx<Acc> a0 = up<Acc>(d[(long long)j * ld]);
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q) cmac(acc[q], a0, up<Acc>(xs[q * N + j]));
+          }
+        } else {
+          const int b = P.xoff;
+          const int nc = rank[b];
+          const Op* d = U + P.data + r;
+          const cplx<Acc>* ts = t + far[b].toff;
+          for (int j = g; j < nc; j += G) {
+            cplx<Acc> a0 = up<Acc>(d[(long long)j * ld]);
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q) cmac(acc[q], a0, ts[(long long)q * tstride + j]);
+          }
+        }
+      }
+    }
+    if (G > 1) {
+      if (active) {
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q) red[(q * G + g) * rcount + (r - rbase)] = acc[q];
+      }
+      __syncthreads();
+      if (active && g == 0) {
+        for (int gg = 1; gg < G; ++gg)
+#pragma unroll
+          for (int q = 0; q < NRHS; ++q) {
+            cplx<Acc> o = red[(q * G + gg) * rcount + (r - rbase)];
+            acc[q].re += o.re;
+            acc[q].im += o.im;
+          }
+      }
+      __syncthreads();
+    }
+    if (active && g == 0) {
+#pragma unroll
+      for (int q = 0; q < NRHS; ++q) {
+        Y o;
+        o.re = decltype(o.re)(acc[q].re);
+        o.im = decltype(o.im)(acc[q].im);
+        y[q * N + row0 + r] = o;
+      }
+    }
+  }
+}
+
+template <typename Op, typename X, typename Y, typename Acc, int NRHS>
+static void hmv_impl(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V, cplx<Acc>* t,
+                     const X* x, Y* y, cudaStream_t st) {
+  int nfar = (int)ctx->far_h.size();
+  if (count_if(nfar)) k_hmv_t<Op, X, Acc, NRHS><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, V, x, ctx->N, t,
+                                                            ctx->t_entries);
+  int threads = 256;
+  size_t sm = (size_t)threads * NRHS * sizeof(cplx<Acc>);
+  count_if(true);
+  k_hmv_rows<Op, X, Y, Acc, NRHS><<<ctx->nleaves, threads, sm, st>>>(
+      ctx->leaf_r0.p, ctx->leaf_nr.p, ctx->panel_ptr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t,
+      ctx->t_entries, x, ctx->N, y);
+}
+
+template <typename Op, typename X, typename Y, typename Acc>
+void launch_hmatvec(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V, cplx<Acc>* t, const X* x,
+                    Y* y, int nrhs, cudaStream_t st) {
+  switch (nrhs) {
+    case 1: hmv_impl<Op, X, Y, Acc, 1>(ctx, near, U, V, t, x, y, st); break;
+    case 2: hmv_impl<Op, X, Y, Acc, 2>(ctx, near, U, V, t, x, y, st); break;
+    case 3: hmv_impl<Op, X, Y, Acc, 3>(ctx, near, U, V, t, x, y, st); break;
+    default: hmv_impl<Op, X, Y, Acc, 4>(ctx, near, U, V, t, x, y, st); break;
+  }
+}
+
+template void launch_hmatvec<c64, c64, c64, float>(const bem_ctx*, const c64*, const c64*, const c64*,
+                                                   cplx<float>*, const c64*, c64*, int, cudaStream_t);
+template void launch_hmatvec<c64, c128, c128, double>(const bem_ctx*, const c64*, const c64*, const c64*,
+                                                      cplx<double>*, const c128*, c128*, int, cudaStream_t);
+template void launch_hmatvec<c128, c128, c128, double>(const bem_ctx*, const c128*, const c128*,
+                                                       const c128*, cplx<double>*, const c128*, c128*, int,
+                                                       cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// block-Jacobi preconditioner
+// ---------------------------------------------------------------------------
+template <typename Pm, typename V, typename Z>
+__global__ void k_precond(const Pm* __restrict__ pinv, const V* __restrict__ v, Z* __restrict__ z, int ne) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  using Acc = typename Promote<decltype(Pm{}.re), decltype(V{}.re)>::type;
+  cplx<Acc> ve[3];
+  for (int a = 0; a < 3; ++a) ve[a] = up<Acc>(v[3LL * e + a]);
+  for (int a = 0; a < 3; ++a) {
+    cplx<Acc> s{0, 0};
+    for (int b = 0; b < 3; ++b) cmac(s, up<Acc>(pinv[9LL * e + 3 * a + b]), ve[b]);
+    Z o;
+    o.re = decltype(o.re)(s.re);
+    o.im = decltype(o.im)(s.im);
+    z[3LL * e + a] = o;
+  }
+}
+template <typename Pm, typename V, typename Z>
+void launch_precond(const Pm* pinv, const V* v, Z* z, int ne, cudaStream_t st) {
+  count_if(true);
+  k_precond<Pm, V, Z><<<(ne + 127) / 128, 128, 0, st>>>(pinv, v, z, ne);
+}
+template void launch_precond<c64, c64, c64>(const c64*, const c64*, c64*, int, cudaStream_t);
+template void launch_precond<c128, c128, c128>(const c128*, const c128*, c128*, int, cudaStream_t);
+template void launch_precond<c128, c128, c64>(const c128*, const c128*, c64*, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Arnoldi pieces (FP64 accumulation)
+// ---------------------------------------------------------------------------
+template <typename Vb, typename W>
+__global__ void k_dots(const Vb* __restrict__ V, long long ldv, const W* __restrict__ w, long long n,
+                       c128* __restrict__ part) {
+  const int l = blockIdx.y;
+  const Vb* v = V + l * ldv;
+  double re = 0, im = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Vb a = v[i];
+    W b = w[i];
+    double ar = a.re, ai = a.im, br = b.re, bi = b.im;
+    re = fma(ar, br, fma(ai, bi, re));   // conj(a) * b
+    im = fma(ar, bi, fma(-ai, br, im));
+  }
+  re = wsum(re);
+  im = wsum(im);
+  __shared__ double s[2][32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s[0][wid] = re;
+    s[1][wid] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0, ti = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      tr += s[0][k];
+      ti += s[1][k];
+    }
+    part[(long long)l * gridDim.x + blockIdx.x] = c128{tr, ti};
+  }
+}
+template <typename Vb, typename W>
+int launch_dots(const Vb* V, long long ldv, int nvec, const W* w, long long n, c128* part, cudaStream_t st) {
+  int nblk = (int)std::min<long long>(std::max<long long>(1, n / 4096), 64);
+  dim3 grid(nblk, nvec);
+  count_if(true);
+  k_dots<Vb, W><<<grid, 256, 0, st>>>(V, ldv, w, n, part);
+  return nblk;
+}
+template int launch_dots<c64, c64>(const c64*, long long, int, const c64*, long long, c128*, cudaStream_t);
+template int launch_dots<c128, c128>(const c128*, long long, int, const c128*, long long, c128*, cudaStream_t);
+
+__global__ void k_dots_final(const c128* __restrict__ part, int nblk, c128* __restrict__ out) {
+  int l = blockIdx.x;
+  double re = 0, im = 0;
+  for (int k = threadIdx.x; k < nblk; k += 32) {
+    re += part[(long long)l * nblk + k].re;
+    im += part[(long long)l * nblk + k].im;
+  }
+  re = wsum(re);
+  im = wsum(im);
+  if (threadIdx.x == 0) out[l] = c128{re, im};
+}
+void launch_dots_final(const c128* part, int nblk, int nvec, c128* out, cudaStream_t st) {
+  count_if(true);
+  k_dots_final<<<nvec, 32, 0, st>>>(part, nblk, out);
+}
+
+template <typename Vb, typename W>
+__global__ void k_update(const Vb* __restrict__ V, long long ldv, int nvec, const c128* __restrict__ h,
+                         W* __restrict__ w, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double re = 0, im = 0;
+  for (int l = 0; l < nvec; ++l) {
+    Vb a = V[l * ldv + i];
+    c128 c = h[l];
+    re = fma((double)a.re, c.re, fma(-(double)a.im, c.im, re));
+    im = fma((double)a.re, c.im, fma((double)a.im, c.re, im));
+  }
+  W o = w[i];
+  o.re = decltype(o.re)((double)o.re - re);
+  o.im = decltype(o.im)((double)o.im - im);
+  w[i] = o;
+}
+template <typename Vb, typename W>
+void launch_update(const Vb* V, long long ldv, int nvec, const c128* h, W* w, long long n, cudaStream_t st) {
+  count_if(true);
+  k_update<Vb, W><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, ldv, nvec, h, w, n);
+}
+template void launch_update<c64, c64>(const c64*, long long, int, const c128*, c64*, long long, cudaStream_t);
+template void launch_update<c128, c128>(const c128*, long long, int, const c128*, c128*, long long,
+                                        cudaStream_t);
+
+template <typename W, typename Vb>
+__global__ void k_scale(const W* __restrict__ w, Vb* __restrict__ v, long long n, const double* __restrict__ nrm2) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = nrm2[0] > 0 ? 1.0 / sqrt(nrm2[0]) : 0.0;
+  W a = w[i];
+  Vb o;
+  o.re = decltype(o.re)(a.re * s);
+  o.im = decltype(o.im)(a.im * s);
+  v[i] = o;
+}
+template <typename W, typename Vb>
+void launch_scale(const W* w, Vb* v, long long n, const double* nrm2, cudaStream_t st) {
+  count_if(true);
+  k_scale<W, Vb><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w, v, n, nrm2);
+}
+template void launch_scale<c64, c64>(const c64*, c64*, long long, const double*, cudaStream_t);
+template void launch_scale<c128, c128>(const c128*, c128*, long long, const double*, cudaStream_t);
+
+__global__ void k_residual(const c128* __restrict__ b, const c128* __restrict__ y, c128* __restrict__ r, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  r[i] = c128{b[i].re - y[i].re, b[i].im - y[i].im};
+}
+void launch_residual(const c128* b, const c128* y, c128* r, long long n, cudaStream_t st) {
+  count_if(true);
+  k_residual<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b, y, r, n);
+}
+
+template <typename Vb>
+__global__ void k_combine(const Vb* __restrict__ V, long long ldv, int nvec, const c128* __restrict__ y,
+                          c128* __restrict__ out, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double re = 0, im = 0;
+  for (int l = 0; l < nvec; ++l) {
+    Vb a = V[l * ldv + i];
+    c128 c = y[l];
+    re = fma((double)a.re, c.re, fma(-(double)a.im, c.im, re));
+    im = fma((double)a.re, c.im, fma((double)a.im, c.re, im));
+  }
+  out[i] = c128{re, im};
+}
+template <typename Vb>
+void launch_combine(const Vb* V, long long ldv, int nvec, const c128* y, c128* out, long long n, cudaStream_t st) {
+  count_if(true);
+  k_combine<Vb><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, ldv, nvec, y, out, n);
+}
+template void launch_combine<c64>(const c64*, long long, int, const c128*, c128*, long long, cudaStream_t);
+template void launch_combine<c128>(const c128*, long long, int, const c128*, c128*, long long, cudaStream_t);
+
+__global__ void k_axpy(c128 a, const c128* __restrict__ x, c128* __restrict__ y, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  c128 v = x[i];
+  y[i] = c128{y[i].re + a.re * v.re - a.im * v.im, y[i].im + a.re * v.im + a.im * v.re};
+}
+void launch_axpy(c128 a, const c128* x, c128* y, long long n, cudaStream_t st) {
+  count_if(true);
+  k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, x, y, n);
+}
+
+template <typename O>
+__global__ void k_copy_cast(const c128* __restrict__ x, O* __restrict__ y, long long n, double s) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  O o;
+  o.re = decltype(o.re)(x[i].re * s);
+  o.im = decltype(o.im)(x[i].im * s);
+  y[i] = o;
+}
+void launch_copy_cast(const c128* x, c64* y, long long n, double scale, cudaStream_t st) {
+  count_if(true);
+  k_copy_cast<c64><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n, scale);
+}
+void launch_copy_cast(const c128* x, c128* y, long long n, double scale, cudaStream_t st) {
+  count_if(true);
+  k_copy_cast<c128><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n, scale);
+}
+
+// ---------------------------------------------------------------------------
+// modified Fourier transforms (FP64)
+// ---------------------------------------------------------------------------
+__global__ void k_load_dft(const double* __restrict__ P, int N, double T, double eta, c128* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N / 2) return;
+  double dt = T / N;
+  double re = 0, im = 0;
+  for (int n = 0; n < N; ++n) {
+    long long m = ((long long)n * k) % N;
+    double sn, cs;
+    sincospi(2.0 * (double)m / N, &sn, &cs);
+    double a = exp(-eta * n * dt) * P[n];
+    re += a * cs;
+    im -= a * sn;
+  }
+  out[k] = c128{re / N, im / N};
+}
+void launch_load_dft(const double* P, int n_omega, double T, double eta, c128* out, cudaStream_t st) {
+  int nf = n_omega / 2 + 1;
+  count_if(true);
+  k_load_dft<<<(nf + 127) / 128, 128, 0, st>>>(P, n_omega, T, eta, out);
+}
+
+// R(n dt) = e^{eta n dt} [W_0 Re R_0 + 2 Re sum_{k=1}^{N/2-1} W_k R_k e^{2 pi i n k/N}
+//                         + W_{N/2} Re(R_{N/2}) (-1)^n]
+__global__ void k_idft(const c128* __restrict__ spec, long long ldspec, const long long* __restrict__ idx,
+                       long long ndof, int N, double T, double eta, int window, double* __restrict__ out) {
+  extern __shared__ double tab[];  // cos, sin of 2 pi m / N, m < N
+  for (int m = threadIdx.x + threadIdx.y * blockDim.x; m < N; m += blockDim.x * blockDim.y) {
+    double sn, cs;
+    sincospi(2.0 * (double)m / N, &sn, &cs);
+    tab[2 * m] = cs;
+    tab[2 * m + 1] = sn;
+  }
+  __syncthreads();
+  long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (d >= ndof) return;
+  long long col = idx ? idx[d] : d;
+  const double dt = T / N;
+  auto W = [&](int k) -> double {
+    if (window == BEM_WIN_HANNING) return 0.5 * (1.0 + tab[2 * k]);
+    if (window == BEM_WIN_BLACKMAN) return 0.42 + 0.5 * tab[2 * k] + 0.08 * tab[2 * ((2 * k) % N)];
+    return 1.0;
+  };
+  for (int n = blockIdx.y * blockDim.y + threadIdx.y; n < N; n += gridDim.y * blockDim.y) {
+    double acc = W(0) * spec[col].re;
+    double sgn = (n & 1) ? -1.0 : 1.0;
+    acc += W(N / 2) * spec[(long long)(N / 2) * ldspec + col].re * sgn;
+    double s2 = 0;
+    int m = 0;
+    for (int k = 1; k < N / 2; ++k) {
+      m += n;
+      if (m >= N) m -= N;
+      c128 v = spec[(long long)k * ldspec + col];
+      s2 += W(k) * (v.re * tab[2 * m] - v.im * tab[2 * m + 1]);
+    }
+    acc += 2.0 * s2;
+    out[(long long)n * ndof + d] = exp(eta * n * dt) * acc;
+  }
+}
+void launch_idft(const c128* spec, long long ldspec, const long long* idx, long long ndof, int n_omega, double T,
+                 double eta, int window, double* out, cudaStream_t st) {
+  dim3 block(32, 8);
+  dim3 grid((unsigned)((ndof + 31) / 32), (unsigned)std::min(64, (n_omega + 7) / 8));
+  size_t sm = 2 * sizeof(double) * n_omega;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_idft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  count_if(true);
+  k_idft<<<grid, block, sm, st>>>(spec, ldspec, idx, ndof, n_omega, T, eta, window, out);
+}
+
+}  // namespace bem
