@@ -134,7 +134,14 @@ def _c128(a):
     return np.ascontiguousarray(a, dtype=np.complex128)
 
 
-def _tptr(t):
+def _tptr(t, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (checked: layout and dtype)."""
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and str(t.dtype) != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
     return ctypes.c_void_p(int(t.data_ptr()))
 
 
@@ -189,8 +196,11 @@ class Context:
         self.ne = tri.shape[0]
 
     def mesh_dev(self, xyz_t, tri_t, bc_t, opts: Opts | None = None):
-        self._check(self.lib.bem_mesh_dev(self.h, _tptr(xyz_t), xyz_t.shape[0], _tptr(tri_t), tri_t.shape[0],
-                                          _tptr(bc_t), ctypes.byref(opts) if opts else None))
+        if xyz_t.dim() != 2 or xyz_t.shape[1] != 3 or tri_t.dim() != 2 or tri_t.shape[1] != 3:
+            raise ValueError("xyz and tri must be (n, 3)")
+        self._check(self.lib.bem_mesh_dev(self.h, _tptr(xyz_t, "torch.float64"), xyz_t.shape[0],
+                                          _tptr(tri_t, "torch.int32"), tri_t.shape[0], _tptr(bc_t, "torch.int8"),
+                                          ctypes.byref(opts) if opts else None))
         self.ne = int(tri_t.shape[0])
 
     def set_material(self, E, nu, rho):
@@ -212,7 +222,8 @@ class Context:
 
     def solve_sweep_dev(self, T, n_omega, load_t, pattern_t, opts: Opts | None = None, allow_unconverged=False):
         stats = (FreqStats * (n_omega // 2 + 1))()
-        rc = self.lib.bem_solve_sweep_dev(self.h, float(T), int(n_omega), _tptr(load_t), _tptr(pattern_t),
+        rc = self.lib.bem_solve_sweep_dev(self.h, float(T), int(n_omega), _tptr(load_t, "torch.float64"),
+                                          _tptr(pattern_t, "torch.float64"),
                                           ctypes.byref(opts) if opts else None, stats)
         self._check(rc, allow=(-5,) if allow_unconverged else ())
         self.n_omega = n_omega
@@ -230,7 +241,10 @@ class Context:
         return out
 
     def time_response_dev(self, dofs_t, out_t):
-        self._check(self.lib.bem_time_response_dev(self.h, _tptr(dofs_t), dofs_t.numel(), _tptr(out_t)))
+        if out_t.numel() != self.n_omega * dofs_t.numel():
+            raise ValueError("out must hold n_omega x ndof values")
+        self._check(self.lib.bem_time_response_dev(self.h, _tptr(dofs_t, "torch.int64"), dofs_t.numel(),
+                                                   _tptr(out_t, "torch.float64")))
 
     # --- step-level entry points -------------------------------------------
     def load_dft(self, T, n_omega, eta, load_hist):

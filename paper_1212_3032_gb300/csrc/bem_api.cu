@@ -38,11 +38,7 @@ int fail_cuda(bem_ctx* ctx, cudaError_t e, const char* what, const char* file, i
   return e == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA;
 }
 
-// Gauss-Legendre nodes/weights on [0, 1] by Newton iteration on P_q; series
-// coefficients of the regular radial parts from the exponential series:
-//   Ah_m = (-1)^m [1/m! - 1/(m+1)! + 1/(m+2)!]
-//   Bh_m = (-1)^m [1/(m+2)! - 1/(m+1)!]
-//   Ch_m = (-1)^m [1/m! - 3/(m+1)! + 3/(m+2)!]
+// Gauss-Legendre nodes/weights on [0, 1] by Newton iteration on P_q.
 void make_rule_tables(RuleTables& t) {
   memset(&t, 0, sizeof(t));
   for (int q = 1; q <= GL_MAX; ++q) {
@@ -81,26 +77,20 @@ void make_rule_tables(RuleTables& t) {
       t.gl_w[q][i] = v[i].second;
     }
   }
-  long double fact[SERIES_TERMS + 3];
-  fact[0] = 1;
-  for (int k = 1; k < SERIES_TERMS + 3; ++k) fact[k] = fact[k - 1] * k;
-  long double a[SERIES_TERMS + 1], b[SERIES_TERMS + 1], c[SERIES_TERMS + 1];
-  for (int m = 0; m <= SERIES_TERMS; ++m) {
-    long double sg = (m % 2) ? -1 : 1;
-    a[m] = sg * (1 / fact[m] - 1 / fact[m + 1] + 1 / fact[m + 2]);
-    b[m] = sg * (1 / fact[m + 2] - 1 / fact[m + 1]);
-    c[m] = sg * (1 / fact[m] - 3 / fact[m + 1] + 3 / fact[m + 2]);
-  }
-  for (int m = 0; m < SERIES_TERMS; ++m) {
-    t.ser[0][m] = (double)a[m];
-    t.ser[1][m] = (double)b[m];
-    t.ser[2][m] = (double)c[m];
-    t.ser[3][m] = (double)((m + 1) * a[m + 1]);
-    t.ser[4][m] = (double)((m + 1) * b[m + 1]);
-    t.ser[5][m] = (double)((m + 1) * c[m + 1]);
-  }
+  for (int q = 0; q <= GL_MAX; ++q)
+    for (int i = 0; i < GL_MAX; ++i) {
+      t.gl_xf[q][i] = (float)t.gl_x[q][i];
+      t.gl_wf[q][i] = (float)t.gl_w[q][i];
+    }
 }
 
+// Taylor coefficients of Phi, Psi, A, B, C (see KParams). From the
+// exponential series, the regular parts of the bracketed functions are
+//   A(z) - 1/z^2 : a_m = (-1)^m [1/m! - 1/(m+1)! + 1/(m+2)!]
+//   B(z) - 1/z^2 : b_m = (-1)^m [1/(m+2)! - 1/(m+1)!]
+//   C(z) - 3/z^2 : c_m = (-1)^m [1/m! - 3/(m+1)! + 3/(m+2)!]
+// and with gamma = c_s / c_p, beta2 = gamma^2, k2 = 1 / gamma^2:
+//   phi_m = a_m - gamma^(m+2) b_m,  psi_m = c_m (1 - gamma^(m+2)).
 template <typename R> KParams<R> make_params(const bem_ctx* ctx, double sre, double sim) {
   KParams<R> P;
   std::complex<double> s(sre, sim);
@@ -115,6 +105,26 @@ template <typename R> KParams<R> make_params(const bem_ctx* ctx, double sre, dou
   P.nu = R(ctx->nu);
   P.kel_u = R(1.0 / (16.0 * M_PI * ctx->mu * (1.0 - ctx->nu)));
   P.kel_t = R(1.0 / (8.0 * M_PI * (1.0 - ctx->nu)));
+  long double g = (long double)ctx->cs / (long double)ctx->cp;
+  long double k2 = 1.0L / (g * g);
+  long double fact[SER_MAX + 3];
+  fact[0] = 1;
+  for (int k = 1; k < SER_MAX + 3; ++k) fact[k] = fact[k - 1] * k;
+  long double gp = g * g;  // gamma^(m+2)
+  for (int m = 0; m < SER_MAX; ++m) {
+    long double sg = (m % 2) ? -1 : 1;
+    long double am = sg * (1 / fact[m] - 1 / fact[m + 1] + 1 / fact[m + 2]);
+    long double bm = sg * (1 / fact[m + 2] - 1 / fact[m + 1]);
+    long double cm = sg * (1 / fact[m] - 3 / fact[m + 1] + 3 / fact[m + 2]);
+    long double ph = am - gp * bm;
+    long double ps = cm * (1 - gp);
+    P.ser[0][m] = R(ph);
+    P.ser[1][m] = R(ps);
+    P.ser[2][m] = R((m - 1) * ph - ps);
+    P.ser[3][m] = R(2 * (3 - m) * ps);
+    P.ser[4][m] = R(k2 * ((m - 1) * ph - (m + 1) * ps) - 2 * ((m - 1) * ph - m * ps));
+    gp *= g;
+  }
   return P;
 }
 
@@ -509,6 +519,40 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
     pan.insert(pan.end(), per[l].begin(), per[l].end());
   }
   pptr[L] = (int)pan.size();
+  // tasks: runs of at most ~TASK_COLS stored columns of one leaf row (the far
+  // panels counted at their rank cap), so that there are several CTAs per SM
+  const int TASK_COLS = 576;
+  std::vector<Task> tk;
+  std::vector<int> tptr(L + 1, 0);
+  long long slot = 0;
+  for (int l = 0; l < L; ++l) {
+    tptr[l] = (int)tk.size();
+    int p = pptr[l];
+    while (p < pptr[l + 1]) {
+      Task t;
+      t.leaf = l;
+      t.p0 = p;
+      t.slot = (int)slot;
+      int cols = 0;
+      do {
+        const Panel& P = pan[p];
+        cols += P.kind == 0 ? P.ncols : ctx->far_h[P.xoff].rmax;
+        ++p;
+      } while (p < pptr[l + 1] && cols < TASK_COLS);
+      t.p1 = p;
+      slot += 3LL * nr[l];
+      tk.push_back(t);
+    }
+  }
+  tptr[L] = (int)tk.size();
+  ctx->ntasks = (int)tk.size();
+  ctx->part_rows = slot;
+  BEM_CUDA_TRY(ctx->tasks.alloc(std::max<size_t>(1, tk.size())));
+  BEM_CUDA_TRY(ctx->task_ptr.alloc(L + 1));
+  BEM_CUDA_TRY(ctx->part.alloc(std::max<long long>(1, 8 * slot)));  // 4 rhs x complex FP64
+  if (!tk.empty())
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->tasks.p, tk.data(), tk.size() * sizeof(Task), cudaMemcpyHostToDevice, st));
+  BEM_CUDA_TRY(cudaMemcpyAsync(ctx->task_ptr.p, tptr.data(), (L + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
   BEM_CUDA_TRY(ctx->leaf_r0.alloc(L));
   BEM_CUDA_TRY(ctx->leaf_nr.alloc(L));
   BEM_CUDA_TRY(ctx->panel_ptr.alloc(L + 1));
@@ -518,6 +562,26 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   BEM_CUDA_TRY(cudaMemcpyAsync(ctx->panel_ptr.p, pptr.data(), (L + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
   if (!pan.empty())
     BEM_CUDA_TRY(cudaMemcpyAsync(ctx->panels.p, pan.data(), pan.size() * sizeof(Panel), cudaMemcpyHostToDevice, st));
+
+  // admissible blocks: small ones (one warp each) and large ones (one CTA each)
+  {
+    std::vector<int> sm_l, lg_l;
+    for (size_t b = 0; b < ctx->far_h.size(); ++b) {
+      const FarBlk& fb = ctx->far_h[b];
+      (fb.nr + fb.nc <= 256 ? sm_l : lg_l).push_back((int)b);
+    }
+    ctx->nfar_small = (int)sm_l.size();
+    ctx->nfar_large = (int)lg_l.size();
+    BEM_CUDA_TRY(ctx->far_small.alloc(std::max<size_t>(1, sm_l.size())));
+    BEM_CUDA_TRY(ctx->far_large.alloc(std::max<size_t>(1, lg_l.size())));
+    if (!sm_l.empty())
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->far_small.p, sm_l.data(), sm_l.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!lg_l.empty())
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->far_large.p, lg_l.data(), lg_l.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
+  BEM_CUDA_TRY(ctx->polar.alloc(27LL * ne));
+  launch_polar(ctx->ed.p, ne, ctx->polar.p, st);
+  CK("polar");
 
   // singular and near-singular pairs of the near blocks
   int nnb = (int)ctx->near_h.size();
@@ -627,15 +691,16 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
     BEM_CUDA_TRY(ctx->t32.ensure(4LL * std::max(1, ctx->t_entries)));
     BEM_CUDA_TRY(ctx->t64.ensure(4LL * std::max(1, ctx->t_entries)));
     BEM_CUDA_TRY(ctx->prec_inv32.ensure(9LL * ctx->ne));
-    launch_sing<c64>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->bc.p, ctx->sing_static.p, Pd, ctx->near32.p,
-                     ctx->prec_inv.p, pattern_tree, pk, b, status.p, st);
-    CK("sing");
     KParams<float> Pf = make_params<float>(ctx, sre, sim);
+    launch_sing<float, c64>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pf,
+                            ctx->near32.p, ctx->prec_inv.p, pattern_tree, pk, b, status.p, st);
+    CK("sing");
     launch_near_regular<float, c64>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf,
                                     ctx->near32.p, st);
     CK("near_regular");
-    launch_aca<float, c64>(ctx->far_d.p, (int)nf, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, ctx->u32.p, ctx->v32.p,
-                           ctx->rank.p, ctx->aca_fail.p, o.aca_tol, st);
+    launch_aca<float, c64>(ctx->far_d.p, ctx->far_small.p, ctx->nfar_small, ctx->far_large.p, ctx->nfar_large,
+                           ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, ctx->u32.p, ctx->v32.p, ctx->rank.p, ctx->aca_fail.p,
+                           o.aca_tol, st);
     CK("aca");
     long long n9 = 9LL * ctx->ne;
     count_if(true);
@@ -646,14 +711,15 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
     BEM_CUDA_TRY(ctx->u64.ensure(std::max<long long>(1, ctx->u_entries)));
     BEM_CUDA_TRY(ctx->v64.ensure(std::max<long long>(1, ctx->v_entries)));
     BEM_CUDA_TRY(ctx->t64.ensure(4LL * std::max(1, ctx->t_entries)));
-    launch_sing<c128>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->bc.p, ctx->sing_static.p, Pd, ctx->near64.p,
-                      ctx->prec_inv.p, pattern_tree, pk, b, status.p, st);
+    launch_sing<double, c128>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pd,
+                              ctx->near64.p, ctx->prec_inv.p, pattern_tree, pk, b, status.p, st);
     CK("sing");
     launch_near_regular<double, c128>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd,
                                       ctx->near64.p, st);
     CK("near_regular");
-    launch_aca<double, c128>(ctx->far_d.p, (int)nf, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd, ctx->u64.p, ctx->v64.p,
-                             ctx->rank.p, ctx->aca_fail.p, o.aca_tol, st);
+    launch_aca<double, c128>(ctx->far_d.p, ctx->far_small.p, ctx->nfar_small, ctx->far_large.p, ctx->nfar_large,
+                             ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd, ctx->u64.p, ctx->v64.p, ctx->rank.p,
+                             ctx->aca_fail.p, o.aca_tol, st);
     CK("aca");
   }
   prof_end(ctx, ev, 1, 0.0);
@@ -1072,13 +1138,13 @@ extern "C" int bem_rhs(bem_ctx* ctx, double p_re, double p_im, const double* pat
     KParams<float> Pf = make_params<float>(ctx, ctx->s_re, ctx->s_im);
     launch_rhs<float>(ctx->ne, ctx->loaded.p, ctx->nloaded, ctx->ef.p, ctx->ed.p, ctx->bc.p, ctx->pattern.p, Pf, pk,
                       bd.p, ctx->stream);
-    launch_sing<c64>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->bc.p, ctx->sing_static.p, Pd, nullptr, nullptr,
-                     ctx->pattern.p, pk, bd.p, ctx->status.p, ctx->stream);
+    launch_sing<float, c64>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pf,
+                            nullptr, nullptr, ctx->pattern.p, pk, bd.p, ctx->status.p, ctx->stream);
   } else {
     launch_rhs<double>(ctx->ne, ctx->loaded.p, ctx->nloaded, ctx->ef.p, ctx->ed.p, ctx->bc.p, ctx->pattern.p, Pd, pk,
                        bd.p, ctx->stream);
-    launch_sing<c128>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->bc.p, ctx->sing_static.p, Pd, nullptr, nullptr,
-                      ctx->pattern.p, pk, bd.p, ctx->status.p, ctx->stream);
+    launch_sing<double, c128>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pd,
+                              nullptr, nullptr, ctx->pattern.p, pk, bd.p, ctx->status.p, ctx->stream);
   }
   CK("rhs");
   std::vector<c128> bt(ctx->N);

@@ -451,7 +451,32 @@ __global__ void __launch_bounds__(256) k_near_regular(const NearBlk* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// singular + near-singular entries (FP64): one warp per pair
+// polar parameters of the self rule: per element, per triangle (c, p_k, p_k+1):
+// d, fh[3], gh[3], theta_a, dtheta (once per mesh, FP64)
+// ---------------------------------------------------------------------------
+__global__ void k_polar(const ElemD* __restrict__ ed, int ne, double* __restrict__ out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const ElemD& E = ed[e];
+  for (int sub = 0; sub < 3; ++sub) {
+    PolarSub S = polar_sub(E.c, vtx(E, sub), vtx(E, (sub + 1) % 3), E.n);
+    double* o = out + 27LL * e + 9 * sub;
+    o[0] = S.d;
+    for (int a = 0; a < 3; ++a) {
+      o[1 + a] = S.fh[a];
+      o[4 + a] = S.gh[a];
+    }
+    o[7] = S.tha;
+    o[8] = S.dth;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// singular + near-singular entries: one warp per pair.
+//   entry = static Kelvin part (FP64, once per mesh) + dynamic remainder
+//   (self: polar 8 x 6 per triangle; near: collapsed 4x4), the remainder
+//   evaluated cancellation-free in R (FP32 on the mixed path, FP64 plain).
+// Also: block-Jacobi inverses (FP64) and the pairs' right-hand-side share.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool inv3(const c128* A, c128* Ai) {
   // cofactor inverse of a complex 3x3 (row-major)
@@ -473,11 +498,17 @@ __device__ __forceinline__ bool inv3(const c128* A, c128* Ai) {
   return true;
 }
 
-template <typename Op>
+template <typename R> __device__ __forceinline__ R wred(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename R, typename Op>
 __global__ void k_sing(const SingPair* __restrict__ pairs, int npairs, const ElemD* __restrict__ ed,
-                       const signed char* __restrict__ bc, const double* __restrict__ stat,
-                       KParams<double> P, Op* __restrict__ near, c128* __restrict__ pinv,
-                       const double* __restrict__ pattern, c128 pk, c128* __restrict__ b,
+                       const double* __restrict__ polar, const signed char* __restrict__ bc,
+                       const double* __restrict__ stat, KParams<R> P, Op* __restrict__ near,
+                       c128* __restrict__ pinv, const double* __restrict__ pattern, c128 pk, c128* __restrict__ b,
                        int* __restrict__ status) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
@@ -485,54 +516,53 @@ __global__ void k_sing(const SingPair* __restrict__ pairs, int npairs, const Ele
   SingPair sp = pairs[warp];
   const ElemD& E = ed[sp.e];
   const ElemD& I = ed[sp.i];
-  UTAcc<double> acc;
+  R n[3] = {R(E.n[0]), R(E.n[1]), R(E.n[2])};
+  UTAcc<R> acc;
   acc.zero();
   if (sp.self) {
     for (int q = lane; q < 3 * SELF_NT * SELF_NR; q += 32) {
       int sub = q / (SELF_NT * SELF_NR);
       int m = (q / SELF_NR) % SELF_NT, l = q % SELF_NR;
-      PolarSub S = polar_sub(E.c, vtx(E, sub), vtx(E, (sub + 1) % 3), E.n);
-      double th = S.tha + S.dth * gl_x<double>(SELF_NT, m);
-      double wth = S.dth * gl_w<double>(SELF_NT, m);
-      double sn, cs;
-      sincos(th, &sn, &cs);
-      double R = S.d / cs;
-      double r = R * gl_x<double>(SELF_NR, l);
-      double w = wth * R * gl_w<double>(SELF_NR, l) * r;
-      double rv[3];
-      for (int a = 0; a < 3; ++a) rv[a] = r * (cs * S.fh[a] + sn * S.gh[a]);
-      accumulate_point<double>(acc, rv[0], rv[1], rv[2], E.n[0], E.n[1], E.n[2], w, P);
-      subtract_kelvin(acc, rv[0], rv[1], rv[2], E.n[0], E.n[1], E.n[2], w, P);
+      const double* ps = polar + 27LL * sp.e + 9 * sub;
+      R d = R(ps[0]), tha = R(ps[7]), dth = R(ps[8]);
+      R th = tha + dth * gl_x<R>(SELF_NT, m);
+      R wth = dth * gl_w<R>(SELF_NT, m);
+      R sn, cs;
+      sincos_r(th, &sn, &cs);
+      R Rr = d / cs;
+      R r = Rr * gl_x<R>(SELF_NR, l);
+      R w = wth * Rr * gl_w<R>(SELF_NR, l) * r;
+      R rv[3];
+      for (int a = 0; a < 3; ++a) rv[a] = r * (cs * R(ps[1 + a]) + sn * R(ps[4 + a]));
+      accumulate_point<R, false>(acc, rv[0], rv[1], rv[2], n[0], n[1], n[2], w, P);
     }
   } else if (lane < NEAR_Q_REM * NEAR_Q_REM) {
     int ia = lane / NEAR_Q_REM, ib = lane % NEAR_Q_REM;
-    double u = gl_x<double>(NEAR_Q_REM, ia), v = (1.0 - u) * gl_x<double>(NEAR_Q_REM, ib);
-    double w = E.area2 * gl_w<double>(NEAR_Q_REM, ia) * gl_w<double>(NEAR_Q_REM, ib) * (1.0 - u);
-    double rv[3];
+    R u = gl_x<R>(NEAR_Q_REM, ia), v = (R(1) - u) * gl_x<R>(NEAR_Q_REM, ib);
+    R w = R(E.area2) * gl_w<R>(NEAR_Q_REM, ia) * gl_w<R>(NEAR_Q_REM, ib) * (R(1) - u);
+    R rv[3];
     for (int k = 0; k < 3; ++k)
-      rv[k] = E.p0[k] + u * (E.p1[k] - E.p0[k]) + v * (E.p2[k] - E.p0[k]) - I.c[k];
-    accumulate_point<double>(acc, rv[0], rv[1], rv[2], E.n[0], E.n[1], E.n[2], w, P);
-    subtract_kelvin(acc, rv[0], rv[1], rv[2], E.n[0], E.n[1], E.n[2], w, P);
+      rv[k] = R(E.p0[k] - I.c[k]) + u * R(E.p1[k] - E.p0[k]) + v * R(E.p2[k] - E.p0[k]);
+    accumulate_point<R, false>(acc, rv[0], rv[1], rv[2], n[0], n[1], n[2], w, P);
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    acc.u[k].re = warp_sum(acc.u[k].re);
-    acc.u[k].im = warp_sum(acc.u[k].im);
+    acc.u[k].re = wred(acc.u[k].re);
+    acc.u[k].im = wred(acc.u[k].im);
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    acc.t[k].re = warp_sum(acc.t[k].re);
-    acc.t[k].im = warp_sum(acc.t[k].im);
+    acc.t[k].re = wred(acc.t[k].re);
+    acc.t[k].im = wred(acc.t[k].im);
   }
   if (lane != 0) return;
   const double* st = stat + 18 * (long long)warp;
   c128 U[9], T[9];
   for (int a = 0; a < 3; ++a)
     for (int c = 0; c < 3; ++c) {
-      U[3 * a + c] = acc.U(a, c);
-      U[3 * a + c].re += st[3 * a + c];
-      T[3 * a + c] = acc.t[3 * a + c];
-      T[3 * a + c].re += st[9 + 3 * a + c];
+      cplx<R> uu = acc.U(a, c), tt = acc.t[3 * a + c];
+      U[3 * a + c] = c128{(double)uu.re + st[3 * a + c], (double)uu.im};
+      T[3 * a + c] = c128{(double)tt.re + st[9 + 3 * a + c], (double)tt.im};
     }
   if (sp.self)
     for (int a = 0; a < 3; ++a) T[4 * a].re += 0.5;  // free term c_ij = delta_ij / 2
@@ -566,12 +596,32 @@ __global__ void k_sing(const SingPair* __restrict__ pairs, int npairs, const Ele
 }
 
 // ---------------------------------------------------------------------------
-// right-hand side over regular pairs, on the fly: one warp per row element
+// right-hand side over regular pairs, on the fly: one warp per row element.
+// Traction-loaded columns need U only (B = U); displacement-loaded columns
+// need T (B = -T).
 // ---------------------------------------------------------------------------
+template <typename R, int Q>
+__device__ __forceinline__ void integrate_collapsed_u(cplx<R>* u, const R* o0, const R* e1, const R* e2, R area2,
+                                                      const KParams<R>& P) {
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    R uu = gl_x<R>(Q, a), wu = gl_w<R>(Q, a);
+    R omu = R(1) - uu;
+#pragma unroll
+    for (int bq = 0; bq < Q; ++bq) {
+      R v = omu * gl_x<R>(Q, bq);
+      R w = area2 * wu * gl_w<R>(Q, bq) * omu;
+      accumulate_point_u<R>(u, o0[0] + uu * e1[0] + v * e2[0], o0[1] + uu * e1[1] + v * e2[1],
+                            o0[2] + uu * e1[2] + v * e2[2], w, P);
+    }
+  }
+}
+
 template <typename R>
-__global__ void k_rhs(int ne, const int* __restrict__ loaded, int nloaded, const ElemF* __restrict__ ef,
-                      const ElemD* __restrict__ ed, const signed char* __restrict__ bc,
-                      const double* __restrict__ pattern, KParams<R> P, c128 pk, c128* __restrict__ b) {
+__global__ void __launch_bounds__(256) k_rhs(int ne, const int* __restrict__ loaded, int nloaded,
+                                             const ElemF* __restrict__ ef, const ElemD* __restrict__ ed,
+                                             const signed char* __restrict__ bc, const double* __restrict__ pattern,
+                                             KParams<R> P, c128 pk, c128* __restrict__ b) {
   int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (i >= ne) return;
@@ -582,15 +632,28 @@ __global__ void k_rhs(int ne, const int* __restrict__ loaded, int nloaded, const
     int band;
     pair_geo(ef, ed, i, e, g, band);
     if (band == BAND_SELF || band == BAND_NEAR) continue;
-    UTAcc<R> acc;
-    regular_pair<R>(acc, g, band, P);
-    bool trac = bc[e] == BEM_BC_TRACTION;
     const double* pt = pattern + 3 * (long long)e;
-    for (int a = 0; a < 3; ++a)
-      for (int c = 0; c < 3; ++c) {
-        cplx<R> Bv = trac ? acc.U(a, c) : -acc.t[3 * a + c];
-        cfmr(s[a], Bv, R(pt[c]));
-      }
+    R p3[3] = {R(pt[0]), R(pt[1]), R(pt[2])};
+    if (bc[e] == BEM_BC_TRACTION) {
+      cplx<R> u[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) u[k] = mk<R>(0, 0);
+      if (band == BAND_Q4) integrate_collapsed_u<R, 4>(u, g.o0, g.e1, g.e2, g.area2, P);
+      else if (band == BAND_Q2) integrate_collapsed_u<R, 2>(u, g.o0, g.e1, g.e2, g.area2, P);
+      else accumulate_point_u<R>(u, g.d[0], g.d[1], g.d[2], R(0.5) * g.area2, P);
+      const int idx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cfmr(s[a], u[idx[a][c]], p3[c]);
+    } else {
+      UTAcc<R> acc;
+      regular_pair<R>(acc, g, band, P);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cfmr(s[a], -acc.t[3 * a + c], p3[c]);
+    }
   }
   for (int a = 0; a < 3; ++a) {
     double re = warp_sum((double)s[a].re), im = warp_sum((double)s[a].im);
@@ -600,18 +663,35 @@ __global__ void k_rhs(int ne, const int* __restrict__ loaded, int nloaded, const
 
 // ---------------------------------------------------------------------------
 // ACA with partial pivoting: one CTA per admissible block
+//   residual row i* -> v_k (scaled by the pivot), residual column j* -> u_k,
+//   ||S_k||_F^2 = ||S_{k-1}||_F^2 + 2 Re sum_{l<k} (u_l^H u_k)(v_l^H v_k) + |u_k|^2 |v_k|^2,
+//   stop when |u_k| |v_k| <= eps ||S_k||_F or at the rank cap.
+// Norms are accumulated in the storage precision (FP32 on the mixed path).
 // ---------------------------------------------------------------------------
-template <typename R> struct BlockRed {
-  double v[32];
-  int idx[32];
+constexpr int ACA_THREADS = 128;
+constexpr int ACA_WARPS = ACA_THREADS / 32;
+constexpr int ACA_RMAX = 128;
+
+template <typename T> struct AcaShared {
+  T dot[4][ACA_RMAX + 1][ACA_WARPS];  // ur, ui, vr, vi partials per column l and warp
+  T amax[ACA_WARPS];
+  int aidx[ACA_WARPS];
+  T scal[4];
+  int rows_used[ACA_RMAX];
 };
 
-// block-wide max |value| with index (ties -> smaller index)
-__device__ __forceinline__ void block_argmax(double& v, int& idx, BlockRed<double>& sh) {
+template <typename T> __device__ __forceinline__ T wsumT(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide max with index (ties -> smaller index); result valid in all threads
+template <typename T> __device__ __forceinline__ void aca_argmax(T& v, int& idx, AcaShared<T>& sh) {
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    T ov = __shfl_xor_sync(0xffffffffu, v, o);
     int oi = __shfl_xor_sync(0xffffffffu, idx, o);
     if (ov > v || (ov == v && oi < idx)) {
       v = ov;
@@ -620,55 +700,42 @@ __device__ __forceinline__ void block_argmax(double& v, int& idx, BlockRed<doubl
   }
   __syncthreads();
   if (lane == 0) {
-    sh.v[wid] = v;
-    sh.idx[wid] = idx;
+    sh.amax[wid] = v;
+    sh.aidx[wid] = idx;
   }
   __syncthreads();
-  v = sh.v[0];
-  idx = sh.idx[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-    if (sh.v[w] > v || (sh.v[w] == v && sh.idx[w] < idx)) {
-      v = sh.v[w];
-      idx = sh.idx[w];
+  v = sh.amax[0];
+  idx = sh.aidx[0];
+  for (int w = 1; w < ACA_WARPS; ++w)
+    if (sh.amax[w] > v || (sh.amax[w] == v && sh.aidx[w] < idx)) {
+      v = sh.amax[w];
+      idx = sh.aidx[w];
     }
 }
 
-__device__ __forceinline__ double block_sum(double v, BlockRed<double>& sh) {
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) sh.v[wid] = v;
-  __syncthreads();
-  double t = 0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh.v[w];
-  return t;
-}
-
 template <typename R, typename Op>
-__global__ void __launch_bounds__(256) k_aca(const FarBlk* __restrict__ blks, const ElemF* __restrict__ ef,
-                                             const ElemD* __restrict__ ed,
-                                             const signed char* __restrict__ bc, KParams<R> P,
-                                             Op* __restrict__ Ustore, Op* __restrict__ Vstore,
-                                             int* __restrict__ rank, int* __restrict__ fails,
-                                             double eps) {
+__global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ list, const FarBlk* __restrict__ blks,
+                                                     const ElemF* __restrict__ ef,
+                                                     const ElemD* __restrict__ ed,
+                                                     const signed char* __restrict__ bc, KParams<R> P,
+                                                     Op* __restrict__ Ustore, Op* __restrict__ Vstore,
+                                                     int* __restrict__ rank, int* __restrict__ fails, double eps_d) {
   using T = decltype(Op{}.re);
-  FarBlk B = blks[blockIdx.x];
+  const T eps = T(eps_d);
+  const int bi = list[blockIdx.x];
+  FarBlk B = blks[bi];
   const int m = 3 * B.nr, n = 3 * B.nc;
   Op* Ub = Ustore + B.uoff;
   Op* Vb = Vstore + B.voff;
-  __shared__ BlockRed<double> red;
-  __shared__ Op sU[256];   // U[i*, l] for l < k  (rmax <= 256)
-  __shared__ Op sV[256];   // V[j*, l]
-  __shared__ int rows_used[256];
-  const int rmax = min(B.rmax, 256);
+  __shared__ AcaShared<T> sh;
+  const int rmax = min(B.rmax, ACA_RMAX);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int k = 0;
   int istar = 0;
-  double normS2 = 0.0;
+  T normS2 = 0;
   bool converged = false;
   while (k < rmax) {
     // --- residual row istar -> V[:, k]
-    for (int l = threadIdx.x; l < k; l += blockDim.x) sU[l] = Ub[(long long)l * m + istar];
-    __syncthreads();
     int ie = B.r0 + istar / 3, ia = istar % 3;
     for (int el = threadIdx.x; el < B.nc; el += blockDim.x) {
       int e = B.c0 + el;
@@ -678,30 +745,31 @@ __global__ void __launch_bounds__(256) k_aca(const FarBlk* __restrict__ blks, co
       UTAcc<R> acc;
       regular_pair<R>(acc, g, band, P);
       bool trac = bc[e] == BEM_BC_TRACTION;
+#pragma unroll
       for (int c = 0; c < 3; ++c) {
         cplx<R> v = trac ? acc.t[3 * ia + c] : -acc.U(ia, c);
         int j = 3 * el + c;
         cplx<T> vv = mk<T>(T(v.re), T(v.im));
         for (int l = 0; l < k; ++l) {
-          Op ul = sU[l], vl = Vb[(long long)l * n + j];
+          Op ul = Ub[(long long)l * m + istar], vl = Vb[(long long)l * n + j];
           vv = vv - mk<T>(ul.re, ul.im) * mk<T>(vl.re, vl.im);
         }
         Vb[(long long)k * n + j] = to_op<Op>(vv);
       }
     }
     __syncthreads();
-    double best = -1.0;
+    T best = T(-1);
     int jstar = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       Op v = Vb[(long long)k * n + j];
-      double a = (double)v.re * v.re + (double)v.im * v.im;
+      T a = v.re * v.re + v.im * v.im;
       if (a > best) {
         best = a;
         jstar = j;
       }
     }
-    block_argmax(best, jstar, red);
-    if (!(best > 0.0)) {
+    aca_argmax(best, jstar, sh);
+    if (!(best > T(0))) {
       converged = true;  // zero residual row: the block is represented exactly
       break;
     }
@@ -712,9 +780,8 @@ __global__ void __launch_bounds__(256) k_aca(const FarBlk* __restrict__ blks, co
       Op v = Vb[(long long)k * n + j];
       Vb[(long long)k * n + j] = to_op<Op>(mk<T>(v.re, v.im) * ipiv);
     }
-    // --- residual column jstar -> U[:, k]
-    for (int l = threadIdx.x; l < k; l += blockDim.x) sV[l] = Vb[(long long)l * n + jstar];
     __syncthreads();
+    // --- residual column jstar -> U[:, k]
     int je = B.c0 + jstar / 3, jc = jstar % 3;
     bool trac = bc[je] == BEM_BC_TRACTION;
     for (int il = threadIdx.x; il < B.nr; il += blockDim.x) {
@@ -724,73 +791,90 @@ __global__ void __launch_bounds__(256) k_aca(const FarBlk* __restrict__ blks, co
       pair_geo(ef, ed, i, je, g, band);
       UTAcc<R> acc;
       regular_pair<R>(acc, g, band, P);
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
         cplx<R> v = trac ? acc.t[3 * a + jc] : -acc.U(a, jc);
         int ii = 3 * il + a;
         cplx<T> vv = mk<T>(T(v.re), T(v.im));
         for (int l = 0; l < k; ++l) {
-          Op ul = Ub[(long long)l * m + ii], vl = sV[l];
+          Op ul = Ub[(long long)l * m + ii], vl = Vb[(long long)l * n + jstar];
           vv = vv - mk<T>(ul.re, ul.im) * mk<T>(vl.re, vl.im);
         }
         Ub[(long long)k * m + ii] = to_op<Op>(vv);
       }
     }
-    if (threadIdx.x == 0) rows_used[k] = istar;
+    if (threadIdx.x == 0) sh.rows_used[k] = istar;
     __syncthreads();
     // earlier pivot rows are exactly represented already: their residual is zero
-    for (int l = threadIdx.x; l < k; l += blockDim.x) Ub[(long long)k * m + rows_used[l]] = Op{};
+    for (int l = threadIdx.x; l < k; l += blockDim.x) Ub[(long long)k * m + sh.rows_used[l]] = Op{};
     __syncthreads();
-    // --- norms: ||S_k||^2 = ||S_{k-1}||^2 + 2 Re sum_l (u_l^H u_k)(v_l^H v_k) + |u_k|^2 |v_k|^2
-    double nu2 = 0, nv2 = 0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      Op u = Ub[(long long)k * m + i];
-      nu2 += (double)u.re * u.re + (double)u.im * u.im;
-    }
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      Op v = Vb[(long long)k * n + j];
-      nv2 += (double)v.re * v.re + (double)v.im * v.im;
-    }
-    nu2 = block_sum(nu2, red);
-    nv2 = block_sum(nv2, red);
-    double cross = 0.0;
-    for (int l = 0; l < k; ++l) {
-      double ur = 0, ui = 0, vr = 0, vi = 0;
+    // --- all inner products u_l^H u_k, v_l^H v_k (l <= k) in one pass
+    for (int l = 0; l <= k; ++l) {
+      T ur = 0, ui = 0, vr = 0, vi = 0;
       for (int i = threadIdx.x; i < m; i += blockDim.x) {
         Op a = Ub[(long long)l * m + i], b2 = Ub[(long long)k * m + i];
-        ur += (double)a.re * b2.re + (double)a.im * b2.im;
-        ui += (double)a.re * b2.im - (double)a.im * b2.re;
+        ur += a.re * b2.re + a.im * b2.im;
+        ui += a.re * b2.im - a.im * b2.re;
       }
       for (int j = threadIdx.x; j < n; j += blockDim.x) {
         Op a = Vb[(long long)l * n + j], b2 = Vb[(long long)k * n + j];
-        vr += (double)a.re * b2.re + (double)a.im * b2.im;
-        vi += (double)a.re * b2.im - (double)a.im * b2.re;
+        vr += a.re * b2.re + a.im * b2.im;
+        vi += a.re * b2.im - a.im * b2.re;
       }
-      ur = block_sum(ur, red);
-      ui = block_sum(ui, red);
-      vr = block_sum(vr, red);
-      vi = block_sum(vi, red);
-      cross += ur * vr - ui * vi;
+      ur = wsumT(ur);
+      ui = wsumT(ui);
+      vr = wsumT(vr);
+      vi = wsumT(vi);
+      if (lane == 0) {
+        sh.dot[0][l][wid] = ur;
+        sh.dot[1][l][wid] = ui;
+        sh.dot[2][l][wid] = vr;
+        sh.dot[3][l][wid] = vi;
+      }
     }
-    normS2 += 2.0 * cross + nu2 * nv2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T cross = 0, nu2 = 0, nv2 = 0;
+      for (int l = 0; l <= k; ++l) {
+        T ur = 0, ui = 0, vr = 0, vi = 0;
+        for (int w = 0; w < ACA_WARPS; ++w) {
+          ur += sh.dot[0][l][w];
+          ui += sh.dot[1][l][w];
+          vr += sh.dot[2][l][w];
+          vi += sh.dot[3][l][w];
+        }
+        if (l < k) cross += ur * vr - ui * vi;
+        else {
+          nu2 = ur;
+          nv2 = vr;
+        }
+      }
+      normS2 += T(2) * cross + nu2 * nv2;
+      sh.scal[0] = normS2;
+      sh.scal[1] = nu2 * nv2;
+    }
+    __syncthreads();
+    normS2 = sh.scal[0];
+    T term = sh.scal[1];
     ++k;
-    if (nu2 * nv2 <= eps * eps * normS2) {
+    if (term <= eps * eps * normS2) {
       converged = true;
       break;
     }
     // --- next pivot row: largest entry of u_k outside the rows used so far
-    double bu = -1.0;
+    T bu = T(-1);
     int inext = 0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       if (i == istar) continue;
       Op u = Ub[(long long)(k - 1) * m + i];
-      double a = (double)u.re * u.re + (double)u.im * u.im;
+      T a = u.re * u.re + u.im * u.im;
       if (a > bu) {
         bu = a;
         inext = i;
       }
     }
-    block_argmax(bu, inext, red);
-    if (!(bu > 0.0)) {
+    aca_argmax(bu, inext, sh);
+    if (!(bu > T(0))) {
       converged = true;
       break;
     }
@@ -798,7 +882,176 @@ __global__ void __launch_bounds__(256) k_aca(const FarBlk* __restrict__ blks, co
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    rank[blockIdx.x] = k;
+    rank[bi] = k;
+    if (!converged) atomicAdd(fails, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// ACA, one warp per (small) admissible block: same algorithm as k_aca with
+// warp-synchronous reductions (no block barriers), so thousands of small
+// blocks run concurrently.
+// ---------------------------------------------------------------------------
+constexpr int ACAW_WARPS = 4;
+
+template <typename T> __device__ __forceinline__ void warp_argmax(T& v, int& idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+}
+
+template <typename R, typename Op>
+__global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restrict__ list, int count,
+                                                              const FarBlk* __restrict__ blks,
+                                                              const ElemF* __restrict__ ef,
+                                                              const ElemD* __restrict__ ed,
+                                                              const signed char* __restrict__ bc, KParams<R> P,
+                                                              Op* __restrict__ Ustore, Op* __restrict__ Vstore,
+                                                              int* __restrict__ rank, int* __restrict__ fails,
+                                                              double eps_d) {
+  using T = decltype(Op{}.re);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * ACAW_WARPS + wid;
+  if (item >= count) return;
+  const int bi = list[item];
+  __shared__ int rows_used_all[ACAW_WARPS][ACA_RMAX];
+  int* rows_used = rows_used_all[wid];
+  const T eps = T(eps_d);
+  const FarBlk B = blks[bi];
+  const int m = 3 * B.nr, n = 3 * B.nc;
+  Op* Ub = Ustore + B.uoff;
+  Op* Vb = Vstore + B.voff;
+  const int rmax = min(B.rmax, ACA_RMAX);
+  int k = 0, istar = 0;
+  T normS2 = 0;
+  bool converged = false;
+  while (k < rmax) {
+    int ie = B.r0 + istar / 3, ia = istar % 3;
+    for (int el = lane; el < B.nc; el += 32) {
+      int e = B.c0 + el;
+      PairGeo<R> g;
+      int band;
+      pair_geo(ef, ed, ie, e, g, band);
+      UTAcc<R> acc;
+      regular_pair<R>(acc, g, band, P);
+      bool trac = bc[e] == BEM_BC_TRACTION;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        cplx<R> v = trac ? acc.t[3 * ia + c] : -acc.U(ia, c);
+        int j = 3 * el + c;
+        cplx<T> vv = mk<T>(T(v.re), T(v.im));
+        for (int l = 0; l < k; ++l) {
+          Op ul = Ub[(long long)l * m + istar], vl = Vb[(long long)l * n + j];
+          vv = vv - mk<T>(ul.re, ul.im) * mk<T>(vl.re, vl.im);
+        }
+        Vb[(long long)k * n + j] = to_op<Op>(vv);
+      }
+    }
+    __syncwarp();
+    T best = T(-1);
+    int jstar = 0;
+    for (int j = lane; j < n; j += 32) {
+      Op v = Vb[(long long)k * n + j];
+      T a = v.re * v.re + v.im * v.im;
+      if (a > best) {
+        best = a;
+        jstar = j;
+      }
+    }
+    warp_argmax(best, jstar);
+    if (!(best > T(0))) {
+      converged = true;
+      break;
+    }
+    Op pv = Vb[(long long)k * n + jstar];
+    cplx<T> ipiv = inv(mk<T>(pv.re, pv.im));
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
+      Op v = Vb[(long long)k * n + j];
+      Vb[(long long)k * n + j] = to_op<Op>(mk<T>(v.re, v.im) * ipiv);
+    }
+    __syncwarp();
+    int je = B.c0 + jstar / 3, jc = jstar % 3;
+    bool trac = bc[je] == BEM_BC_TRACTION;
+    for (int il = lane; il < B.nr; il += 32) {
+      int i = B.r0 + il;
+      PairGeo<R> g;
+      int band;
+      pair_geo(ef, ed, i, je, g, band);
+      UTAcc<R> acc;
+      regular_pair<R>(acc, g, band, P);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        cplx<R> v = trac ? acc.t[3 * a + jc] : -acc.U(a, jc);
+        int ii = 3 * il + a;
+        cplx<T> vv = mk<T>(T(v.re), T(v.im));
+        for (int l = 0; l < k; ++l) {
+          Op ul = Ub[(long long)l * m + ii], vl = Vb[(long long)l * n + jstar];
+          vv = vv - mk<T>(ul.re, ul.im) * mk<T>(vl.re, vl.im);
+        }
+        Ub[(long long)k * m + ii] = to_op<Op>(vv);
+      }
+    }
+    if (lane == 0) rows_used[k] = istar;
+    __syncwarp();
+    for (int l = lane; l < k; l += 32) Ub[(long long)k * m + rows_used[l]] = Op{};
+    __syncwarp();
+    T cross = 0, nu2 = 0, nv2 = 0;
+    for (int l = 0; l <= k; ++l) {
+      T ur = 0, ui = 0, vr = 0, vi = 0;
+      for (int i = lane; i < m; i += 32) {
+        Op a = Ub[(long long)l * m + i], b2 = Ub[(long long)k * m + i];
+        ur += a.re * b2.re + a.im * b2.im;
+        ui += a.re * b2.im - a.im * b2.re;
+      }
+      for (int j = lane; j < n; j += 32) {
+        Op a = Vb[(long long)l * n + j], b2 = Vb[(long long)k * n + j];
+        vr += a.re * b2.re + a.im * b2.im;
+        vi += a.re * b2.im - a.im * b2.re;
+      }
+      ur = wsumT(ur);
+      ui = wsumT(ui);
+      vr = wsumT(vr);
+      vi = wsumT(vi);
+      if (l < k) cross += ur * vr - ui * vi;
+      else {
+        nu2 = ur;
+        nv2 = vr;
+      }
+    }
+    normS2 += T(2) * cross + nu2 * nv2;
+    ++k;
+    if (nu2 * nv2 <= eps * eps * normS2) {
+      converged = true;
+      break;
+    }
+    T bu = T(-1);
+    int inext = 0;
+    for (int i = lane; i < m; i += 32) {
+      if (i == istar) continue;
+      Op u = Ub[(long long)(k - 1) * m + i];
+      T a = u.re * u.re + u.im * u.im;
+      if (a > bu) {
+        bu = a;
+        inext = i;
+      }
+    }
+    warp_argmax(bu, inext);
+    if (!(bu > T(0))) {
+      converged = true;
+      break;
+    }
+    istar = inext;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    rank[bi] = k;
     if (!converged) atomicAdd(fails, 1);
   }
 }
@@ -832,11 +1085,16 @@ void launch_near_regular(const NearBlk* blks, int nblk, const ElemF* ef, const E
                          const signed char* bc, const KParams<R>& P, Op* near, cudaStream_t st) {
   if (count_if(nblk)) k_near_regular<R, Op><<<nblk, 256, 0, st>>>(blks, ef, ed, bc, P, near);
 }
-template <typename Op>
-void launch_sing(const SingPair* pairs, int n, const ElemD* ed, const signed char* bc, const double* stat,
-                 const KParams<double>& P, Op* near, c128* pinv, const double* pattern, c128 pk, c128* b,
-                 int* status, cudaStream_t st) {
-  if (count_if(n)) k_sing<Op><<<(n + 3) / 4, 128, 0, st>>>(pairs, n, ed, bc, stat, P, near, pinv, pattern, pk, b, status);
+void launch_polar(const ElemD* ed, int ne, double* out, cudaStream_t st) {
+  count_if(true);
+  k_polar<<<(ne + 127) / 128, 128, 0, st>>>(ed, ne, out);
+}
+template <typename R, typename Op>
+void launch_sing(const SingPair* pairs, int n, const ElemD* ed, const double* polar, const signed char* bc,
+                 const double* stat, const KParams<R>& P, Op* near, c128* pinv, const double* pattern, c128 pk,
+                 c128* b, int* status, cudaStream_t st) {
+  if (count_if(n))
+    k_sing<R, Op><<<(n + 3) / 4, 128, 0, st>>>(pairs, n, ed, polar, bc, stat, P, near, pinv, pattern, pk, b, status);
 }
 template <typename R>
 void launch_rhs(int ne, const int* loaded, int nloaded, const ElemF* ef, const ElemD* ed,
@@ -846,9 +1104,14 @@ void launch_rhs(int ne, const int* loaded, int nloaded, const ElemF* ef, const E
   k_rhs<R><<<(ne + 7) / 8, 256, 0, st>>>(ne, loaded, nloaded, ef, ed, bc, pattern, P, pk, b);
 }
 template <typename R, typename Op>
-void launch_aca(const FarBlk* blks, int nblk, const ElemF* ef, const ElemD* ed, const signed char* bc,
-                const KParams<R>& P, Op* U, Op* V, int* rank, int* fails, double eps, cudaStream_t st) {
-  if (count_if(nblk)) k_aca<R, Op><<<nblk, 256, 0, st>>>(blks, ef, ed, bc, P, U, V, rank, fails, eps);
+void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int* large_list, int nlarge,
+                const ElemF* ef, const ElemD* ed, const signed char* bc, const KParams<R>& P, Op* U, Op* V, int* rank,
+                int* fails, double eps, cudaStream_t st) {
+  if (count_if(nlarge))
+    k_aca<R, Op><<<nlarge, ACA_THREADS, 0, st>>>(large_list, blks, ef, ed, bc, P, U, V, rank, fails, eps);
+  if (count_if(nsmall))
+    k_aca_warp<R, Op><<<(nsmall + ACAW_WARPS - 1) / ACAW_WARPS, 32 * ACAW_WARPS, 0, st>>>(
+        small_list, nsmall, blks, ef, ed, bc, P, U, V, rank, fails, eps);
 }
 
 template void launch_near_regular<float, c64>(const NearBlk*, int, const ElemF*, const ElemD*,
@@ -856,20 +1119,21 @@ template void launch_near_regular<float, c64>(const NearBlk*, int, const ElemF*,
 template void launch_near_regular<double, c128>(const NearBlk*, int, const ElemF*, const ElemD*,
                                                 const signed char*, const KParams<double>&, c128*,
                                                 cudaStream_t);
-template void launch_sing<c64>(const SingPair*, int, const ElemD*, const signed char*, const double*,
-                               const KParams<double>&, c64*, c128*, const double*, c128, c128*, int*,
-                               cudaStream_t);
-template void launch_sing<c128>(const SingPair*, int, const ElemD*, const signed char*, const double*,
-                                const KParams<double>&, c128*, c128*, const double*, c128, c128*, int*,
-                                cudaStream_t);
+template void launch_sing<float, c64>(const SingPair*, int, const ElemD*, const double*, const signed char*,
+                                      const double*, const KParams<float>&, c64*, c128*, const double*, c128,
+                                      c128*, int*, cudaStream_t);
+template void launch_sing<double, c128>(const SingPair*, int, const ElemD*, const double*, const signed char*,
+                                        const double*, const KParams<double>&, c128*, c128*, const double*, c128,
+                                        c128*, int*, cudaStream_t);
 template void launch_rhs<float>(int, const int*, int, const ElemF*, const ElemD*, const signed char*,
                                 const double*, const KParams<float>&, c128, c128*, cudaStream_t);
 template void launch_rhs<double>(int, const int*, int, const ElemF*, const ElemD*, const signed char*,
                                  const double*, const KParams<double>&, c128, c128*, cudaStream_t);
-template void launch_aca<float, c64>(const FarBlk*, int, const ElemF*, const ElemD*, const signed char*,
-                                     const KParams<float>&, c64*, c64*, int*, int*, double, cudaStream_t);
-template void launch_aca<double, c128>(const FarBlk*, int, const ElemF*, const ElemD*, const signed char*,
-                                       const KParams<double>&, c128*, c128*, int*, int*, double,
-                                       cudaStream_t);
+template void launch_aca<float, c64>(const FarBlk*, const int*, int, const int*, int, const ElemF*, const ElemD*,
+                                     const signed char*, const KParams<float>&, c64*, c64*, int*, int*, double,
+                                     cudaStream_t);
+template void launch_aca<double, c128>(const FarBlk*, const int*, int, const int*, int, const ElemF*,
+                                       const ElemD*, const signed char*, const KParams<double>&, c128*, c128*, int*,
+                                       int*, double, cudaStream_t);
 
 }  // namespace bem

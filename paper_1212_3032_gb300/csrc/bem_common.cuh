@@ -52,6 +52,9 @@ template <typename To, typename From> BEM_HD cplx<To> ccast(cplx<From> a) {
   return {To(a.re), To(a.im)};
 }
 
+__device__ __forceinline__ void sincos_r(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_r(double x, double* s, double* c) { sincos(x, s, c); }
+
 // exp(-z) for complex z
 __device__ __forceinline__ cplx<float> cexp_neg(cplx<float> z) {
   float sn, cs;
@@ -88,14 +91,30 @@ constexpr int NEAR_Q_REM = 4;
 constexpr int BAND_SELF = 0, BAND_NEAR = 1, BAND_Q4 = 2, BAND_Q2 = 3, BAND_Q1 = 4;
 
 constexpr int GL_MAX = 16;        // Gauss-Legendre tables for q = 1..16
-constexpr int SERIES_TERMS = 24;  // Taylor coefficients of the regular radial parts
 
 // Radius (in |z_s|) below which the radial functions use Taylor series.
-constexpr double Z_SERIES = 1.25;
-constexpr int SERIES_M_F32 = 14;  // terms used in FP32 (|z|^15/15! < 3e-11 at |z| = 1.25)
-constexpr int SERIES_M_F64 = 22;  // terms used in FP64
+constexpr double Z_SERIES = 1.0;
+constexpr int SERIES_M_F32 = 12;  // terms used in FP32 (1/13! < 2e-10 at |z| = 1)
+constexpr int SERIES_M_F64 = 20;  // terms used in FP64 (1/21! < 2e-20)
+constexpr int SER_MAX = 21;
 
 // Material and frequency parameters of one kernel evaluation (Sec. 2.1).
+//
+// With z = s r / c_s and gamma = c_s / c_p (so z_p = gamma z), the radial
+// functions enter U and T only through
+//   Phi = r phi, Psi = r psi,
+//   A = r^2 (phi' - psi/r)            = r Phi' - Phi - Psi,
+//   B = r^2 (4 psi/r - 2 psi')        = 2 (3 Psi - r Psi'),
+//   C = r^2 (k2 (phi' - psi' - 2psi/r) - 2 (phi' - psi' - psi/r))
+//     = k2 (r Phi' - Phi - r Psi' - Psi) - 2 (r Phi' - Phi - r Psi').
+// Each is an entire function of z with Taylor coefficients (m-th):
+//   phi_m = a_m - beta2 gamma^m b_m,  psi_m = c_m (1 - beta2 gamma^m),
+//   A_m = (m-1) phi_m - psi_m,  B_m = 2 (3-m) psi_m,
+//   C_m = k2 ((m-1) phi_m - (m+1) psi_m) - 2 ((m-1) phi_m - m psi_m),
+// where a_m, b_m, c_m are those of A(z) - 1/z^2, B(z) - 1/z^2, C(z) - 3/z^2
+// (exponential series). The m = 0 terms are the static (Kelvin) values; the
+// dynamic remainder is the sum over m >= 1 (m >= 2 for A, C), free of
+// cancellation.
 template <typename R> struct KParams {
   cplx<R> s;      // complex frequency s = eta + i omega_k
   cplx<R> ks;     // s / c_s  (= d z_s / d r)
@@ -107,14 +126,16 @@ template <typename R> struct KParams {
   R nu;           // Poisson ratio (Kelvin parts)
   R kel_u;        // 1 / (16 pi mu (1 - nu))
   R kel_t;        // 1 / (8 pi (1 - nu))
+  R ser[5][SER_MAX];  // Taylor coefficients of Phi, Psi, A, B, C (index m)
 };
-
 // Device-side tables (one copy per translation unit that includes
 // bem_kernels.cuh; each is filled by its own upload function).
 struct RuleTables {
   double gl_x[GL_MAX + 1][GL_MAX];  // nodes on [0, 1]
   double gl_w[GL_MAX + 1][GL_MAX];
-  double ser[6][SERIES_TERMS];      // A, B, C coefficients and derivative coefficients
+  // FP32 copies for the FP32 evaluation path (no FP64 conversions in inner loops)
+  float gl_xf[GL_MAX + 1][GL_MAX];
+  float gl_wf[GL_MAX + 1][GL_MAX];
 };
 
 }  // namespace bem

@@ -58,6 +58,15 @@ struct Panel {
   int kind;
 };
 
+// A contiguous run of panels of one leaf row handled by one CTA of the
+// matrix-vector product; its partial row sums go to rows [slot, slot + rows)
+// of the partial buffer and are added up per leaf in a fixed order.
+struct Task {
+  int leaf;
+  int p0, p1;  // panel range
+  int slot;
+};
+
 // Singular (SELF) and near-singular (NEAR) element pairs, FP64 path.
 struct SingPair {
   int i, e;         // collocation element, integration element (tree order)
@@ -139,6 +148,14 @@ struct bem_ctx {
   bem::DevBuf<int> leaf_r0, leaf_nr;  // per leaf
   bem::DevBuf<int> panel_ptr;         // CSR over leaves
   bem::DevBuf<bem::Panel> panels;
+  int ntasks = 0;
+  long long part_rows = 0;            // rows of the partial buffer per right-hand side
+  bem::DevBuf<bem::Task> tasks;
+  bem::DevBuf<int> task_ptr;          // CSR of tasks over leaves
+  bem::DevBuf<double> part;           // partial sums (sized for 4 rhs of complex FP64)
+  int nfar_small = 0, nfar_large = 0;
+  bem::DevBuf<int> far_small, far_large;  // admissible block indices by size class
+  bem::DevBuf<double> polar;          // ne x 27 self-rule polar parameters
   // singular pairs and their static parts
   int nsing = 0;
   bem::DevBuf<bem::SingPair> sing;

@@ -18,17 +18,20 @@ void launch_static(const SingPair* pairs, int n, const ElemD* ed, const KParams<
 template <typename R, typename Op>
 void launch_near_regular(const NearBlk* blks, int nblk, const ElemF* ef, const ElemD* ed,
                          const signed char* bc, const KParams<R>& P, Op* near, cudaStream_t st);
-template <typename Op>
-void launch_sing(const SingPair* pairs, int n, const ElemD* ed, const signed char* bc, const double* stat,
-                 const KParams<double>& P, Op* near, c128* pinv, const double* pattern, c128 pk, c128* b,
-                 int* status, cudaStream_t st);
+void launch_polar(const ElemD* ed, int ne, double* out, cudaStream_t st);
+template <typename R, typename Op>
+void launch_sing(const SingPair* pairs, int n, const ElemD* ed, const double* polar, const signed char* bc,
+                 const double* stat, const KParams<R>& P, Op* near, c128* pinv, const double* pattern, c128 pk,
+                 c128* b, int* status, cudaStream_t st);
 template <typename R>
 void launch_rhs(int ne, const int* loaded, int nloaded, const ElemF* ef, const ElemD* ed,
                 const signed char* bc, const double* pattern, const KParams<R>& P, c128 pk, c128* b,
                 cudaStream_t st);
+// Admissible blocks split in two lists: small ones one warp each, large ones one CTA each.
 template <typename R, typename Op>
-void launch_aca(const FarBlk* blks, int nblk, const ElemF* ef, const ElemD* ed, const signed char* bc,
-                const KParams<R>& P, Op* U, Op* V, int* rank, int* fails, double eps, cudaStream_t st);
+void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int* large_list, int nlarge,
+                const ElemF* ef, const ElemD* ed, const signed char* bc, const KParams<R>& P, Op* U, Op* V, int* rank,
+                int* fails, double eps, cudaStream_t st);
 
 // ---- solver (bem_solve.cu) ----
 // H-matrix product y = A x for nrhs right-hand sides (x, y: nrhs vectors of

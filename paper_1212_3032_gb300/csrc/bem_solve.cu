@@ -5,10 +5,11 @@
 // H-matrix product (HBM-bound): y = D_near x + sum_b U_b (V_b^T x)
 //   k_hmv_t     t_b = V_b^T x for every admissible block (one CTA per block,
 //               one warp per factor column, coalesced column reads)
-//   k_hmv_rows  one CTA per leaf row cluster: streams its dense near blocks
-//               and its slices of the U_b factors once, column-major, each
-//               thread owning one row of the leaf (coalesced 8/16-byte loads),
-//               G column groups reduced through shared memory; no atomics.
+//   k_hmv_tasks one CTA per task (a run of panels of one leaf row: dense near
+//               blocks and slices of the U_b factors), every stored entry
+//               read once, coalesced across rows (column-major storage),
+//               partial row sums to a per-task slot; no atomics
+//   k_hmv_reduce per leaf row, the task slots summed in a fixed order
 #include <algorithm>
 
 #include "bem_internal.h"
@@ -69,21 +70,24 @@ __global__ void __launch_bounds__(256) k_hmv_t(const FarBlk* __restrict__ blks, 
 }
 
 // ---------------------------------------------------------------------------
-// phase 2: rows of one leaf cluster
+// phase 2: one CTA per task (a run of column panels of one leaf row). Each
+// thread owns one row of the leaf and one of G column groups; every column
+// of a panel is read once, coalesced across the rows (column-major blocks),
+// 8 independent loads in flight per thread. Partial row sums go to the task's
+// slot of the partial buffer (no atomics).
 // ---------------------------------------------------------------------------
-template <typename Op, typename X, typename Y, typename Acc, int NRHS>
-__global__ void __launch_bounds__(256) k_hmv_rows(const int* __restrict__ leaf_r0, const int* __restrict__ leaf_nr,
-                                                  const int* __restrict__ pptr, const Panel* __restrict__ panels,
-                                                  const FarBlk* __restrict__ far, const int* __restrict__ rank,
-                                                  const Op* __restrict__ near, const Op* __restrict__ U,
-                                                  const cplx<Acc>* __restrict__ t, int tstride,
-                                                  const X* __restrict__ x, long long N, Y* __restrict__ y) {
+constexpr int HMV_THREADS = 384;
+
+template <typename Op, typename X, typename Acc, int NRHS>
+__global__ void __launch_bounds__(HMV_THREADS) k_hmv_tasks(
+    const Task* __restrict__ tasks, const int* __restrict__ leaf_nr, const Panel* __restrict__ panels,
+    const FarBlk* __restrict__ far, const int* __restrict__ rank, const Op* __restrict__ near,
+    const Op* __restrict__ U, const cplx<Acc>* __restrict__ t, int tstride, const X* __restrict__ x, long long N,
+    cplx<Acc>* __restrict__ part, long long pstride) {
   extern __shared__ unsigned char smem_raw[];
   cplx<Acc>* red = reinterpret_cast<cplx<Acc>*>(smem_raw);
-  const int leaf = blockIdx.x;
-  const int rows = 3 * leaf_nr[leaf];
-  const long long row0 = 3LL * leaf_r0[leaf];
-  const int p0 = pptr[leaf], p1 = pptr[leaf + 1];
+  const Task tk = tasks[blockIdx.x];
+  const int rows = 3 * leaf_nr[tk.leaf];
   for (int rbase = 0; rbase < rows; rbase += blockDim.x) {
     const int rcount = min(rows - rbase, (int)blockDim.x);
     const int G = max(1, (int)blockDim.x / rcount);
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(256) k_hmv_rows(const int* __restrict__ leaf_r
 #pragma unroll
     for (int q = 0; q < NRHS; ++q) acc[q] = cplx<Acc>{0, 0};
     if (active) {
-      for (int p = p0; p < p1; ++p) {
+      for (int p = tk.p0; p < tk.p1; ++p) {
         const Panel P = panels[p];
         const long long ld = P.ld;
         if (P.kind == 0) {
@@ -102,18 +106,15 @@ __global__ void __launch_bounds__(256) k_hmv_rows(const int* __restrict__ leaf_r
           const X* xs = x + P.xoff;
           const int nc = P.ncols;
           int j = g;
-          for (; j + 3 * G < nc; j += 4 * G) {
-            cplx<Acc> a0 = up<Acc>(d[(long long)j * ld]);
-            cplx<Acc> a1 = up<Acc>(d[(long long)(j + G) * ld]);
-            cplx<Acc> a2 = up<Acc>(d[(long long)(j + 2 * G) * ld]);
-            cplx<Acc> a3 = up<Acc>(d[(long long)(j + 3 * G) * ld]);
+          for (; j + 7 * G < nc; j += 8 * G) {
+            cplx<Acc> a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = up<Acc>(d[(long long)(j + u * G) * ld]);
 #pragma unroll
             for (int q = 0; q < NRHS; ++q) {
               const X* xq = xs + q * N;
-              cmac(acc[q], a0, up<Acc>(xq[j]));
-              cmac(acc[q], a1, up<Acc>(xq[j + G]));
-              cmac(acc[q], a2, up<Acc>(xq[j + 2 * G]));
-              cmac(acc[q], a3, up<Acc>(xq[j + 3 * G]));
+#pragma unroll
+              for (int u = 0; u < 8; ++u) cmac(acc[q], a[u], up<Acc>(xq[j + u * G]));
             }
           }
           for (; j < nc; j += G) {
@@ -126,7 +127,17 @@ __global__ void __launch_bounds__(256) k_hmv_rows(const int* __restrict__ leaf_r
           const int nc = rank[b];
           const Op* d = U + P.data + r;
           const cplx<Acc>* ts = t + far[b].toff;
-          for (int j = g; j < nc; j += G) {
+          int j = g;
+          for (; j + 3 * G < nc; j += 4 * G) {
+            cplx<Acc> a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = up<Acc>(d[(long long)(j + u * G) * ld]);
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) cmac(acc[q], a[u], ts[(long long)q * tstride + j + u * G]);
+          }
+          for (; j < nc; j += G) {
             cplx<Acc> a0 = up<Acc>(d[(long long)j * ld]);
 #pragma unroll
             for (int q = 0; q < NRHS; ++q) cmac(acc[q], a0, ts[(long long)q * tstride + j]);
@@ -153,12 +164,34 @@ __global__ void __launch_bounds__(256) k_hmv_rows(const int* __restrict__ leaf_r
     }
     if (active && g == 0) {
 #pragma unroll
-      for (int q = 0; q < NRHS; ++q) {
-        Y o;
-        o.re = decltype(o.re)(acc[q].re);
-        o.im = decltype(o.im)(acc[q].im);
-        y[q * N + row0 + r] = o;
+      for (int q = 0; q < NRHS; ++q) part[q * pstride + tk.slot + r] = acc[q];
+    }
+  }
+}
+
+// phase 3: y[rows of leaf] = sum over the leaf's tasks, in task order
+template <typename Acc, typename Y, int NRHS>
+__global__ void __launch_bounds__(256) k_hmv_reduce(const int* __restrict__ leaf_r0, const int* __restrict__ leaf_nr,
+                                                    const int* __restrict__ task_ptr, const Task* __restrict__ tasks,
+                                                    const cplx<Acc>* __restrict__ part, long long pstride,
+                                                    long long N, Y* __restrict__ y) {
+  const int leaf = blockIdx.x;
+  const int rows = 3 * leaf_nr[leaf];
+  const long long row0 = 3LL * leaf_r0[leaf];
+  const int t0 = task_ptr[leaf], t1 = task_ptr[leaf + 1];
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      cplx<Acc> s{0, 0};
+      for (int k = t0; k < t1; ++k) {
+        cplx<Acc> v = part[q * pstride + tasks[k].slot + r];
+        s.re += v.re;
+        s.im += v.im;
       }
+      Y o;
+      o.re = decltype(o.re)(s.re);
+      o.im = decltype(o.im)(s.im);
+      y[q * N + row0 + r] = o;
     }
   }
 }
@@ -168,13 +201,16 @@ static void hmv_impl(const bem_ctx* ctx, const Op* near, const Op* U, const Op* 
                      const X* x, Y* y, cudaStream_t st) {
   int nfar = (int)ctx->far_h.size();
   if (count_if(nfar)) k_hmv_t<Op, X, Acc, NRHS><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, V, x, ctx->N, t,
-                                                            ctx->t_entries);
-  int threads = 256;
-  size_t sm = (size_t)threads * NRHS * sizeof(cplx<Acc>);
+                                                                       ctx->t_entries);
+  cplx<Acc>* part = reinterpret_cast<cplx<Acc>*>(ctx->part.p);
+  size_t sm = (size_t)HMV_THREADS * NRHS * sizeof(cplx<Acc>);
   count_if(true);
-  k_hmv_rows<Op, X, Y, Acc, NRHS><<<ctx->nleaves, threads, sm, st>>>(
-      ctx->leaf_r0.p, ctx->leaf_nr.p, ctx->panel_ptr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t,
-      ctx->t_entries, x, ctx->N, y);
+  k_hmv_tasks<Op, X, Acc, NRHS><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
+      ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t, ctx->t_entries, x, ctx->N,
+      part, ctx->part_rows);
+  count_if(true);
+  k_hmv_reduce<Acc, Y, NRHS><<<ctx->nleaves, 256, 0, st>>>(ctx->leaf_r0.p, ctx->leaf_nr.p, ctx->task_ptr.p,
+                                                          ctx->tasks.p, part, ctx->part_rows, ctx->N, y);
 }
 
 template <typename Op, typename X, typename Y, typename Acc>

@@ -53,6 +53,12 @@ class Mesh:
     pattern: np.ndarray
     name: str = ""
 
+    def __post_init__(self):
+        self.xyz = np.ascontiguousarray(self.xyz, dtype=np.float64)
+        self.tri = np.ascontiguousarray(self.tri, dtype=np.int32)
+        self.bc_type = np.ascontiguousarray(self.bc_type, dtype=np.int8)
+        self.pattern = np.ascontiguousarray(self.pattern, dtype=np.float64)
+
     @property
     def ne(self) -> int:
         return int(self.tri.shape[0])
@@ -142,7 +148,7 @@ def geodesic_sphere(n: int, radius: float = 1.0, center=(0.0, 0.0, 0.0),
     if inward:
         tri = tri[:, [0, 2, 1]]
     xyz = xyz * radius + np.asarray(center, dtype=np.float64)
-    return xyz, tri.astype(np.int32)
+    return np.ascontiguousarray(xyz), np.ascontiguousarray(tri, dtype=np.int32)
 
 
 def box_mesh(lx: float, ly: float, lz: float, h: float, center=(0.0, 0.0, 0.0)):
@@ -179,7 +185,7 @@ def box_mesh(lx: float, ly: float, lz: float, h: float, center=(0.0, 0.0, 0.0)):
     xyz = pool.array()
     tri = np.array(tris, dtype=np.int64)
     tri = _orient_outward(xyz, tri, np.asarray(center, dtype=np.float64))
-    return xyz, tri.astype(np.int32)
+    return np.ascontiguousarray(xyz), np.ascontiguousarray(tri, dtype=np.int32)
 
 
 def ellipsoid_mesh(n: int, semi_axes, center=(0.0, 0.0, 0.0)):

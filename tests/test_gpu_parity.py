@@ -3,7 +3,10 @@
 Tolerances (written from the arithmetic):
 * mixed precision (c64 storage, FP32 kernel evaluation): single entries carry
   a few FP32 roundings (~1e-6 relative); rows/vectors are compared at 2e-5;
-* plain (c128 everywhere): 1e-10;
+* plain (c128 everywhere): 1e-8 -- the oracle evaluates the radial
+  functions by their closed forms, whose 1/z^3 terms cancel to O(1), so at
+  |z| ~ 1e-3 (innermost polar nodes of the self element at low frequency) it
+  keeps only ~8 digits; the GPU path sums the Taylor series there;
 * low-rank blocks add the ACA tolerance (rows compared at 30 x aca_tol);
 * solutions: the benchmark spec's target 1e-4 relative L2 in the frequency domain
   and 1e-3 for time traces (mixed); plain form 1e-8 / 1e-7.
@@ -85,7 +88,7 @@ def _mesh_ctx(ctx, B, mesh, **kw):
     return o
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 2e-5), (1, 1e-10)])
+@pytest.mark.parametrize("prec,tol", [(0, 2e-5), (1, 1e-8)])
 @pytest.mark.parametrize("s", [0.625, 0.625 + 5.0j, 0.3 + 40.0j])
 def test_dense_rows_match_oracle(ctx, B, prec, tol, s):
     mesh = inputs.cavity_problem(4)                       # 320 elements
@@ -107,7 +110,7 @@ def _mixed_bc_mesh():
     return inputs.cube_with_cavities(n_face=8, n_cav=2, cav_radius=0.12, cav_n=3, seed=5)
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 2e-5), (1, 1e-10)])
+@pytest.mark.parametrize("prec,tol", [(0, 2e-5), (1, 1e-8)])
 def test_mixed_bc_rows_and_rhs(ctx, B, prec, tol):
     mesh = _mixed_bc_mesh()
     o = _mesh_ctx(ctx, B, mesh, dense=1, precision=prec)
@@ -161,7 +164,7 @@ def test_solve_matches_direct(ctx, B, prec, tol, ptol):
     A, b = bem.system_rows(g, mesh.bc_type, mesh.pattern.astype(complex), s, MAT)
     x_ref = solvers.direct_solve(A, b)
     bg = ctx.rhs(1.0, mesh.pattern)
-    assert _rel(bg, b) <= (2e-5 if prec == 0 else 1e-10)
+    assert _rel(bg, b) <= (2e-5 if prec == 0 else 1e-8)
     x, st = ctx.solve_assembled(bg, opts=o)
     assert st["converged"] == 1 and st["rel_residual"] <= tol
     assert _rel(x, x_ref) <= ptol
@@ -264,10 +267,43 @@ def test_single_element_and_tiny_sweep(ctx, B):
     xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
     tri = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]], dtype=np.int32)
     m = inputs.pressurised_surface(xyz, tri)
-    ctx.mesh(m.xyz, m.tri, m.bc_type, B.default_opts(dense=1, precision=1))
+    o = B.default_opts(dense=1, precision=1, tol=1e-12)
+    ctx.mesh(m.xyz, m.tri, m.bc_type, o)
     ctx.set_window(0.5, 0)
-    stats = ctx.solve_sweep(4.0, 2, inputs.heaviside_history(2), m.pattern, B.default_opts(dense=1, precision=1))
+    stats = ctx.solve_sweep(4.0, 2, inputs.heaviside_history(2), m.pattern, o)
     ref = osweep.solve_sweep(m, MAT, 4.0, 2, 0.5, inputs.heaviside_history(2))
     for k in range(2):
         assert _rel(ctx.get_frequency_solution(k), ref["a"][k]) <= 1e-9
     assert len(stats) == 2
+
+
+def test_device_pointer_entry_points(ctx, B):
+    """The _dev variants give the same sweep as the host-pointer API."""
+    import torch
+    mesh = inputs.cavity_problem(3)
+    T, N = 8.0, 16
+    o = B.default_opts(dense=0, leaf_size=16, precision=0, tol=1e-7)
+    ctx.set_window(5.0 / T, 1)
+    ctx.mesh(mesh.xyz, mesh.tri, mesh.bc_type, o)
+    ctx.solve_sweep(T, N, inputs.heaviside_history(N), mesh.pattern, o)
+    a_host = [ctx.get_frequency_solution(k) for k in range(N // 2 + 1)]
+    tr_host = ctx.time_response(np.arange(3 * mesh.ne))
+    dev = torch.device("cuda", 0)
+    xyz = torch.tensor(mesh.xyz, device=dev)
+    tri = torch.tensor(mesh.tri, device=dev)
+    bc = torch.tensor(mesh.bc_type, device=dev)
+    with pytest.raises(ValueError):
+        ctx.mesh_dev(xyz, tri.t().contiguous().t(), bc, o)      # non-contiguous layout is refused
+    ctx.mesh_dev(xyz, tri, bc, o)
+    ctx.solve_sweep_dev(T, N, torch.tensor(inputs.heaviside_history(N), device=dev),
+                        torch.tensor(mesh.pattern, device=dev), o)
+    # the right-hand side sums singular contributions with FP64 atomics, so two
+    # runs agree to rounding, not bitwise
+    for k in range(N // 2 + 1):
+        assert _rel(ctx.get_frequency_solution(k), a_host[k]) <= 1e-9
+    out = torch.empty((N, 3 * mesh.ne), dtype=torch.float64, device=dev)
+    ctx.time_response_dev(torch.arange(3 * mesh.ne, device=dev), out)
+    assert np.abs(out.cpu().numpy() - tr_host).max() <= 1e-9 * np.abs(tr_host).max()
+    with pytest.raises(B.BemError):
+        ctx.time_response_dev(torch.tensor([0, 3 * mesh.ne], device=dev), torch.empty((N, 2), dtype=torch.float64,
+                                                                                       device=dev))
