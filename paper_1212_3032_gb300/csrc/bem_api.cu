@@ -583,6 +583,36 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   launch_polar(ctx->ed.p, ne, ctx->polar.p, st);
   CK("polar");
 
+  // regular pairs of every near block, sorted by (band, distance)
+  {
+    int nnb = (int)ctx->near_h.size();
+    std::vector<long long> po(std::max(1, nnb));
+    long long tot = 0;
+    ctx->max_nr = 1;
+    for (int b = 0; b < nnb; ++b) {
+      po[b] = tot;
+      tot += (long long)ctx->near_h[b].nr * ctx->near_h[b].nc;
+      ctx->max_nr = std::max(ctx->max_nr, ctx->near_h[b].nr);
+    }
+    BEM_CUDA_TRY(ctx->poff.alloc(std::max(1, nnb)));
+    BEM_CUDA_TRY(ctx->plist.alloc(std::max<long long>(1, tot)));
+    BEM_CUDA_TRY(ctx->pcount.alloc(std::max(1, nnb)));
+    if (nnb) BEM_CUDA_TRY(cudaMemcpyAsync(ctx->poff.p, po.data(), nnb * sizeof(long long), cudaMemcpyHostToDevice, st));
+    launch_pair_sort(ctx->near_d.p, nnb, ctx->ef.p, ctx->ed.p, ctx->poff.p, ctx->plist.p, ctx->pcount.p, st);
+    CK("pair_sort");
+    // far right-hand-side items: (far block, first row), 8 rows each
+    std::vector<int> items;
+    for (size_t b = 0; b < ctx->far_h.size(); ++b)
+      for (int r = 0; r < ctx->far_h[b].nr; r += 8) {
+        items.push_back((int)b);
+        items.push_back(r);
+      }
+    ctx->nrhs_items = (int)(items.size() / 2);
+    BEM_CUDA_TRY(ctx->rhs_items.alloc(std::max<size_t>(2, items.size())));
+    if (!items.empty())
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->rhs_items.p, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
+
   // singular and near-singular pairs of the near blocks
   int nnb = (int)ctx->near_h.size();
   DevBuf<int> cnt;
@@ -674,15 +704,14 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
   BEM_CUDA_TRY(ctx->status.ensure(1));
   DevBuf<int>& status = ctx->status;
   if (b) {
-    if (is_mixed(ctx)) {
-      KParams<float> Pf = make_params<float>(ctx, sre, sim);
-      launch_rhs<float>(ctx->ne, ctx->loaded.p, ctx->nloaded, ctx->ef.p, ctx->ed.p, ctx->bc.p, pattern_tree, Pf,
-                        pk, b, st);
-    } else {
-      launch_rhs<double>(ctx->ne, ctx->loaded.p, ctx->nloaded, ctx->ef.p, ctx->ed.p, ctx->bc.p, pattern_tree, Pd,
-                         pk, b, st);
-    }
-    CK("rhs");
+    BEM_CUDA_TRY(cudaMemsetAsync(b, 0, ctx->N * sizeof(c128), st));
+    if (is_mixed(ctx))
+      launch_rhs_far<float>(ctx->rhs_items.p, ctx->nrhs_items, ctx->far_d.p, ctx->ef.p, ctx->ed.p, ctx->bc.p,
+                            ctx->patf.p, ctx->pattern.p, make_params<float>(ctx, sre, sim), pk, b, st);
+    else
+      launch_rhs_far<double>(ctx->rhs_items.p, ctx->nrhs_items, ctx->far_d.p, ctx->ef.p, ctx->ed.p, ctx->bc.p,
+                             ctx->patf.p, ctx->pattern.p, Pd, pk, b, st);
+    CK("rhs_far");
   }
   if (is_mixed(ctx)) {
     BEM_CUDA_TRY(ctx->near32.ensure(std::max<long long>(1, ctx->near_entries)));
@@ -695,8 +724,9 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
     launch_sing<float, c64>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pf,
                             ctx->near32.p, ctx->prec_inv.p, pattern_tree, pk, b, status.p, st);
     CK("sing");
-    launch_near_regular<float, c64>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf,
-                                    ctx->near32.p, st);
+    launch_near_regular<float, c64>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->max_nr, ctx->plist.p, ctx->poff.p,
+                                    ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, ctx->near32.p,
+                                    b ? ctx->patf.p : nullptr, b ? ctx->pattern.p : nullptr, pk, b, st);
     CK("near_regular");
     launch_aca<float, c64>(ctx->far_d.p, ctx->far_small.p, ctx->nfar_small, ctx->far_large.p, ctx->nfar_large,
                            ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, ctx->u32.p, ctx->v32.p, ctx->rank.p, ctx->aca_fail.p,
@@ -714,8 +744,9 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
     launch_sing<double, c128>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pd,
                               ctx->near64.p, ctx->prec_inv.p, pattern_tree, pk, b, status.p, st);
     CK("sing");
-    launch_near_regular<double, c128>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd,
-                                      ctx->near64.p, st);
+    launch_near_regular<double, c128>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->max_nr, ctx->plist.p,
+                                      ctx->poff.p, ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd, ctx->near64.p,
+                                      b ? ctx->patf.p : nullptr, b ? ctx->pattern.p : nullptr, pk, b, st);
     CK("near_regular");
     launch_aca<double, c128>(ctx->far_d.p, ctx->far_small.p, ctx->nfar_small, ctx->far_large.p, ctx->nfar_large,
                              ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd, ctx->u64.p, ctx->v64.p, ctx->rank.p,
@@ -752,7 +783,33 @@ int apply64(bem_ctx* ctx, const c128* x, c128* y, int nrhs) {
   return BEM_OK;
 }
 
+__global__ void k_pattern_f32(const double* __restrict__ p, float* __restrict__ q, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) q[i] = (float)p[i];
+}
+
+// y = A x for the mixed-precision operator with FP32 products: x rounded to
+// c64, FP32 sums within each task of the product, FP64 sums across tasks.
+// Relative accuracy ~1e-6 of |A||x|: used for true residuals when the
+// tolerance is >= 1e-6 and for the extrapolation products.
+int apply_fast(bem_ctx* ctx, const c128* x, c128* y, int nrhs) {
+  if (!is_mixed(ctx)) return apply64(ctx, x, y, nrhs);
+  BEM_CUDA_TRY(ctx->w32.ensure((size_t)nrhs * ctx->N));
+  launch_copy_cast(x, ctx->w32.p, nrhs * ctx->N, 1.0, ctx->stream);
+  cudaEvent_t ev = prof_begin(ctx);
+  launch_hmatvec<c64, c64, c128, float>(ctx, ctx->near32.p, ctx->u32.p, ctx->v32.p,
+                                        reinterpret_cast<cplx<float>*>(ctx->t32.p), ctx->w32.p, y, nrhs, ctx->stream);
+  CK("hmatvec_fast");
+  prof_end(ctx, ev, 0, hmv_bytes(ctx, 8, 8, 16, nrhs, ctx->used_lowrank));
+  return BEM_OK;
+}
+
 int prepare_loaded(bem_ctx* ctx, const double* pattern_tree) {
+  BEM_CUDA_TRY(ctx->patf.ensure(3LL * ctx->ne));
+  count_if(true);
+  k_pattern_f32<<<(unsigned)((3LL * ctx->ne + 255) / 256), 256, 0, ctx->stream>>>(pattern_tree, ctx->patf.p,
+                                                                                 3LL * ctx->ne);
+  CK("pattern_f32");
   BEM_CUDA_TRY(ctx->loaded.ensure(ctx->ne + 1));
   count_if(true);
   k_loaded<<<1, 1024, 0, ctx->stream>>>(pattern_tree, ctx->ne, ctx->loaded.p, ctx->loaded.p + ctx->ne);
@@ -838,8 +895,9 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
   std::vector<std::complex<double>> H((m + 1) * m), cs(m), sn(m), g(m + 1);
   double* hh = ctx->host_red;
   while (true) {
-    // true residual (FP64)
-    TRY(apply64(ctx, x, ctx->y64.p, 1));
+    // true residual, FP64 sums (FP32 products when the tolerance allows)
+    if (mixed && o.tol >= 1e-6) TRY(apply_fast(ctx, x, ctx->y64.p, 1));
+    else TRY(apply64(ctx, x, ctx->y64.p, 1));
     launch_residual(b, ctx->y64.p, ctx->r64.p, N, st);
     CK("residual");
     std::complex<double> rr;
@@ -976,7 +1034,7 @@ int sem_impl(bem_ctx* ctx, const c128* const* X, int K, const c128* b, c128* a0)
   BEM_CUDA_TRY(Q.alloc(K * N));
   for (int q = 0; q < K; ++q)
     BEM_CUDA_TRY(cudaMemcpyAsync(Xc.p + q * N, X[q], N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
-  TRY(apply64(ctx, Xc.p, Y.p, K));
+  TRY(apply_fast(ctx, Xc.p, Y.p, K));
   BEM_CUDA_TRY(ctx->red.ensure(2LL * 64 * 8 * 2 + 64));
   c128* part = reinterpret_cast<c128*>(ctx->red.p);
   c128* hdev = part + 64 * 8;
@@ -1134,15 +1192,22 @@ extern "C" int bem_rhs(bem_ctx* ctx, double p_re, double p_im, const double* pat
   BEM_CUDA_TRY(bd.alloc(ctx->N));
   c128 pk{p_re, p_im};
   KParams<double> Pd = make_params<double>(ctx, ctx->s_re, ctx->s_im);
+  BEM_CUDA_TRY(cudaMemsetAsync(bd.p, 0, ctx->N * sizeof(c128), ctx->stream));
   if (is_mixed(ctx)) {
     KParams<float> Pf = make_params<float>(ctx, ctx->s_re, ctx->s_im);
-    launch_rhs<float>(ctx->ne, ctx->loaded.p, ctx->nloaded, ctx->ef.p, ctx->ed.p, ctx->bc.p, ctx->pattern.p, Pf, pk,
-                      bd.p, ctx->stream);
+    launch_rhs_far<float>(ctx->rhs_items.p, ctx->nrhs_items, ctx->far_d.p, ctx->ef.p, ctx->ed.p, ctx->bc.p,
+                          ctx->patf.p, ctx->pattern.p, Pf, pk, bd.p, ctx->stream);
+    launch_near_regular<float, c64>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->max_nr, ctx->plist.p, ctx->poff.p,
+                                    ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, (c64*)nullptr, ctx->patf.p,
+                                    ctx->pattern.p, pk, bd.p, ctx->stream);
     launch_sing<float, c64>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pf,
                             nullptr, nullptr, ctx->pattern.p, pk, bd.p, ctx->status.p, ctx->stream);
   } else {
-    launch_rhs<double>(ctx->ne, ctx->loaded.p, ctx->nloaded, ctx->ef.p, ctx->ed.p, ctx->bc.p, ctx->pattern.p, Pd, pk,
-                       bd.p, ctx->stream);
+    launch_rhs_far<double>(ctx->rhs_items.p, ctx->nrhs_items, ctx->far_d.p, ctx->ef.p, ctx->ed.p, ctx->bc.p,
+                           ctx->patf.p, ctx->pattern.p, Pd, pk, bd.p, ctx->stream);
+    launch_near_regular<double, c128>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->max_nr, ctx->plist.p,
+                                      ctx->poff.p, ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd,
+                                      (c128*)nullptr, ctx->patf.p, ctx->pattern.p, pk, bd.p, ctx->stream);
     launch_sing<double, c128>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pd,
                               nullptr, nullptr, ctx->pattern.p, pk, bd.p, ctx->status.p, ctx->stream);
   }

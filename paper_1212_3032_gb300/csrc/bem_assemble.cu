@@ -418,37 +418,197 @@ __global__ void k_static(const SingPair* __restrict__ pairs, int npairs, const E
 }
 
 // ---------------------------------------------------------------------------
-// regular near-field entries: one CTA per near block
+// geometry of a pair without the band decision
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pair_geom(const ElemF* ef, const ElemD* ed, int i, int e, PairGeo<float>& g) {
+  const ElemF& I = ef[i];
+  const ElemF& E = ef[e];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g.d[a] = (E.c_hi[a] - I.c_hi[a]) + (E.c_lo[a] - I.c_lo[a]);
+    g.o0[a] = g.d[a] + E.o0[a];
+    g.e1[a] = E.e1[a];
+    g.e2[a] = E.e2[a];
+    g.n[a] = E.n[a];
+  }
+  g.area2 = E.area2;
+}
+__device__ __forceinline__ void pair_geom(const ElemF* ef, const ElemD* ed, int i, int e, PairGeo<double>& g) {
+  const ElemD& I = ed[i];
+  const ElemD& E = ed[e];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g.d[a] = E.c[a] - I.c[a];
+    g.o0[a] = E.p0[a] - I.c[a];
+    g.e1[a] = E.p1[a] - E.p0[a];
+    g.e2[a] = E.p2[a] - E.p0[a];
+    g.n[a] = E.n[a];
+  }
+  g.area2 = E.area2;
+}
+
+// ---------------------------------------------------------------------------
+// per near block, its regular pairs sorted by (band, distance) once per mesh,
+// so that the warps of the per-frequency kernel take the same quadrature
+// branch. Entry: il | el << 12 | band << 24 (SELF/NEAR pairs are left out;
+// the FP32 band decision falls back to FP64 next to a threshold, as in the
+// rest of the library).
+// ---------------------------------------------------------------------------
+constexpr int SORT_MAX = 4096;
+
+__global__ void __launch_bounds__(1024) k_pair_sort(const NearBlk* __restrict__ blks, const ElemF* __restrict__ ef,
+                                                    const ElemD* __restrict__ ed, const long long* __restrict__ poff,
+                                                    unsigned* __restrict__ plist, int* __restrict__ pcount) {
+  __shared__ unsigned long long key[SORT_MAX];
+  __shared__ int cnt;
+  const NearBlk B = blks[blockIdx.x];
+  const int np = B.nr * B.nc;
+  const long long base = poff[blockIdx.x];
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  if (np > SORT_MAX) {
+    // large block (leaf size above 64): natural order, band stored per pair
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+      int il = p % B.nr, el = p / B.nr;
+      PairGeo<float> g;
+      int band;
+      pair_geo(ef, ed, B.r0 + il, B.c0 + el, g, band);
+      if (band == BAND_SELF || band == BAND_NEAR) continue;
+      int pos = atomicAdd(&cnt, 1);
+      plist[base + pos] = (unsigned)il | ((unsigned)el << 12) | ((unsigned)band << 24);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) pcount[blockIdx.x] = cnt;
+    return;
+  }
+  int P2 = 1;
+  while (P2 < np) P2 <<= 1;
+  for (int p = threadIdx.x; p < P2; p += blockDim.x) {
+    unsigned long long k = ~0ULL;
+    if (p < np) {
+      int il = p % B.nr, el = p / B.nr;
+      PairGeo<float> g;
+      int band;
+      pair_geo(ef, ed, B.r0 + il, B.c0 + el, g, band);
+      if (band != BAND_SELF && band != BAND_NEAR) {
+        k = ((unsigned long long)band << 61) | ((unsigned long long)__float_as_uint(g.d2) << 24) |
+            (unsigned long long)p;
+        atomicAdd(&cnt, 1);
+      }
+    }
+    key[p] = k;
+  }
+  __syncthreads();
+  // bitonic sort of P2 keys
+  for (int size = 2; size <= P2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
+        int lo = 2 * t - (t & (stride - 1));
+        int hi = lo + stride;
+        bool up = ((lo & size) == 0);
+        unsigned long long a = key[lo], b = key[hi];
+        if ((a > b) == up) {
+          key[lo] = b;
+          key[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const int c = cnt;
+  for (int q = threadIdx.x; q < c; q += blockDim.x) {
+    unsigned long long k = key[q];
+    int p = (int)(k & 0xFFFFFFULL);
+    unsigned band = (unsigned)(k >> 61);
+    int il = p % B.nr, el = p / B.nr;
+    plist[base + q] = (unsigned)il | ((unsigned)el << 12) | (band << 24);
+  }
+  if (threadIdx.x == 0) pcount[blockIdx.x] = c;
+}
+
+// ---------------------------------------------------------------------------
+// regular near-field entries and their share of the right-hand side:
+// one CTA per near block, pairs taken from the sorted list
 // ---------------------------------------------------------------------------
 template <typename R, typename Op>
 __global__ void __launch_bounds__(256) k_near_regular(const NearBlk* __restrict__ blks,
-                                                      const ElemF* __restrict__ ef,
+                                                      const unsigned* __restrict__ plist,
+                                                      const long long* __restrict__ poff,
+                                                      const int* __restrict__ pcount, const ElemF* __restrict__ ef,
                                                       const ElemD* __restrict__ ed,
-                                                      const signed char* __restrict__ bc,
-                                                      KParams<R> P, Op* __restrict__ near) {
-  NearBlk B = blks[blockIdx.x];
-  int np = B.nr * B.nc;
-  long long ld = 3 * B.nr;
-  for (int p = threadIdx.x; p < np; p += blockDim.x) {
-    int il = p % B.nr, el = p / B.nr;
-    int i = B.r0 + il, e = B.c0 + el;
+                                                      const signed char* __restrict__ bc, KParams<R> P,
+                                                      Op* __restrict__ near, const float* __restrict__ patf,
+                                                      const double* __restrict__ patd, c128 pk,
+                                                      c128* __restrict__ b) {
+  extern __shared__ __align__(16) unsigned char rsum_raw[];
+  R* rsum = reinterpret_cast<R*>(rsum_raw);  // 3 nr complex row sums of B pattern
+  const NearBlk B = blks[blockIdx.x];
+  const int cnt = pcount[blockIdx.x];
+  const long long base = poff[blockIdx.x];
+  const long long ld = 3 * B.nr;
+  if (b)
+    for (int r = threadIdx.x; r < 6 * B.nr; r += blockDim.x) rsum[r] = R(0);
+  __syncthreads();
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const unsigned code = plist[base + q];
+    const int il = code & 0xFFF, el = (code >> 12) & 0xFFF, band = code >> 24;
+    const int i = B.r0 + il, e = B.c0 + el;
     PairGeo<R> g;
-    int band;
-    pair_geo(ef, ed, i, e, g, band);
-    if (band == BAND_SELF || band == BAND_NEAR) continue;
+    pair_geom(ef, ed, i, e, g);
     UTAcc<R> acc;
     regular_pair<R>(acc, g, band, P);
-    bool trac = bc[e] == BEM_BC_TRACTION;
-    Op* dst = near + B.off + (3 * el) * ld + 3 * il;
+    const bool trac = bc[e] == BEM_BC_TRACTION;
+    if (near) {
+      Op* dst = near + B.off + (3 * el) * ld + 3 * il;
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        cplx<R> v = trac ? acc.t[3 * a + b] : -acc.U(a, b);
-        dst[b * ld + a] = to_op<Op>(v);
+        for (int a = 0; a < 3; ++a) {
+          cplx<R> v = trac ? acc.t[3 * a + c] : -acc.U(a, c);
+          dst[c * ld + a] = to_op<Op>(v);
+        }
+    }
+    if (b) {
+      R pt[3];
+      if (sizeof(R) == 4) {
+        pt[0] = R(patf[3 * e]);
+        pt[1] = R(patf[3 * e + 1]);
+        pt[2] = R(patf[3 * e + 2]);
+      } else {
+        pt[0] = R(patd[3 * e]);
+        pt[1] = R(patd[3 * e + 1]);
+        pt[2] = R(patd[3 * e + 2]);
       }
+      if (pt[0] != R(0) || pt[1] != R(0) || pt[2] != R(0)) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          cplx<R> sa = mk<R>(0, 0);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) cfmr(sa, trac ? acc.U(a, c) : -acc.t[3 * a + c], pt[c]);
+          atomicAdd(&rsum[2 * (3 * il + a)], sa.re);
+          atomicAdd(&rsum[2 * (3 * il + a) + 1], sa.im);
+        }
+      }
+    }
+  }
+  if (!b) return;
+  __syncthreads();
+  for (int r = threadIdx.x; r < 3 * B.nr; r += blockDim.x) {
+    c128 v = c128{(double)rsum[2 * r], (double)rsum[2 * r + 1]} * pk;
+    if (v.re != 0.0 || v.im != 0.0) {
+      atomicAdd(&b[3LL * B.r0 + r].re, v.re);
+      atomicAdd(&b[3LL * B.r0 + r].im, v.im);
+    }
   }
 }
+
+// ---------------------------------------------------------------------------
+// far-field share of the right-hand side, on the fly: one warp per row of an
+// admissible block (items of 8 rows); traction-loaded columns need U only
+// ---------------------------------------------------------------------------
+struct RhsItem {
+  int blk, il0;
+};
 
 // ---------------------------------------------------------------------------
 // polar parameters of the self rule: per element, per triangle (c, p_k, p_k+1):
@@ -618,22 +778,34 @@ __device__ __forceinline__ void integrate_collapsed_u(cplx<R>* u, const R* o0, c
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_rhs(int ne, const int* __restrict__ loaded, int nloaded,
-                                             const ElemF* __restrict__ ef, const ElemD* __restrict__ ed,
-                                             const signed char* __restrict__ bc, const double* __restrict__ pattern,
-                                             KParams<R> P, c128 pk, c128* __restrict__ b) {
-  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (i >= ne) return;
+__global__ void __launch_bounds__(256) k_rhs_far(const RhsItem* __restrict__ items, const FarBlk* __restrict__ far,
+                                                 const ElemF* __restrict__ ef, const ElemD* __restrict__ ed,
+                                                 const signed char* __restrict__ bc, const float* __restrict__ patf,
+                                                 const double* __restrict__ patd, KParams<R> P, c128 pk,
+                                                 c128* __restrict__ b) {
+  const RhsItem it = items[blockIdx.x];
+  const FarBlk B = far[it.blk];
+  const int il = it.il0 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (il >= B.nr) return;
+  const int i = B.r0 + il;
   cplx<R> s[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
-  for (int j = lane; j < nloaded; j += 32) {
-    int e = loaded[j];
+  for (int el = lane; el < B.nc; el += 32) {
+    const int e = B.c0 + el;
+    R p3[3];
+    if (sizeof(R) == 4) {
+      p3[0] = R(patf[3 * e]);
+      p3[1] = R(patf[3 * e + 1]);
+      p3[2] = R(patf[3 * e + 2]);
+    } else {
+      p3[0] = R(patd[3 * e]);
+      p3[1] = R(patd[3 * e + 1]);
+      p3[2] = R(patd[3 * e + 2]);
+    }
+    if (p3[0] == R(0) && p3[1] == R(0) && p3[2] == R(0)) continue;
     PairGeo<R> g;
     int band;
     pair_geo(ef, ed, i, e, g, band);
-    if (band == BAND_SELF || band == BAND_NEAR) continue;
-    const double* pt = pattern + 3 * (long long)e;
-    R p3[3] = {R(pt[0]), R(pt[1]), R(pt[2])};
     if (bc[e] == BEM_BC_TRACTION) {
       cplx<R> u[6];
 #pragma unroll
@@ -655,17 +827,23 @@ __global__ void __launch_bounds__(256) k_rhs(int ne, const int* __restrict__ loa
         for (int c = 0; c < 3; ++c) cfmr(s[a], -acc.t[3 * a + c], p3[c]);
     }
   }
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
-    double re = warp_sum((double)s[a].re), im = warp_sum((double)s[a].im);
-    if (lane == 0) b[3 * (long long)i + a] = mk<double>(re, im) * pk;
+    R re = wred(s[a].re), im = wred(s[a].im);
+    if (lane == 0 && (re != R(0) || im != R(0))) {
+      c128 v = c128{(double)re, (double)im} * pk;
+      atomicAdd(&b[3LL * i + a].re, v.re);
+      atomicAdd(&b[3LL * i + a].im, v.im);
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // ACA with partial pivoting: one CTA per admissible block
 //   residual row i* -> v_k (scaled by the pivot), residual column j* -> u_k,
-//   ||S_k||_F^2 = ||S_{k-1}||_F^2 + 2 Re sum_{l<k} (u_l^H u_k)(v_l^H v_k) + |u_k|^2 |v_k|^2,
-//   stop when |u_k| |v_k| <= eps ||S_k||_F or at the rank cap.
+//   ||S_k||_F^2 estimated by sum_{l<=k} |u_l|^2 |v_l|^2 (the usual diagonal
+//   estimate; the cross terms are dropped), stop when
+//   |u_k| |v_k| <= eps ||S_k||_F or at the rank cap.
 // Norms are accumulated in the storage precision (FP32 on the mixed path).
 // ---------------------------------------------------------------------------
 constexpr int ACA_THREADS = 128;
@@ -673,7 +851,7 @@ constexpr int ACA_WARPS = ACA_THREADS / 32;
 constexpr int ACA_RMAX = 128;
 
 template <typename T> struct AcaShared {
-  T dot[4][ACA_RMAX + 1][ACA_WARPS];  // ur, ui, vr, vi partials per column l and warp
+  T dot[2][1][ACA_WARPS];  // per-warp partial norms
   T amax[ACA_WARPS];
   int aidx[ACA_WARPS];
   T scal[4];
@@ -745,17 +923,25 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
       UTAcc<R> acc;
       regular_pair<R>(acc, g, band, P);
       bool trac = bc[e] == BEM_BC_TRACTION;
+      cplx<T> vv[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         cplx<R> v = trac ? acc.t[3 * ia + c] : -acc.U(ia, c);
-        int j = 3 * el + c;
-        cplx<T> vv = mk<T>(T(v.re), T(v.im));
-        for (int l = 0; l < k; ++l) {
-          Op ul = Ub[(long long)l * m + istar], vl = Vb[(long long)l * n + j];
-          vv = vv - mk<T>(ul.re, ul.im) * mk<T>(vl.re, vl.im);
-        }
-        Vb[(long long)k * n + j] = to_op<Op>(vv);
+        vv[c] = mk<T>(T(v.re), T(v.im));
       }
+      const Op* vrow = Vb + 3 * el;
+#pragma unroll 4
+      for (int l = 0; l < k; ++l) {
+        Op ul = Ub[(long long)l * m + istar];
+        const Op* vl = vrow + (long long)l * n;
+        Op v0 = vl[0], v1 = vl[1], v2 = vl[2];
+        cplx<T> cu = mk<T>(ul.re, ul.im);
+        vv[0] = vv[0] - cu * mk<T>(v0.re, v0.im);
+        vv[1] = vv[1] - cu * mk<T>(v1.re, v1.im);
+        vv[2] = vv[2] - cu * mk<T>(v2.re, v2.im);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Vb[(long long)k * n + 3 * el + c] = to_op<Op>(vv[c]);
     }
     __syncthreads();
     T best = T(-1);
@@ -791,69 +977,62 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
       pair_geo(ef, ed, i, je, g, band);
       UTAcc<R> acc;
       regular_pair<R>(acc, g, band, P);
+      cplx<T> uu[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         cplx<R> v = trac ? acc.t[3 * a + jc] : -acc.U(a, jc);
-        int ii = 3 * il + a;
-        cplx<T> vv = mk<T>(T(v.re), T(v.im));
-        for (int l = 0; l < k; ++l) {
-          Op ul = Ub[(long long)l * m + ii], vl = Vb[(long long)l * n + jstar];
-          vv = vv - mk<T>(ul.re, ul.im) * mk<T>(vl.re, vl.im);
-        }
-        Ub[(long long)k * m + ii] = to_op<Op>(vv);
+        uu[a] = mk<T>(T(v.re), T(v.im));
       }
+      const Op* ucol = Ub + 3 * il;
+#pragma unroll 4
+      for (int l = 0; l < k; ++l) {
+        Op vl = Vb[(long long)l * n + jstar];
+        const Op* ul = ucol + (long long)l * m;
+        Op u0 = ul[0], u1 = ul[1], u2 = ul[2];
+        cplx<T> cv = mk<T>(vl.re, vl.im);
+        uu[0] = uu[0] - mk<T>(u0.re, u0.im) * cv;
+        uu[1] = uu[1] - mk<T>(u1.re, u1.im) * cv;
+        uu[2] = uu[2] - mk<T>(u2.re, u2.im) * cv;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Ub[(long long)k * m + 3 * il + a] = to_op<Op>(uu[a]);
     }
     if (threadIdx.x == 0) sh.rows_used[k] = istar;
     __syncthreads();
     // earlier pivot rows are exactly represented already: their residual is zero
     for (int l = threadIdx.x; l < k; l += blockDim.x) Ub[(long long)k * m + sh.rows_used[l]] = Op{};
     __syncthreads();
-    // --- all inner products u_l^H u_k, v_l^H v_k (l <= k) in one pass
-    for (int l = 0; l <= k; ++l) {
-      T ur = 0, ui = 0, vr = 0, vi = 0;
+    // Frobenius norm of the approximant estimated by its diagonal terms:
+    // ||S_k||^2 ~ sum_l |u_l|^2 |v_l|^2
+    {
+      T nu2 = 0, nv2 = 0;
       for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        Op a = Ub[(long long)l * m + i], b2 = Ub[(long long)k * m + i];
-        ur += a.re * b2.re + a.im * b2.im;
-        ui += a.re * b2.im - a.im * b2.re;
+        Op a = Ub[(long long)k * m + i];
+        nu2 += a.re * a.re + a.im * a.im;
       }
       for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        Op a = Vb[(long long)l * n + j], b2 = Vb[(long long)k * n + j];
-        vr += a.re * b2.re + a.im * b2.im;
-        vi += a.re * b2.im - a.im * b2.re;
+        Op a = Vb[(long long)k * n + j];
+        nv2 += a.re * a.re + a.im * a.im;
       }
-      ur = wsumT(ur);
-      ui = wsumT(ui);
-      vr = wsumT(vr);
-      vi = wsumT(vi);
+      nu2 = wsumT(nu2);
+      nv2 = wsumT(nv2);
       if (lane == 0) {
-        sh.dot[0][l][wid] = ur;
-        sh.dot[1][l][wid] = ui;
-        sh.dot[2][l][wid] = vr;
-        sh.dot[3][l][wid] = vi;
+        sh.dot[0][0][wid] = nu2;
+        sh.dot[1][0][wid] = nv2;
       }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      T cross = 0, nu2 = 0, nv2 = 0;
-      for (int l = 0; l <= k; ++l) {
-        T ur = 0, ui = 0, vr = 0, vi = 0;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        T a = 0, b2 = 0;
         for (int w = 0; w < ACA_WARPS; ++w) {
-          ur += sh.dot[0][l][w];
-          ui += sh.dot[1][l][w];
-          vr += sh.dot[2][l][w];
-          vi += sh.dot[3][l][w];
+          a += sh.dot[0][0][w];
+          b2 += sh.dot[1][0][w];
         }
-        if (l < k) cross += ur * vr - ui * vi;
-        else {
-          nu2 = ur;
-          nv2 = vr;
-        }
+        normS2 += a * b2;
+        sh.scal[0] = normS2;
+        sh.scal[1] = a * b2;
       }
-      normS2 += T(2) * cross + nu2 * nv2;
-      sh.scal[0] = normS2;
-      sh.scal[1] = nu2 * nv2;
+      __syncthreads();
     }
-    __syncthreads();
     normS2 = sh.scal[0];
     T term = sh.scal[1];
     ++k;
@@ -941,17 +1120,25 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
       UTAcc<R> acc;
       regular_pair<R>(acc, g, band, P);
       bool trac = bc[e] == BEM_BC_TRACTION;
+      cplx<T> vv[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         cplx<R> v = trac ? acc.t[3 * ia + c] : -acc.U(ia, c);
-        int j = 3 * el + c;
-        cplx<T> vv = mk<T>(T(v.re), T(v.im));
-        for (int l = 0; l < k; ++l) {
-          Op ul = Ub[(long long)l * m + istar], vl = Vb[(long long)l * n + j];
-          vv = vv - mk<T>(ul.re, ul.im) * mk<T>(vl.re, vl.im);
-        }
-        Vb[(long long)k * n + j] = to_op<Op>(vv);
+        vv[c] = mk<T>(T(v.re), T(v.im));
       }
+      const Op* vrow = Vb + 3 * el;
+#pragma unroll 4
+      for (int l = 0; l < k; ++l) {
+        Op ul = Ub[(long long)l * m + istar];
+        const Op* vl = vrow + (long long)l * n;
+        Op v0 = vl[0], v1 = vl[1], v2 = vl[2];
+        cplx<T> cu = mk<T>(ul.re, ul.im);
+        vv[0] = vv[0] - cu * mk<T>(v0.re, v0.im);
+        vv[1] = vv[1] - cu * mk<T>(v1.re, v1.im);
+        vv[2] = vv[2] - cu * mk<T>(v2.re, v2.im);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Vb[(long long)k * n + 3 * el + c] = to_op<Op>(vv[c]);
     }
     __syncwarp();
     T best = T(-1);
@@ -986,46 +1173,44 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
       pair_geo(ef, ed, i, je, g, band);
       UTAcc<R> acc;
       regular_pair<R>(acc, g, band, P);
+      cplx<T> uu[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         cplx<R> v = trac ? acc.t[3 * a + jc] : -acc.U(a, jc);
-        int ii = 3 * il + a;
-        cplx<T> vv = mk<T>(T(v.re), T(v.im));
-        for (int l = 0; l < k; ++l) {
-          Op ul = Ub[(long long)l * m + ii], vl = Vb[(long long)l * n + jstar];
-          vv = vv - mk<T>(ul.re, ul.im) * mk<T>(vl.re, vl.im);
-        }
-        Ub[(long long)k * m + ii] = to_op<Op>(vv);
+        uu[a] = mk<T>(T(v.re), T(v.im));
       }
+      const Op* ucol = Ub + 3 * il;
+#pragma unroll 4
+      for (int l = 0; l < k; ++l) {
+        Op vl = Vb[(long long)l * n + jstar];
+        const Op* ul = ucol + (long long)l * m;
+        Op u0 = ul[0], u1 = ul[1], u2 = ul[2];
+        cplx<T> cv = mk<T>(vl.re, vl.im);
+        uu[0] = uu[0] - mk<T>(u0.re, u0.im) * cv;
+        uu[1] = uu[1] - mk<T>(u1.re, u1.im) * cv;
+        uu[2] = uu[2] - mk<T>(u2.re, u2.im) * cv;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Ub[(long long)k * m + 3 * il + a] = to_op<Op>(uu[a]);
     }
     if (lane == 0) rows_used[k] = istar;
     __syncwarp();
     for (int l = lane; l < k; l += 32) Ub[(long long)k * m + rows_used[l]] = Op{};
     __syncwarp();
-    T cross = 0, nu2 = 0, nv2 = 0;
-    for (int l = 0; l <= k; ++l) {
-      T ur = 0, ui = 0, vr = 0, vi = 0;
-      for (int i = lane; i < m; i += 32) {
-        Op a = Ub[(long long)l * m + i], b2 = Ub[(long long)k * m + i];
-        ur += a.re * b2.re + a.im * b2.im;
-        ui += a.re * b2.im - a.im * b2.re;
-      }
-      for (int j = lane; j < n; j += 32) {
-        Op a = Vb[(long long)l * n + j], b2 = Vb[(long long)k * n + j];
-        vr += a.re * b2.re + a.im * b2.im;
-        vi += a.re * b2.im - a.im * b2.re;
-      }
-      ur = wsumT(ur);
-      ui = wsumT(ui);
-      vr = wsumT(vr);
-      vi = wsumT(vi);
-      if (l < k) cross += ur * vr - ui * vi;
-      else {
-        nu2 = ur;
-        nv2 = vr;
-      }
+    // Frobenius norm of the approximant estimated by its diagonal terms:
+    // ||S_k||^2 ~ sum_l |u_l|^2 |v_l|^2
+    T nu2 = 0, nv2 = 0;
+    for (int i = lane; i < m; i += 32) {
+      Op a = Ub[(long long)k * m + i];
+      nu2 += a.re * a.re + a.im * a.im;
     }
-    normS2 += T(2) * cross + nu2 * nv2;
+    for (int j = lane; j < n; j += 32) {
+      Op a = Vb[(long long)k * n + j];
+      nv2 += a.re * a.re + a.im * a.im;
+    }
+    nu2 = wsumT(nu2);
+    nv2 = wsumT(nv2);
+    normS2 += nu2 * nv2;
     ++k;
     if (nu2 * nv2 <= eps * eps * normS2) {
       converged = true;
@@ -1080,10 +1265,18 @@ void launch_static(const SingPair* pairs, int n, const ElemD* ed, const KParams<
                    cudaStream_t st) {
   if (count_if(n)) k_static<<<(n + 3) / 4, 128, 0, st>>>(pairs, n, ed, P, out);
 }
+void launch_pair_sort(const NearBlk* blks, int nblk, const ElemF* ef, const ElemD* ed, const long long* poff,
+                      unsigned* plist, int* pcount, cudaStream_t st) {
+  if (count_if(nblk)) k_pair_sort<<<nblk, 1024, 0, st>>>(blks, ef, ed, poff, plist, pcount);
+}
 template <typename R, typename Op>
-void launch_near_regular(const NearBlk* blks, int nblk, const ElemF* ef, const ElemD* ed,
-                         const signed char* bc, const KParams<R>& P, Op* near, cudaStream_t st) {
-  if (count_if(nblk)) k_near_regular<R, Op><<<nblk, 256, 0, st>>>(blks, ef, ed, bc, P, near);
+void launch_near_regular(const NearBlk* blks, int nblk, int max_nr, const unsigned* plist, const long long* poff,
+                         const int* pcount, const ElemF* ef, const ElemD* ed, const signed char* bc,
+                         const KParams<R>& P, Op* near, const float* patf, const double* patd, c128 pk, c128* b,
+                         cudaStream_t st) {
+  size_t sm = b ? 6 * sizeof(R) * max_nr : 0;
+  if (count_if(nblk))
+    k_near_regular<R, Op><<<nblk, 256, sm, st>>>(blks, plist, poff, pcount, ef, ed, bc, P, near, patf, patd, pk, b);
 }
 void launch_polar(const ElemD* ed, int ne, double* out, cudaStream_t st) {
   count_if(true);
@@ -1097,11 +1290,12 @@ void launch_sing(const SingPair* pairs, int n, const ElemD* ed, const double* po
     k_sing<R, Op><<<(n + 3) / 4, 128, 0, st>>>(pairs, n, ed, polar, bc, stat, P, near, pinv, pattern, pk, b, status);
 }
 template <typename R>
-void launch_rhs(int ne, const int* loaded, int nloaded, const ElemF* ef, const ElemD* ed,
-                const signed char* bc, const double* pattern, const KParams<R>& P, c128 pk, c128* b,
-                cudaStream_t st) {
-  count_if(true);
-  k_rhs<R><<<(ne + 7) / 8, 256, 0, st>>>(ne, loaded, nloaded, ef, ed, bc, pattern, P, pk, b);
+void launch_rhs_far(const void* items, int nitems, const FarBlk* far, const ElemF* ef, const ElemD* ed,
+                    const signed char* bc, const float* patf, const double* patd, const KParams<R>& P, c128 pk,
+                    c128* b, cudaStream_t st) {
+  if (count_if(nitems))
+    k_rhs_far<R><<<nitems, 256, 0, st>>>(reinterpret_cast<const RhsItem*>(items), far, ef, ed, bc, patf, patd, P, pk,
+                                         b);
 }
 template <typename R, typename Op>
 void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int* large_list, int nlarge,
@@ -1114,21 +1308,24 @@ void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int
         small_list, nsmall, blks, ef, ed, bc, P, U, V, rank, fails, eps);
 }
 
-template void launch_near_regular<float, c64>(const NearBlk*, int, const ElemF*, const ElemD*,
-                                              const signed char*, const KParams<float>&, c64*, cudaStream_t);
-template void launch_near_regular<double, c128>(const NearBlk*, int, const ElemF*, const ElemD*,
-                                                const signed char*, const KParams<double>&, c128*,
-                                                cudaStream_t);
+template void launch_near_regular<float, c64>(const NearBlk*, int, int, const unsigned*, const long long*,
+                                              const int*, const ElemF*, const ElemD*, const signed char*,
+                                              const KParams<float>&, c64*, const float*, const double*, c128, c128*,
+                                              cudaStream_t);
+template void launch_near_regular<double, c128>(const NearBlk*, int, int, const unsigned*, const long long*,
+                                                const int*, const ElemF*, const ElemD*, const signed char*,
+                                                const KParams<double>&, c128*, const float*, const double*, c128,
+                                                c128*, cudaStream_t);
 template void launch_sing<float, c64>(const SingPair*, int, const ElemD*, const double*, const signed char*,
                                       const double*, const KParams<float>&, c64*, c128*, const double*, c128,
                                       c128*, int*, cudaStream_t);
 template void launch_sing<double, c128>(const SingPair*, int, const ElemD*, const double*, const signed char*,
                                         const double*, const KParams<double>&, c128*, c128*, const double*, c128,
                                         c128*, int*, cudaStream_t);
-template void launch_rhs<float>(int, const int*, int, const ElemF*, const ElemD*, const signed char*,
-                                const double*, const KParams<float>&, c128, c128*, cudaStream_t);
-template void launch_rhs<double>(int, const int*, int, const ElemF*, const ElemD*, const signed char*,
-                                 const double*, const KParams<double>&, c128, c128*, cudaStream_t);
+template void launch_rhs_far<float>(const void*, int, const FarBlk*, const ElemF*, const ElemD*, const signed char*,
+                                    const float*, const double*, const KParams<float>&, c128, c128*, cudaStream_t);
+template void launch_rhs_far<double>(const void*, int, const FarBlk*, const ElemF*, const ElemD*, const signed char*,
+                                     const float*, const double*, const KParams<double>&, c128, c128*, cudaStream_t);
 template void launch_aca<float, c64>(const FarBlk*, const int*, int, const int*, int, const ElemF*, const ElemD*,
                                      const signed char*, const KParams<float>&, c64*, c64*, int*, int*, double,
                                      cudaStream_t);

@@ -153,6 +153,13 @@ struct bem_ctx {
   bem::DevBuf<bem::Task> tasks;
   bem::DevBuf<int> task_ptr;          // CSR of tasks over leaves
   bem::DevBuf<double> part;           // partial sums (sized for 4 rhs of complex FP64)
+  int max_nr = 0;                     // largest leaf (elements)
+  bem::DevBuf<long long> poff;        // per near block: offset of its sorted pair list
+  bem::DevBuf<unsigned> plist;        // sorted regular pairs of the near blocks
+  bem::DevBuf<int> pcount;            // regular pairs per near block
+  int nrhs_items = 0;
+  bem::DevBuf<int> rhs_items;         // (far block, first row) pairs for the far RHS
+  bem::DevBuf<float> patf;            // prescribed pattern (tree order, FP32)
   int nfar_small = 0, nfar_large = 0;
   bem::DevBuf<int> far_small, far_large;  // admissible block indices by size class
   bem::DevBuf<double> polar;          // ne x 27 self-rule polar parameters

@@ -15,18 +15,25 @@ void launch_sing_fill(const NearBlk* blks, int nblk, const ElemD* ed, const int*
                       cudaStream_t st);
 void launch_static(const SingPair* pairs, int n, const ElemD* ed, const KParams<double>& P, double* out,
                    cudaStream_t st);
+void launch_pair_sort(const NearBlk* blks, int nblk, const ElemF* ef, const ElemD* ed, const long long* poff,
+                      unsigned* plist, int* pcount, cudaStream_t st);
+// Regular near-field entries (near may be null) and, when b is given, the
+// near blocks' share of b += pk * B(s) pattern (atomic adds; b zeroed first).
 template <typename R, typename Op>
-void launch_near_regular(const NearBlk* blks, int nblk, const ElemF* ef, const ElemD* ed,
-                         const signed char* bc, const KParams<R>& P, Op* near, cudaStream_t st);
+void launch_near_regular(const NearBlk* blks, int nblk, int max_nr, const unsigned* plist, const long long* poff,
+                         const int* pcount, const ElemF* ef, const ElemD* ed, const signed char* bc,
+                         const KParams<R>& P, Op* near, const float* patf, const double* patd, c128 pk, c128* b,
+                         cudaStream_t st);
 void launch_polar(const ElemD* ed, int ne, double* out, cudaStream_t st);
 template <typename R, typename Op>
 void launch_sing(const SingPair* pairs, int n, const ElemD* ed, const double* polar, const signed char* bc,
                  const double* stat, const KParams<R>& P, Op* near, c128* pinv, const double* pattern, c128 pk,
                  c128* b, int* status, cudaStream_t st);
+// Far blocks' share of b += pk * B(s) pattern (items: far block, first row of 8).
 template <typename R>
-void launch_rhs(int ne, const int* loaded, int nloaded, const ElemF* ef, const ElemD* ed,
-                const signed char* bc, const double* pattern, const KParams<R>& P, c128 pk, c128* b,
-                cudaStream_t st);
+void launch_rhs_far(const void* items, int nitems, const FarBlk* far, const ElemF* ef, const ElemD* ed,
+                    const signed char* bc, const float* patf, const double* patd, const KParams<R>& P, c128 pk,
+                    c128* b, cudaStream_t st);
 // Admissible blocks split in two lists: small ones one warp each, large ones one CTA each.
 template <typename R, typename Op>
 void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int* large_list, int nlarge,

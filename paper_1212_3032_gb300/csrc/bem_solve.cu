@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) k_hmv_reduce(const int* __restrict__ leaf
   for (int r = threadIdx.x; r < rows; r += blockDim.x) {
 #pragma unroll
     for (int q = 0; q < NRHS; ++q) {
-      cplx<Acc> s{0, 0};
+      cplx<double> s{0, 0};  // task partials added in FP64
       for (int k = t0; k < t1; ++k) {
         cplx<Acc> v = part[q * pstride + tasks[k].slot + r];
         s.re += v.re;
@@ -226,6 +226,8 @@ void launch_hmatvec(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V
 
 template void launch_hmatvec<c64, c64, c64, float>(const bem_ctx*, const c64*, const c64*, const c64*,
                                                    cplx<float>*, const c64*, c64*, int, cudaStream_t);
+template void launch_hmatvec<c64, c64, c128, float>(const bem_ctx*, const c64*, const c64*, const c64*,
+                                                    cplx<float>*, const c64*, c128*, int, cudaStream_t);
 template void launch_hmatvec<c64, c128, c128, double>(const bem_ctx*, const c64*, const c64*, const c64*,
                                                       cplx<double>*, const c128*, c128*, int, cudaStream_t);
 template void launch_hmatvec<c128, c128, c128, double>(const bem_ctx*, const c128*, const c128*,
