@@ -297,13 +297,13 @@ def test_device_pointer_entry_points(ctx, B):
     ctx.mesh_dev(xyz, tri, bc, o)
     ctx.solve_sweep_dev(T, N, torch.tensor(inputs.heaviside_history(N), device=dev),
                         torch.tensor(mesh.pattern, device=dev), o)
-    # the right-hand side sums singular contributions with FP64 atomics, so two
-    # runs agree to rounding, not bitwise
+    # the right-hand side is summed with atomics (FP32 partial sums on the mixed
+    # path), so two runs agree to FP32 rounding, not bitwise
     for k in range(N // 2 + 1):
-        assert _rel(ctx.get_frequency_solution(k), a_host[k]) <= 1e-9
+        assert _rel(ctx.get_frequency_solution(k), a_host[k]) <= 2e-6
     out = torch.empty((N, 3 * mesh.ne), dtype=torch.float64, device=dev)
     ctx.time_response_dev(torch.arange(3 * mesh.ne, device=dev), out)
-    assert np.abs(out.cpu().numpy() - tr_host).max() <= 1e-9 * np.abs(tr_host).max()
+    assert np.abs(out.cpu().numpy() - tr_host).max() <= 2e-6 * np.abs(tr_host).max()
     with pytest.raises(B.BemError):
         ctx.time_response_dev(torch.tensor([0, 3 * mesh.ne], device=dev), torch.empty((N, 2), dtype=torch.float64,
                                                                                        device=dev))
