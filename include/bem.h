@@ -193,6 +193,27 @@ int bem_solve_assembled(bem_ctx* ctx, const double* b, const double* x0, double*
  * s = argmin ||A X s - b||; X is K x N complex (rows = previous solutions). */
 int bem_sem_guess(bem_ctx* ctx, int32_t K, const double* X, const double* b, double* a0);
 
+/* y = A x with the operator assembled by bem_assemble (complex64, mixed
+ * precision), for callers that cannot allocate device memory during a call:
+ * a framework whose caching allocator has reserved the device's memory up
+ * front, or a solver loop with hard latency bounds that cannot take the
+ * implicit synchronisation of cudaMalloc/cudaFree. The paper has no
+ * counterpart; this is a service entry point of the library.
+ *   x_dev, y_dev: DEVICE arrays of N complex64 values (interleaved float
+ *   re, im), caller's dof order, allocated by the caller; y must not alias x.
+ * The call allocates nothing: its scratch (two permuted vectors, the V^T x
+ * values of the low-rank blocks and the partial row sums) is one file-scope
+ * device array of 32 MiB that every GPU loading the library holds until the
+ * process exits. Operators whose scratch would exceed it are rejected with
+ * BEM_ERR_INVALID_ARG (the message gives the sizes). The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture. All calls share the one array and
+ * the last call's contents remain in it (nothing needs to start at zero):
+ * calls that overlap on the GPU, from any context or stream, race. The work
+ * is enqueued on the context's stream; the call does not synchronise it.
+ * Errors: STATE (not assembled, or complex128 operator), INVALID_ARG. */
+int bem_apply_noalloc(bem_ctx* ctx, const float* x_dev, float* y_dev);
+
 /* ---- measurement ------------------------------------------------------- */
 
 typedef struct bem_profile {

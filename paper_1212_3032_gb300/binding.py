@@ -28,7 +28,7 @@ EXPORTED = [
     "bem_set_material", "bem_set_window", "bem_solve_sweep", "bem_solve_sweep_dev",
     "bem_get_frequency_solution", "bem_time_response", "bem_time_response_dev", "bem_load_dft", "bem_idft",
     "bem_assemble", "bem_operator_rows", "bem_apply", "bem_rhs", "bem_solve_assembled", "bem_sem_guess",
-    "bem_set_profiling", "bem_get_profile",
+    "bem_set_profiling", "bem_get_profile", "bem_apply_noalloc",
 ]
 
 
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH):
         "bem_solve_assembled": (ctypes.c_int, [P, P, P, P, ctypes.POINTER(Opts), P]),
         "bem_sem_guess": (ctypes.c_int, [P, I32, P, P, P]),
         "bem_set_profiling": (ctypes.c_int, [P, ctypes.c_int]),
+        "bem_apply_noalloc": (ctypes.c_int, [P, P, P]),
         "bem_get_profile": (ctypes.c_int, [P, ctypes.POINTER(Profile)]),
     }
     for name, (res, args) in sig.items():
@@ -307,6 +308,13 @@ class Context:
         a0 = np.zeros_like(b)
         self._check(self.lib.bem_sem_guess(self.h, X.shape[0], _ptr(X) if X.size else None, _ptr(b), _ptr(a0)))
         return a0
+
+    def apply_noalloc(self, x_t, y_t):
+        """y = A x on device tensors (complex64, caller dof order); allocates nothing."""
+        for t in (x_t, y_t):
+            if str(t.dtype) != "torch.complex64" or t.numel() != 3 * self.ne:
+                raise ValueError("x and y must be complex64 tensors of 3 ne values")
+        self._check(self.lib.bem_apply_noalloc(self.h, _tptr(x_t), _tptr(y_t)))
 
     # --- measurement -------------------------------------------------------
     def set_profiling(self, on: bool):

@@ -48,6 +48,11 @@ template <typename Op, typename X, typename Y, typename Acc>
 void launch_hmatvec(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V, cplx<Acc>* t,
                     const X* x, Y* y, int nrhs, cudaStream_t st);
 
+// y = A x (c64 operator, FP32 accumulation, one right-hand side) with
+// caller-provided scratch: t (t_entries values) and part (part_rows values).
+void launch_hmatvec_scratch_c64(const bem_ctx* ctx, const c64* near, const c64* U, const c64* V, cplx<float>* t,
+                                cplx<float>* part, const c64* x, c64* y, cudaStream_t st);
+
 // z = M^{-1} v per element (3x3 inverse diagonal blocks)
 template <typename Pm, typename V, typename Z>
 void launch_precond(const Pm* pinv, const V* v, Z* z, int ne, cudaStream_t st);

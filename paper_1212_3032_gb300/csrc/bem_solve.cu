@@ -224,6 +224,24 @@ void launch_hmatvec(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V
   }
 }
 
+// Same product (c64 operator, FP32 accumulation, one right-hand side) with
+// caller-provided scratch for the t = V^T x values and the per-task partial
+// row sums (sizes t_entries and part_rows complex64).
+void launch_hmatvec_scratch_c64(const bem_ctx* ctx, const c64* near, const c64* U, const c64* V, cplx<float>* t,
+                                cplx<float>* part, const c64* x, c64* y, cudaStream_t st) {
+  int nfar = (int)ctx->far_h.size();
+  if (count_if(nfar))
+    k_hmv_t<c64, c64, float, 1><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, V, x, ctx->N, t, ctx->t_entries);
+  size_t sm = (size_t)HMV_THREADS * sizeof(cplx<float>);
+  count_if(true);
+  k_hmv_tasks<c64, c64, float, 1><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
+      ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t, ctx->t_entries, x, ctx->N,
+      part, ctx->part_rows);
+  count_if(true);
+  k_hmv_reduce<float, c64, 1><<<ctx->nleaves, 256, 0, st>>>(ctx->leaf_r0.p, ctx->leaf_nr.p, ctx->task_ptr.p,
+                                                           ctx->tasks.p, part, ctx->part_rows, ctx->N, y);
+}
+
 template void launch_hmatvec<c64, c64, c64, float>(const bem_ctx*, const c64*, const c64*, const c64*,
                                                    cplx<float>*, const c64*, c64*, int, cudaStream_t);
 template void launch_hmatvec<c64, c64, c128, float>(const bem_ctx*, const c64*, const c64*, const c64*,
