@@ -173,17 +173,33 @@ __device__ __forceinline__ void pair_geo(const ElemF* ef, const ElemD* ed, int i
   band = (i == e) ? BAND_SELF : band_of<double>(d2, E.h2);
 }
 
-// Regular-band integral of a pair (bands Q4, Q2, Q1).
+// Regular-band integral of a pair (bands Q4, Q2, Q1): one loop over the
+// points of the band's rule, so the point evaluator is inlined once (keeps
+// the kernels' instruction footprint small).
 template <typename R>
 __device__ __forceinline__ void regular_pair(UTAcc<R>& acc, const PairGeo<R>& g, int band,
                                              const KParams<R>& P) {
   acc.zero();
-  if (band == BAND_Q4) {
-    integrate_collapsed<R, 4>(acc, g.o0, g.e1, g.e2, g.area2, g.n, P);
-  } else if (band == BAND_Q2) {
-    integrate_collapsed<R, 2>(acc, g.o0, g.e1, g.e2, g.area2, g.n, P);
-  } else {
-    accumulate_point<R>(acc, g.d[0], g.d[1], g.d[2], g.n[0], g.n[1], g.n[2], R(0.5) * g.area2, P);
+  const int Q = band == BAND_Q4 ? 4 : (band == BAND_Q2 ? 2 : 1);
+#pragma unroll 1
+  for (int p = 0; p < Q * Q; ++p) {
+    R rx, ry, rz, w;
+    if (Q == 1) {
+      rx = g.d[0];
+      ry = g.d[1];
+      rz = g.d[2];
+      w = R(0.5) * g.area2;
+    } else {
+      const int a = p / Q, b = p - (p / Q) * Q;
+      const R u = gl_x<R>(Q, a);
+      const R omu = R(1) - u;
+      const R v = omu * gl_x<R>(Q, b);
+      w = g.area2 * gl_w<R>(Q, a) * gl_w<R>(Q, b) * omu;
+      rx = g.o0[0] + u * g.e1[0] + v * g.e2[0];
+      ry = g.o0[1] + u * g.e1[1] + v * g.e2[1];
+      rz = g.o0[2] + u * g.e1[2] + v * g.e2[2];
+    }
+    accumulate_point<R>(acc, rx, ry, rz, g.n[0], g.n[1], g.n[2], w, P);
   }
 }
 
@@ -760,20 +776,29 @@ __global__ void k_sing(const SingPair* __restrict__ pairs, int npairs, const Ele
 // Traction-loaded columns need U only (B = U); displacement-loaded columns
 // need T (B = -T).
 // ---------------------------------------------------------------------------
-template <typename R, int Q>
-__device__ __forceinline__ void integrate_collapsed_u(cplx<R>* u, const R* o0, const R* e1, const R* e2, R area2,
-                                                      const KParams<R>& P) {
-#pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    R uu = gl_x<R>(Q, a), wu = gl_w<R>(Q, a);
-    R omu = R(1) - uu;
-#pragma unroll
-    for (int bq = 0; bq < Q; ++bq) {
-      R v = omu * gl_x<R>(Q, bq);
-      R w = area2 * wu * gl_w<R>(Q, bq) * omu;
-      accumulate_point_u<R>(u, o0[0] + uu * e1[0] + v * e2[0], o0[1] + uu * e1[1] + v * e2[1],
-                            o0[2] + uu * e1[2] + v * e2[2], w, P);
+// U-only integral of a pair over its band's rule (one inlined evaluator).
+template <typename R>
+__device__ __forceinline__ void regular_pair_u(cplx<R>* u, const PairGeo<R>& g, int band, const KParams<R>& P) {
+  const int Q = band == BAND_Q4 ? 4 : (band == BAND_Q2 ? 2 : 1);
+#pragma unroll 1
+  for (int p = 0; p < Q * Q; ++p) {
+    R rx, ry, rz, w;
+    if (Q == 1) {
+      rx = g.d[0];
+      ry = g.d[1];
+      rz = g.d[2];
+      w = R(0.5) * g.area2;
+    } else {
+      const int a = p / Q, b = p - (p / Q) * Q;
+      const R uu = gl_x<R>(Q, a);
+      const R omu = R(1) - uu;
+      const R v = omu * gl_x<R>(Q, b);
+      w = g.area2 * gl_w<R>(Q, a) * gl_w<R>(Q, b) * omu;
+      rx = g.o0[0] + uu * g.e1[0] + v * g.e2[0];
+      ry = g.o0[1] + uu * g.e1[1] + v * g.e2[1];
+      rz = g.o0[2] + uu * g.e1[2] + v * g.e2[2];
     }
+    accumulate_point_u<R>(u, rx, ry, rz, w, P);
   }
 }
 
@@ -810,9 +835,7 @@ __global__ void __launch_bounds__(256) k_rhs_far(const RhsItem* __restrict__ ite
       cplx<R> u[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) u[k] = mk<R>(0, 0);
-      if (band == BAND_Q4) integrate_collapsed_u<R, 4>(u, g.o0, g.e1, g.e2, g.area2, P);
-      else if (band == BAND_Q2) integrate_collapsed_u<R, 2>(u, g.o0, g.e1, g.e2, g.area2, P);
-      else accumulate_point_u<R>(u, g.d[0], g.d[1], g.d[2], R(0.5) * g.area2, P);
+      regular_pair_u<R>(u, g, band, P);
       const int idx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
 #pragma unroll
       for (int a = 0; a < 3; ++a)
