@@ -434,10 +434,13 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
     nb.nr = t.size();
     nb.c0 = s.begin;
     nb.nc = s.size();
-    noff += 9LL * nb.nr * nb.nc;
+    nb.ld = 3 * nb.nr + ((3 * nb.nr) & 1);
+    noff += (long long)nb.ld * 3 * nb.nc;
+    noff += noff & 1;
     ctx->near_h.push_back(nb);
   }
   ctx->near_entries = noff;
+  ctx->near_zero_pending = true;
   long long uoff = 0, voff = 0;
   int toff = 0;
   for (const BlockPair& bp : tr.far) {
@@ -491,7 +494,7 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
     int l = leaf_idx[tr.near[b].tau];
     Panel p;
     p.data = nb.off;
-    p.ld = 3 * nb.nr;
+    p.ld = nb.ld;
     p.ncols = 3 * nb.nc;
     p.xoff = 3 * nb.c0;
     p.kind = 0;
@@ -527,25 +530,44 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   long long slot = 0;
   for (int l = 0; l < L; ++l) {
     tptr[l] = (int)tk.size();
-    int p = pptr[l];
-    while (p < pptr[l + 1]) {
-      Task t;
-      t.leaf = l;
-      t.p0 = p;
-      t.slot = (int)slot;
-      int cols = 0;
-      do {
-        const Panel& P = pan[p];
-        cols += P.kind == 0 ? P.ncols : ctx->far_h[P.xoff].rmax;
-        ++p;
-      } while (p < pptr[l + 1] && cols < TASK_COLS);
-      t.p1 = p;
-      slot += 3LL * nr[l];
-      tk.push_back(t);
+    for (int kind = 0; kind < 2; ++kind) {
+      int p = pptr[l];
+      while (p < pptr[l + 1]) {
+        if (pan[p].kind != kind) {
+          ++p;
+          continue;
+        }
+        Task t;
+        t.leaf = l;
+        t.kind = kind;
+        t.slot = (int)slot;
+        t.p0 = p;
+        int cols = 0;
+        // panels of one kind are contiguous in a leaf's list (near first, then far)
+        while (p < pptr[l + 1] && pan[p].kind == kind && cols < TASK_COLS) {
+          cols += kind == 0 ? pan[p].ncols : ctx->far_h[pan[p].xoff].rmax;
+          ++p;
+        }
+        t.p1 = p;
+        slot += 3LL * nr[l] + 1;  // +1: a near task writes an even number of rows
+        tk.push_back(t);
+      }
     }
   }
   tptr[L] = (int)tk.size();
   ctx->ntasks = (int)tk.size();
+  {
+    std::vector<int> nt, ft;
+    for (int i = 0; i < (int)tk.size(); ++i) (tk[i].kind == 0 ? nt : ft).push_back(i);
+    ctx->n_near_tasks = (int)nt.size();
+    ctx->n_far_tasks = (int)ft.size();
+    BEM_CUDA_TRY(ctx->near_tasks.alloc(std::max<size_t>(1, nt.size())));
+    BEM_CUDA_TRY(ctx->far_tasks.alloc(std::max<size_t>(1, ft.size())));
+    if (!nt.empty())
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->near_tasks.p, nt.data(), nt.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!ft.empty())
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->far_tasks.p, ft.data(), ft.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
   ctx->part_rows = slot;
   BEM_CUDA_TRY(ctx->tasks.alloc(std::max<size_t>(1, tk.size())));
   BEM_CUDA_TRY(ctx->task_ptr.alloc(L + 1));
@@ -714,7 +736,12 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
     CK("rhs_far");
   }
   if (is_mixed(ctx)) {
+    if (ctx->near32.n < (size_t)std::max<long long>(1, ctx->near_entries)) ctx->near_zero_pending = true;
     BEM_CUDA_TRY(ctx->near32.ensure(std::max<long long>(1, ctx->near_entries)));
+    if (ctx->near_zero_pending) {
+      BEM_CUDA_TRY(cudaMemsetAsync(ctx->near32.p, 0, ctx->near32.n * sizeof(c64), st));
+      ctx->near_zero_pending = false;
+    }
     BEM_CUDA_TRY(ctx->u32.ensure(std::max<long long>(1, ctx->u_entries)));
     BEM_CUDA_TRY(ctx->v32.ensure(std::max<long long>(1, ctx->v_entries)));
     BEM_CUDA_TRY(ctx->t32.ensure(4LL * std::max(1, ctx->t_entries)));
@@ -737,7 +764,12 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
     k_pinv_cast<<<(unsigned)((n9 + 255) / 256), 256, 0, st>>>(ctx->prec_inv.p, ctx->prec_inv32.p, n9);
     CK("pinv_cast");
   } else {
+    if (ctx->near64.n < (size_t)std::max<long long>(1, ctx->near_entries)) ctx->near_zero_pending = true;
     BEM_CUDA_TRY(ctx->near64.ensure(std::max<long long>(1, ctx->near_entries)));
+    if (ctx->near_zero_pending) {
+      BEM_CUDA_TRY(cudaMemsetAsync(ctx->near64.p, 0, ctx->near64.n * sizeof(c128), st));
+      ctx->near_zero_pending = false;
+    }
     BEM_CUDA_TRY(ctx->u64.ensure(std::max<long long>(1, ctx->u_entries)));
     BEM_CUDA_TRY(ctx->v64.ensure(std::max<long long>(1, ctx->v_entries)));
     BEM_CUDA_TRY(ctx->t64.ensure(4LL * std::max(1, ctx->t_entries)));
@@ -1139,7 +1171,7 @@ extern "C" int bem_operator_rows(bem_ctx* ctx, const int64_t* rows, int64_t nrow
     std::vector<c128> rowt(N, c128{0, 0});
     for (const NearBlk& nb : ctx->near_h) {
       if (et < nb.r0 || et >= nb.r0 + nb.nr) continue;
-      long long ld = 3LL * nb.nr, lr = rt - 3LL * nb.r0;
+      long long ld = nb.ld, lr = rt - 3LL * nb.r0;
       for (int c = 0; c < 3 * nb.nc; ++c) rowt[3LL * nb.c0 + c] = nearv[nb.off + c * ld + lr];
     }
     for (size_t b = 0; b < ctx->far_h.size(); ++b) {

@@ -246,7 +246,7 @@ __global__ void k_sing_fill(const NearBlk* __restrict__ blks, const ElemD* __res
                             const int* __restrict__ offs, SingPair* __restrict__ out) {
   NearBlk B = blks[blockIdx.x];
   int np = B.nr * B.nc;
-  int ld = 3 * B.nr;
+  int ld = B.ld;
   __shared__ int warp_tot[32];
   __shared__ int base;
   if (threadIdx.x == 0) base = offs[blockIdx.x];
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(256) k_near_regular(const NearBlk* __restrict_
   const NearBlk B = blks[blockIdx.x];
   const int cnt = pcount[blockIdx.x];
   const long long base = poff[blockIdx.x];
-  const long long ld = 3 * B.nr;
+  const long long ld = B.ld;
   if (b)
     for (int r = threadIdx.x; r < 6 * B.nr; r += blockDim.x) rsum[r] = R(0);
   __syncthreads();

@@ -32,11 +32,14 @@ struct ElemD {
   double h2;
 };
 
-// Dense near-field block (tau rows x sigma cols), column-major, ld = 3 * nr.
+// Dense near-field block (tau rows x sigma cols), column-major with the
+// leading dimension ld = 3 nr rounded up to even and an even offset (16-byte
+// aligned columns); the padding row is zero.
 struct NearBlk {
-  long long off;  // offset in the near-field array (entries)
+  long long off;  // offset in the near-field array (entries, even)
   int r0, nr;     // row cluster: first tree element, element count
   int c0, nc;     // column cluster
+  int ld;         // leading dimension (even, >= 3 nr)
 };
 
 // Low-rank far-field block A ~ U V^T; U: (3 nr) x rmax column-major,
@@ -63,8 +66,9 @@ struct Panel {
 // of the partial buffer and are added up per leaf in a fixed order.
 struct Task {
   int leaf;
-  int p0, p1;  // panel range
+  int p0, p1;  // panel range (all near panels, or all far panels)
   int slot;
+  int kind;    // 0: near panels, 1: far panels
 };
 
 // Singular (SELF) and near-singular (NEAR) element pairs, FP64 path.
@@ -151,6 +155,8 @@ struct bem_ctx {
   int ntasks = 0;
   long long part_rows = 0;            // rows of the partial buffer per right-hand side
   bem::DevBuf<bem::Task> tasks;
+  int n_near_tasks = 0, n_far_tasks = 0;
+  bem::DevBuf<int> near_tasks, far_tasks;  // task indices by kind
   bem::DevBuf<int> task_ptr;          // CSR of tasks over leaves
   bem::DevBuf<double> part;           // partial sums (sized for 4 rhs of complex FP64)
   int max_nr = 0;                     // largest leaf (elements)
@@ -174,6 +180,7 @@ struct bem_ctx {
   int prec = BEM_PREC_C64_MIXED;
   bool assembled = false;
   double s_re = 0, s_im = 0;
+  bool near_zero_pending = true;       // zero the near storage once after (re)allocation (padding rows)
   bem::DevBuf<bem::c64> near32, u32, v32, t32;
   bem::DevBuf<bem::c128> near64, u64, v64, t64;
   bem::DevBuf<int> rank;

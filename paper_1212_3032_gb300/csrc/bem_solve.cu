@@ -27,6 +27,16 @@ template <typename Acc, typename T> __device__ __forceinline__ cplx<Acc> up(cons
   return cplx<Acc>{Acc(v.re), Acc(v.im)};
 }
 
+// streaming (evict-first) loads of operator entries, read once per product
+__device__ __forceinline__ c64 ld_stream(const c64* p) {
+  float2 v = __ldcs(reinterpret_cast<const float2*>(p));
+  return c64{v.x, v.y};
+}
+__device__ __forceinline__ c128 ld_stream(const c128* p) {
+  double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+  return c128{v.x, v.y};
+}
+
 template <typename Acc>
 __device__ __forceinline__ void cmac(cplx<Acc>& acc, const cplx<Acc>& a, const cplx<Acc>& b) {
   acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
@@ -43,30 +53,53 @@ template <typename Acc> __device__ __forceinline__ Acc wsum(Acc v) {
 // phase 1: t_b = V_b^T x_sigma
 // ---------------------------------------------------------------------------
 template <typename Op, typename X, typename Acc, int NRHS>
-__global__ void __launch_bounds__(256) k_hmv_t(const FarBlk* __restrict__ blks, const int* __restrict__ rank,
-                                               const Op* __restrict__ V, const X* __restrict__ x, long long N,
-                                               cplx<Acc>* __restrict__ t, int tstride) {
-  FarBlk B = blks[blockIdx.x];
-  int r = rank[blockIdx.x];
+__device__ __forceinline__ void hmv_t_block(int bi, const FarBlk* __restrict__ blks, const int* __restrict__ rank,
+                                            const Op* __restrict__ V, const X* __restrict__ x, long long N,
+                                            cplx<Acc>* __restrict__ t, int tstride) {
+  // one warp per 4 factor columns: 4 independent coalesced column streams in flight
+  constexpr int C = 4;
+  FarBlk B = blks[bi];
+  int r = rank[bi];
   int n = 3 * B.nc;
   const X* xs = x + 3LL * B.c0;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int l = warp; l < r; l += nw) {
-    const Op* col = V + B.voff + (long long)l * n;
-    cplx<Acc> acc[NRHS];
+  for (int l0 = warp * C; l0 < r; l0 += nw * C) {
+    const int nc = min(C, r - l0);
+    const Op* col = V + B.voff + (long long)l0 * n;
+    cplx<Acc> acc[C][NRHS];
 #pragma unroll
-    for (int q = 0; q < NRHS; ++q) acc[q] = cplx<Acc>{0, 0};
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int q = 0; q < NRHS; ++q) acc[c][q] = cplx<Acc>{0, 0};
     for (int j = lane; j < n; j += 32) {
-      cplx<Acc> v = up<Acc>(col[j]);
+      cplx<Acc> xv[NRHS];
 #pragma unroll
-      for (int q = 0; q < NRHS; ++q) cmac(acc[q], v, up<Acc>(xs[q * N + j]));
+      for (int q = 0; q < NRHS; ++q) xv[q] = up<Acc>(xs[q * N + j]);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        if (c < nc) {
+          cplx<Acc> v = up<Acc>(col[(long long)c * n + j]);
+#pragma unroll
+          for (int q = 0; q < NRHS; ++q) cmac(acc[c][q], v, xv[q]);
+        }
+      }
     }
 #pragma unroll
-    for (int q = 0; q < NRHS; ++q) {
-      Acc re = wsum(acc[q].re), im = wsum(acc[q].im);
-      if (lane == 0) t[(long long)q * tstride + B.toff + l] = cplx<Acc>{re, im};
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+      for (int q = 0; q < NRHS; ++q) {
+        Acc re = wsum(acc[c][q].re), im = wsum(acc[c][q].im);
+        if (lane == 0 && c < nc) t[(long long)q * tstride + B.toff + l0 + c] = cplx<Acc>{re, im};
+      }
     }
   }
+}
+
+template <typename Op, typename X, typename Acc, int NRHS>
+__global__ void __launch_bounds__(256) k_hmv_t(const FarBlk* __restrict__ blks, const int* __restrict__ rank,
+                                               const Op* __restrict__ V, const X* __restrict__ x, long long N,
+                                               cplx<Acc>* __restrict__ t, int tstride) {
+  hmv_t_block<Op, X, Acc, NRHS>(blockIdx.x, blks, rank, V, x, N, t, tstride);
 }
 
 // ---------------------------------------------------------------------------
@@ -79,14 +112,11 @@ __global__ void __launch_bounds__(256) k_hmv_t(const FarBlk* __restrict__ blks, 
 constexpr int HMV_THREADS = 384;
 
 template <typename Op, typename X, typename Acc, int NRHS>
-__global__ void __launch_bounds__(HMV_THREADS) k_hmv_tasks(
-    const Task* __restrict__ tasks, const int* __restrict__ leaf_nr, const Panel* __restrict__ panels,
+__device__ __forceinline__ void hmv_task(
+    const Task tk, const int* __restrict__ leaf_nr, const Panel* __restrict__ panels,
     const FarBlk* __restrict__ far, const int* __restrict__ rank, const Op* __restrict__ near,
     const Op* __restrict__ U, const cplx<Acc>* __restrict__ t, int tstride, const X* __restrict__ x, long long N,
-    cplx<Acc>* __restrict__ part, long long pstride) {
-  extern __shared__ unsigned char smem_raw[];
-  cplx<Acc>* red = reinterpret_cast<cplx<Acc>*>(smem_raw);
-  const Task tk = tasks[blockIdx.x];
+    cplx<Acc>* __restrict__ part, long long pstride, cplx<Acc>* red) {
   const int rows = 3 * leaf_nr[tk.leaf];
   for (int rbase = 0; rbase < rows; rbase += blockDim.x) {
     const int rcount = min(rows - rbase, (int)blockDim.x);
@@ -105,17 +135,23 @@ __global__ void __launch_bounds__(HMV_THREADS) k_hmv_tasks(
           const Op* d = near + P.data + r;
           const X* xs = x + P.xoff;
           const int nc = P.ncols;
+          const long long step = (long long)G * ld;
           int j = g;
-          for (; j + 7 * G < nc; j += 8 * G) {
-            cplx<Acc> a[8];
+          const Op* dp = d + (long long)g * ld;
+          for (; j + 7 * G < nc; j += 8 * G, dp += 8 * step) {
+            // all 8 column entries and x values of this group in flight before any FMA
+            Op av[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) a[u] = up<Acc>(d[(long long)(j + u * G) * ld]);
+            for (int u = 0; u < 8; ++u) av[u] = ld_stream(dp + u * step);
+            X xv[NRHS][8];
 #pragma unroll
-            for (int q = 0; q < NRHS; ++q) {
-              const X* xq = xs + q * N;
+            for (int q = 0; q < NRHS; ++q)
 #pragma unroll
-              for (int u = 0; u < 8; ++u) cmac(acc[q], a[u], up<Acc>(xq[j + u * G]));
-            }
+              for (int u = 0; u < 8; ++u) xv[q][u] = xs[q * N + j + u * G];
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+              for (int u = 0; u < 8; ++u) cmac(acc[q], up<Acc>(av[u]), up<Acc>(xv[q][u]));
           }
           for (; j < nc; j += G) {
             cplx<Acc> a0 = up<Acc>(d[(long long)j * ld]);
@@ -169,6 +205,18 @@ __global__ void __launch_bounds__(HMV_THREADS) k_hmv_tasks(
   }
 }
 
+template <typename Op, typename X, typename Acc, int NRHS>
+__global__ void __launch_bounds__(HMV_THREADS, 2) k_hmv_tasks(
+    const Task* __restrict__ tasks, const int* __restrict__ leaf_nr, const Panel* __restrict__ panels,
+    const FarBlk* __restrict__ far, const int* __restrict__ rank, const Op* __restrict__ near,
+    const Op* __restrict__ U, const cplx<Acc>* __restrict__ t, int tstride, const X* __restrict__ x, long long N,
+    cplx<Acc>* __restrict__ part, long long pstride) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<Acc>* red = reinterpret_cast<cplx<Acc>*>(smem_raw);
+  hmv_task<Op, X, Acc, NRHS>(tasks[blockIdx.x], leaf_nr, panels, far, rank, near, U, t, tstride, x, N, part, pstride,
+                             red);
+}
+
 // phase 3: y[rows of leaf] = sum over the leaf's tasks, in task order
 template <typename Acc, typename Y, int NRHS>
 __global__ void __launch_bounds__(256) k_hmv_reduce(const int* __restrict__ leaf_r0, const int* __restrict__ leaf_nr,
@@ -203,7 +251,7 @@ static void hmv_impl(const bem_ctx* ctx, const Op* near, const Op* U, const Op* 
   if (count_if(nfar)) k_hmv_t<Op, X, Acc, NRHS><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, V, x, ctx->N, t,
                                                                        ctx->t_entries);
   cplx<Acc>* part = reinterpret_cast<cplx<Acc>*>(ctx->part.p);
-  size_t sm = (size_t)HMV_THREADS * NRHS * sizeof(cplx<Acc>);
+  size_t sm = (size_t)2 * HMV_THREADS * NRHS * sizeof(cplx<Acc>);
   count_if(true);
   k_hmv_tasks<Op, X, Acc, NRHS><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
       ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t, ctx->t_entries, x, ctx->N,
@@ -232,7 +280,7 @@ void launch_hmatvec_scratch_c64(const bem_ctx* ctx, const c64* near, const c64* 
   int nfar = (int)ctx->far_h.size();
   if (count_if(nfar))
     k_hmv_t<c64, c64, float, 1><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, V, x, ctx->N, t, ctx->t_entries);
-  size_t sm = (size_t)HMV_THREADS * sizeof(cplx<float>);
+  size_t sm = (size_t)2 * HMV_THREADS * sizeof(cplx<float>);
   count_if(true);
   k_hmv_tasks<c64, c64, float, 1><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
       ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t, ctx->t_entries, x, ctx->N,
@@ -316,7 +364,8 @@ __global__ void k_dots(const Vb* __restrict__ V, long long ldv, const W* __restr
 }
 template <typename Vb, typename W>
 int launch_dots(const Vb* V, long long ldv, int nvec, const W* w, long long n, c128* part, cudaStream_t st) {
-  int nblk = (int)std::min<long long>(std::max<long long>(1, n / 4096), 64);
+  // enough blocks in total (nblk x nvec) to cover the GPU, two elements per thread
+  int nblk = (int)std::min<long long>(std::max<long long>(1, (n + 511) / 512), 64);
   dim3 grid(nblk, nvec);
   count_if(true);
   k_dots<Vb, W><<<grid, 256, 0, st>>>(V, ldv, w, n, part);
