@@ -180,6 +180,25 @@ def run_reference(args, cfg):
     print(json.dumps(out))
 
 
+GUESS_LABEL = {
+    "sem": "SEM K=4",
+    "zero": "zero",
+    "mlp": "SEM K=4 + learned column (online Adam, 4 steps/frequency; weights carried over from earlier sweeps)",
+}
+
+
+def profile_case(ctx, binding, mesh, cfg, opts):
+    """One frequency of the workload (k = n_omega / 4): mesh, assembly, right-hand
+    side and one GMRES solve, for profiler captures of single launches."""
+    s = cfg["eta"] + 1j * (cfg["n_omega"] // 4) * 2 * math.pi / cfg["T"]
+    ctx.mesh(mesh.xyz, mesh.tri, mesh.bc_type, opts)
+    ctx.assemble(s, opts)
+    b = ctx.rhs(1.0, mesh.pattern)
+    _, st = ctx.solve_assembled(b, opts=opts)
+    print(json.dumps({"profile_case": True, "s": [s.real, s.imag], "iters": st["iters"],
+                      "rel_residual": st["rel_residual"]}))
+
+
 def run_ours(args, cfg):
     import torch
 
@@ -201,8 +220,11 @@ def run_ours(args, cfg):
     n_omega = cfg["n_omega"]
     nf = n_omega // 2 + 1
     load = inputs.heaviside_history(n_omega)
+    guess = {"sem": binding.GUESS_SEM, "mlp": binding.GUESS_MLP, "zero": binding.GUESS_ZERO}[args.guess]
     opts = binding.default_opts(leaf_size=cfg["leaf"], aca_tol=cfg["aca_tol"], tol=cfg["tol"],
-                                precision=binding.PREC_C64_MIXED, guess=binding.GUESS_SEM, sem_k=4)
+                                precision=binding.PREC_C64_MIXED, guess=guess, sem_k=4)
+    if args.profile_case:
+        return profile_case(ctx, binding, mesh, cfg, opts)
     # device-resident inputs
     xyz_t = torch.tensor(mesh.xyz, dtype=torch.float64, device=dev)
     tri_t = torch.tensor(mesh.tri, dtype=torch.int32, device=dev)
@@ -297,10 +319,13 @@ def run_ours(args, cfg):
         "dtype": "c64 (FP32 kernel evaluation; FP64 singular, Arnoldi, refinement)", "data": "synthetic",
         "config": {"workload": args.workload, "triangles": mesh.ne, "unknowns": N, "n_omega": n_omega,
                    "solves_per_step": nf, "T": cfg["T"], "eta": cfg["eta"], "window": "hanning",
-                   "aca_tol": cfg["aca_tol"], "leaf": cfg["leaf"], "gmres_tol": cfg["tol"], "guess": "SEM K=4",
+                   "aca_tol": cfg["aca_tol"], "leaf": cfg["leaf"], "gmres_tol": cfg["tol"],
+                   "guess": GUESS_LABEL[args.guess],
                    "l2": "flushed (256 MB write) before every timed step"},
         "gmres_iters_per_step": iters / args.steps, "unconverged": unconverged,
-        "roofline": {"kernel": "H-matrix product (k_hmv_t + k_hmv_rows)", "bound": "hbm", "achieved": hmv_gbs,
+        "guess_residual_mean": statistics.fmean(s["guess_residual"] for s in stats[1:]),
+        "sem_residual_mean": statistics.fmean(s["sem_residual"] for s in stats[1:]),
+        "roofline": {"kernel": "H-matrix product (k_hmv_t + k_hmv_tasks + k_hmv_reduce)", "bound": "hbm", "achieved": hmv_gbs,
                      "peak": peak, "unit": "GB/s", "frac": (hmv_gbs / peak) if hmv_gbs else None,
                      "peak_source": peak_kind, "traffic": None,
                      "launches": prof["hmv_launches"], "ms_total": prof["hmv_ms"]},
@@ -324,6 +349,9 @@ def main():
     ap.add_argument("--workload", default="cavity5120", choices=sorted(WORKLOADS))
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--guess", default="sem", choices=["sem", "mlp", "zero"])
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one frequency (assembly + one solve) and exit; for profiler captures")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
     if args.impl == "reference":

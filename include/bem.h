@@ -67,6 +67,9 @@ extern "C" {
 /* initial guess of each frequency system */
 #define BEM_GUESS_ZERO 0
 #define BEM_GUESS_SEM 1 /* least-squares solution extrapolation (Sec. 4.2) */
+#define BEM_GUESS_MLP 2 /* Sec. 4.2 extrapolation over the previous solutions
+                           plus one learned proposal column (bem_mlp_*); the
+                           paper has no learned guess */
 
 typedef struct bem_ctx bem_ctx;
 
@@ -98,6 +101,11 @@ typedef struct bem_freq_stats {
   int64_t far_bytes;      /* bytes of low-rank factors actually used */
   int32_t max_rank;
   int32_t aca_failures;   /* far blocks that hit the rank cap */
+  double sem_residual;    /* least-squares residual ||b - A a0|| / ||b|| of the
+                             extrapolation over the previous solutions alone
+                             (products in the operator's precision); with
+                             BEM_GUESS_MLP, compare with guess_residual to see
+                             what the learned column added; 1 without a guess */
 } bem_freq_stats;
 
 /* Fill *opts with the defaults: tol 1e-5, restart 50, max_iters 5000,
@@ -213,6 +221,41 @@ int bem_sem_guess(bem_ctx* ctx, int32_t K, const double* X, const double* b, dou
  * is enqueued on the context's stream; the call does not synchronise it.
  * Errors: STATE (not assembled, or complex128 operator), INVALID_ARG. */
 int bem_apply_noalloc(bem_ctx* ctx, const float* x_dev, float* y_dev);
+
+/* ---- learned initial guess (BEM_GUESS_MLP) ---------------------------------
+ * The paper's extrapolation (Sec. 4.2) fits a_k^(0) in the span of the last
+ * K solutions. The learned guess adds one candidate column p_k to that span,
+ * so its least-squares residual is never above the plain extrapolation's.
+ * p_k comes from a pointwise network applied to every unknown d:
+ *   x(d) = [Re, Im of a_{k-1..k-4}(d) / S] (8), Re(s_k) dt, Im(s_k) dt,
+ *   S = max_d |a_{k-1}(d)|, dt = T / n_omega;
+ *   y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3, p_k(d) = S (y0 + i y1),
+ * widths 10 -> 256 -> 256 -> 2. Parameters: one float vector of
+ * bem_mlp_num_params() values in the order W1 (256 x 10, row-major), b1 (256),
+ * W2 (256 x 256), b2 (256), W3 (2 x 256), b3 (2). The products use the weight
+ * matrices rounded to bfloat16 (round to nearest even) with FP32
+ * accumulation; biases and the Adam state stay FP32. During a sweep with
+ * BEM_GUESS_MLP the network proposes for k >= 4 and, after frequency k is
+ * solved, takes `steps` Adam steps (beta 0.9, 0.999, eps 1e-8) on the mean
+ * over unknowns of |y - a_k / S|^2 (the two outputs summed). The weights
+ * persist in the context across sweeps; without bem_mlp_init or
+ * bem_mlp_set_weights they start from a Glorot-uniform draw with seed 3032. */
+int64_t bem_mlp_num_params(void);
+/* Glorot-uniform weights from `seed`, zero biases, Adam state reset. */
+int bem_mlp_init(bem_ctx* ctx, uint64_t seed);
+/* Adam steps per solved frequency (>= 0; 0 freezes the weights) and the
+ * learning rate (>= 0). Defaults 4 and 1e-3. */
+int bem_mlp_set_training(bem_ctx* ctx, int32_t steps_per_frequency, double lr);
+/* Copy n = bem_mlp_num_params() host floats in / out; set resets Adam. */
+int bem_mlp_set_weights(bem_ctx* ctx, const float* theta, int64_t n);
+int bem_mlp_get_weights(bem_ctx* ctx, float* theta, int64_t n);
+/* Network outputs y (B x 2) for host features x (B x 10), row-major. */
+int bem_mlp_forward(bem_ctx* ctx, const float* x, int64_t B, float* y);
+/* Gradient of the loss at host features x (B x 10) and targets t (B x 2)
+ * into grad (num_params floats) and the loss into *loss (may be NULL). */
+int bem_mlp_gradient(bem_ctx* ctx, const float* x, const float* t, int64_t B, float* grad, double* loss);
+/* One Adam step with learning rate lr on that loss (loss before the step). */
+int bem_mlp_train_step(bem_ctx* ctx, const float* x, const float* t, int64_t B, double lr, double* loss);
 
 /* ---- measurement ------------------------------------------------------- */
 

@@ -21,7 +21,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "NO_MESH", -3: "OOM", -4: "CUDA", -5: "NOT_CONV
 BC_TRACTION, BC_DISPLACEMENT = 0, 1
 WIN_NONE, WIN_HANNING, WIN_BLACKMAN = 0, 1, 2
 PREC_C64_MIXED, PREC_C128 = 0, 1
-GUESS_ZERO, GUESS_SEM = 0, 1
+GUESS_ZERO, GUESS_SEM, GUESS_MLP = 0, 1, 2
 
 EXPORTED = [
     "bem_default_opts", "bem_create", "bem_destroy", "bem_last_error", "bem_mesh", "bem_mesh_dev",
@@ -29,6 +29,8 @@ EXPORTED = [
     "bem_get_frequency_solution", "bem_time_response", "bem_time_response_dev", "bem_load_dft", "bem_idft",
     "bem_assemble", "bem_operator_rows", "bem_apply", "bem_rhs", "bem_solve_assembled", "bem_sem_guess",
     "bem_set_profiling", "bem_get_profile", "bem_apply_noalloc",
+    "bem_mlp_num_params", "bem_mlp_init", "bem_mlp_set_training", "bem_mlp_set_weights", "bem_mlp_get_weights",
+    "bem_mlp_forward", "bem_mlp_gradient", "bem_mlp_train_step",
 ]
 
 
@@ -51,7 +53,7 @@ class FreqStats(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("guess_residual", ctypes.c_double),
                 ("assemble_ms", ctypes.c_double), ("guess_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("near_bytes", ctypes.c_int64), ("far_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int32),
-                ("aca_failures", ctypes.c_int32)]
+                ("aca_failures", ctypes.c_int32), ("sem_residual", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -103,6 +105,14 @@ def load_library(path: str = LIB_PATH):
         "bem_set_profiling": (ctypes.c_int, [P, ctypes.c_int]),
         "bem_apply_noalloc": (ctypes.c_int, [P, P, P]),
         "bem_get_profile": (ctypes.c_int, [P, ctypes.POINTER(Profile)]),
+        "bem_mlp_num_params": (I64, []),
+        "bem_mlp_init": (ctypes.c_int, [P, ctypes.c_uint64]),
+        "bem_mlp_set_training": (ctypes.c_int, [P, I32, D]),
+        "bem_mlp_set_weights": (ctypes.c_int, [P, P, I64]),
+        "bem_mlp_get_weights": (ctypes.c_int, [P, P, I64]),
+        "bem_mlp_forward": (ctypes.c_int, [P, P, I64, P]),
+        "bem_mlp_gradient": (ctypes.c_int, [P, P, P, I64, P, P]),
+        "bem_mlp_train_step": (ctypes.c_int, [P, P, P, I64, D, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -315,6 +325,46 @@ class Context:
             if str(t.dtype) != "torch.complex64" or t.numel() != 3 * self.ne:
                 raise ValueError("x and y must be complex64 tensors of 3 ne values")
         self._check(self.lib.bem_apply_noalloc(self.h, _tptr(x_t), _tptr(y_t)))
+
+    # --- learned initial guess ----------------------------------------------
+    def mlp_num_params(self) -> int:
+        return int(self.lib.bem_mlp_num_params())
+
+    def mlp_init(self, seed: int):
+        self._check(self.lib.bem_mlp_init(self.h, int(seed)))
+
+    def mlp_set_training(self, steps_per_frequency: int, lr: float):
+        self._check(self.lib.bem_mlp_set_training(self.h, int(steps_per_frequency), float(lr)))
+
+    def mlp_set_weights(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        self._check(self.lib.bem_mlp_set_weights(self.h, _ptr(th), th.size))
+
+    def mlp_get_weights(self):
+        th = np.zeros(self.mlp_num_params(), dtype=np.float32)
+        self._check(self.lib.bem_mlp_get_weights(self.h, _ptr(th), th.size))
+        return th
+
+    def mlp_forward(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros((x.shape[0], 2), dtype=np.float32)
+        self._check(self.lib.bem_mlp_forward(self.h, _ptr(x), x.shape[0], _ptr(y)))
+        return y
+
+    def mlp_gradient(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(self.mlp_num_params(), dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self.lib.bem_mlp_gradient(self.h, _ptr(x), _ptr(t), x.shape[0], _ptr(g), ctypes.byref(loss)))
+        return loss.value, g
+
+    def mlp_train_step(self, x, t, lr):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self.lib.bem_mlp_train_step(self.h, _ptr(x), _ptr(t), x.shape[0], float(lr), ctypes.byref(loss)))
+        return loss.value
 
     # --- measurement -------------------------------------------------------
     def set_profiling(self, on: bool):

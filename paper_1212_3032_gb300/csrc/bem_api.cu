@@ -340,6 +340,7 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
     cudaEventDestroy(p.b);
   }
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  mlp_free(ctx);
   delete ctx;
 }
 
@@ -1054,33 +1055,41 @@ int gmres(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq_stat
 // ---------------------------------------------------------------------------
 // solution extrapolation (Sec. 4.2): a0 = X R^{-1} Q^H b, A X = Q R (CGS2, FP64)
 // X: K vectors (device, stride N), in the order a_{k-1}, a_{k-2}, ...
+// extra (optional): one more candidate column after them (the learned
+// proposal), so that the fit over the larger span can only lower the residual.
+// res (optional): res[0] = ||b - A a0|| / ||b|| over the X columns alone,
+// res[1] = over every column, both from ||b||^2 - sum_i |q_i^H b|^2.
 // ---------------------------------------------------------------------------
-int sem_impl(bem_ctx* ctx, const c128* const* X, int K, const c128* b, c128* a0) {
+int sem_impl(bem_ctx* ctx, const c128* const* X, int K, const c128* b, c128* a0, const c128* extra = nullptr,
+             double* res = nullptr) {
   cudaStream_t st = ctx->stream;
   const long long N = ctx->N;
   BEM_CUDA_TRY(cudaMemsetAsync(a0, 0, N * sizeof(c128), st));
-  if (K <= 0) return BEM_OK;
-  DevBuf<c128> Xc, Y, Q;
-  BEM_CUDA_TRY(Xc.alloc(K * N));
-  BEM_CUDA_TRY(Y.alloc(K * N));
-  BEM_CUDA_TRY(Q.alloc(K * N));
-  for (int q = 0; q < K; ++q)
-    BEM_CUDA_TRY(cudaMemcpyAsync(Xc.p + q * N, X[q], N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
-  TRY(apply_fast(ctx, Xc.p, Y.p, K));
+  if (res) res[0] = res[1] = 1.0;
+  const int C = K + (extra ? 1 : 0);
+  if (C <= 0) return BEM_OK;
+  auto column = [&](int c) { return c < K ? X[c] : extra; };
+  BEM_CUDA_TRY(ctx->sem_work.ensure(3LL * C * N));
+  c128* Xc = ctx->sem_work.p;
+  c128* Y = Xc + (long long)C * N;
+  c128* Q = Y + (long long)C * N;
+  for (int q = 0; q < C; ++q)
+    BEM_CUDA_TRY(cudaMemcpyAsync(Xc + q * N, column(q), N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
+  for (int q = 0; q < C; q += 4) TRY(apply_fast(ctx, Xc + q * N, Y + q * N, std::min(4, C - q)));
   BEM_CUDA_TRY(ctx->red.ensure(2LL * 64 * 8 * 2 + 64));
   c128* part = reinterpret_cast<c128*>(ctx->red.p);
   c128* hdev = part + 64 * 8;
-  std::vector<std::complex<double>> R(K * K, 0.0);
+  std::vector<std::complex<double>> R(C * C, 0.0);
   std::vector<int> keep;
   double r00 = 0;
-  for (int c = 0; c < K; ++c) {
-    c128* qc = Q.p + (long long)keep.size() * N;
-    BEM_CUDA_TRY(cudaMemcpyAsync(qc, Y.p + c * N, N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
+  for (int c = 0; c < C; ++c) {
+    c128* qc = Q + (long long)keep.size() * N;
+    BEM_CUDA_TRY(cudaMemcpyAsync(qc, Y + c * N, N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
     std::vector<std::complex<double>> col(keep.size(), 0.0);
     for (int pass = 0; pass < 2 && !keep.empty(); ++pass) {
-      int nb = launch_dots<c128, c128>(Q.p, N, (int)keep.size(), qc, N, part, st);
+      int nb = launch_dots<c128, c128>(Q, N, (int)keep.size(), qc, N, part, st);
       launch_dots_final(part, nb, (int)keep.size(), hdev, st);
-      launch_update<c128, c128>(Q.p, N, (int)keep.size(), hdev, qc, N, st);
+      launch_update<c128, c128>(Q, N, (int)keep.size(), hdev, qc, N, st);
       CK("sem qr");
       std::vector<c128> h(keep.size());
       BEM_CUDA_TRY(cudaMemcpyAsync(h.data(), hdev, keep.size() * sizeof(c128), cudaMemcpyDeviceToHost, st));
@@ -1094,25 +1103,39 @@ int sem_impl(bem_ctx* ctx, const c128* const* X, int K, const c128* b, c128* a0)
     if (!(nrm > 1e-12 * r00) || nrm == 0.0) continue;  // numerically dependent column: drop
     launch_copy_cast(qc, qc, N, 1.0 / nrm, st);
     int kk = (int)keep.size();
-    for (int i = 0; i < kk; ++i) R[i * K + kk] = col[i];
-    R[kk * K + kk] = nrm;
+    for (int i = 0; i < kk; ++i) R[i * C + kk] = col[i];
+    R[kk * C + kk] = nrm;
     keep.push_back(c);
   }
   int kk = (int)keep.size();
   if (kk == 0) return BEM_OK;
-  int nb = launch_dots<c128, c128>(Q.p, N, kk, b, N, part, st);
+  int nb = launch_dots<c128, c128>(Q, N, kk, b, N, part, st);
   launch_dots_final(part, nb, kk, hdev, st);
   CK("sem qhb");
   std::vector<c128> qb(kk);
   BEM_CUDA_TRY(cudaMemcpyAsync(qb.data(), hdev, kk * sizeof(c128), cudaMemcpyDeviceToHost, st));
   BEM_CUDA_TRY(cudaStreamSynchronize(st));
-  std::vector<std::complex<double>> s(kk);
+  if (res) {
+    std::complex<double> bb;
+    TRY(dot_host(ctx, b, b, N, bb));
+    double rem_x = bb.real(), rem_all = bb.real();
+    for (int i = 0; i < kk; ++i) {
+      double q2 = qb[i].re * qb[i].re + qb[i].im * qb[i].im;
+      rem_all -= q2;
+      if (keep[i] < K) rem_x -= q2;
+    }
+    if (bb.real() > 0) {
+      res[0] = std::sqrt(std::max(0.0, rem_x) / bb.real());
+      res[1] = std::sqrt(std::max(0.0, rem_all) / bb.real());
+    }
+  }
+  std::vector<std::complex<double>> sv(kk);
   for (int i = kk - 1; i >= 0; --i) {
     std::complex<double> v(qb[i].re, qb[i].im);
-    for (int j = i + 1; j < kk; ++j) v -= R[i * K + j] * s[j];
-    s[i] = v / R[i * K + i];
+    for (int j = i + 1; j < kk; ++j) v -= R[i * C + j] * sv[j];
+    sv[i] = v / R[i * C + i];
   }
-  for (int i = 0; i < kk; ++i) launch_axpy(c128{s[i].real(), s[i].imag()}, X[keep[i]], a0, N, st);
+  for (int i = 0; i < kk; ++i) launch_axpy(c128{sv[i].real(), sv[i].imag()}, column(keep[i]), a0, N, st);
   CK("sem combine");
   return BEM_OK;
 }
@@ -1373,6 +1396,7 @@ static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_de
   BEM_CUDA_TRY(ctx->b64.ensure(N));
   BEM_CUDA_TRY(cudaStreamSynchronize(st));
   const double dw = 2.0 * M_PI / T;
+  const double dt = T / n_omega;
   int worst = BEM_OK;
   Timer t0, t1, t2;
   for (int k = 0; k < nf; ++k) {
@@ -1385,20 +1409,26 @@ static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_de
     TRY(assemble_impl(ctx, s.s_re, s.s_im, o, ctx->pattern.p, ctx->Pk_host[k], ctx->b64.p));
     cudaEventRecord(t0.b, st);
     cudaEventRecord(t1.a, st);
-    int K = (o.guess == BEM_GUESS_SEM) ? std::min(k, std::max(0, std::min(o.sem_k, 4))) : 0;
-    if (K > 0) {
-      std::vector<const c128*> X;
-      for (int q = 1; q <= K; ++q) X.push_back(ctx->sol.p + (long long)(k - q) * N);
-      TRY(sem_impl(ctx, X.data(), K, ctx->b64.p, xk));
+    int K = (o.guess != BEM_GUESS_ZERO) ? std::min(k, std::max(0, std::min(o.sem_k, 4))) : 0;
+    const c128* prev[4] = {};
+    for (int q = 1; q <= 4 && q <= k; ++q) prev[q - 1] = ctx->sol.p + (long long)(k - q) * N;
+    const c128* extra = nullptr;
+    if (o.guess == BEM_GUESS_MLP && k >= 4) TRY(mlp_propose(ctx, prev, s.s_re * dt, s.s_im * dt, &extra));
+    double res[2] = {1.0, 1.0};
+    if (K > 0 || extra) {
+      TRY(sem_impl(ctx, prev, K, ctx->b64.p, xk, extra, res));
     } else {
       BEM_CUDA_TRY(cudaMemsetAsync(xk, 0, N * sizeof(c128), st));
     }
+    s.sem_residual = res[0];
     cudaEventRecord(t1.b, st);
     cudaEventRecord(t2.a, st);
     int rc = gmres(ctx, ctx->b64.p, xk, o, &s);
     cudaEventRecord(t2.b, st);
     if (rc != BEM_OK && rc != BEM_ERR_NOT_CONVERGED) return rc;
     if (rc == BEM_ERR_NOT_CONVERGED) worst = rc;
+    if (o.guess == BEM_GUESS_MLP && k >= 4)
+      TRY(mlp_train(ctx, prev, xk, s.s_re * dt, s.s_im * dt, ctx->mlp_steps, ctx->mlp_lr));
     int fails = 0;
     BEM_CUDA_TRY(cudaMemcpyAsync(&fails, ctx->aca_fail.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     BEM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1438,6 +1468,8 @@ static int sweep_checks(bem_ctx* ctx, double T, int32_t n_omega, const bem_opts&
     return fail(ctx, BEM_ERR_INVALID_ARG, "bad solver options");
   if (o.precision != BEM_PREC_C64_MIXED && o.precision != BEM_PREC_C128)
     return fail(ctx, BEM_ERR_INVALID_ARG, "unknown precision");
+  if (o.guess != BEM_GUESS_ZERO && o.guess != BEM_GUESS_SEM && o.guess != BEM_GUESS_MLP)
+    return fail(ctx, BEM_ERR_INVALID_ARG, "unknown initial guess");
   return BEM_OK;
 }
 

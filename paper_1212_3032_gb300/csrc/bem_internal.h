@@ -107,6 +107,8 @@ template <typename T> struct DevBuf {
 bool count_if(bool c);
 long long launch_count();
 
+struct MlpState;  // learned initial guess (bem_mlp.cu)
+
 // Host-side rule tables (Gauss-Legendre on [0,1], series coefficients).
 void make_rule_tables(RuleTables& t);
 
@@ -212,6 +214,12 @@ struct bem_ctx {
   long long launches_at_reset = 0;  // sum_b rank_b (3 nr_b + 3 nc_b) after the last ACA
   double prof_hmv_ms = 0, prof_hmv_bytes = 0, prof_asm_ms = 0;
 
+  // learned initial guess
+  bem::MlpState* mlp = nullptr;
+  int mlp_steps = 4;       // Adam steps after each solved frequency
+  double mlp_lr = 1e-3;
+  bem::DevBuf<bem::c128> sem_work;     // extrapolation workspace (3 x columns x N)
+
   // sweep results
   int n_omega = 0;
   double T = 0;
@@ -223,5 +231,11 @@ struct bem_ctx {
 
 namespace bem {
 int fail(bem_ctx* ctx, int code, const std::string& msg);
+// learned initial guess (bem_mlp.cu)
+void mlp_free(bem_ctx* ctx);
+int mlp_ready(bem_ctx* ctx);
+int mlp_propose(bem_ctx* ctx, const c128* const* prev, double sre_dt, double sim_dt, const c128** out);
+int mlp_train(bem_ctx* ctx, const c128* const* prev, const c128* ak, double sre_dt, double sim_dt, int steps,
+              double lr);
 int fail_cuda(bem_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
 }
