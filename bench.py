@@ -188,10 +188,14 @@ GUESS_LABEL = {
 
 
 def profile_case(ctx, binding, mesh, cfg, opts):
-    """One frequency of the workload (k = n_omega / 4): mesh, assembly, right-hand
-    side and one GMRES solve, for profiler captures of single launches."""
-    s = cfg["eta"] + 1j * (cfg["n_omega"] // 4) * 2 * math.pi / cfg["T"]
+    """Two neighbouring frequencies of the workload (k = n_omega / 4 - 1, then
+    k = n_omega / 4, whose assembly reuses the first one's ACA pivots), then
+    the right-hand side and one GMRES solve at the second, for profiler
+    captures of single launches."""
+    k = cfg["n_omega"] // 4
     ctx.mesh(mesh.xyz, mesh.tri, mesh.bc_type, opts)
+    ctx.assemble(cfg["eta"] + 1j * (k - 1) * 2 * math.pi / cfg["T"], opts)
+    s = cfg["eta"] + 1j * k * 2 * math.pi / cfg["T"]
     ctx.assemble(s, opts)
     b = ctx.rhs(1.0, mesh.pattern)
     _, st = ctx.solve_assembled(b, opts=opts)
@@ -215,6 +219,7 @@ def run_ours(args, cfg):
     ctx = binding.Context(local, stream=stream.cuda_stream)
     ctx.set_material(**MAT)
     ctx.set_window(cfg["eta"], binding.WIN_HANNING)
+    ctx.set_aca_reuse(not args.no_aca_reuse)
     mesh = inputs.cavity_problem(cfg["n"])
     N = 3 * mesh.ne
     n_omega = cfg["n_omega"]
@@ -330,6 +335,8 @@ def run_ours(args, cfg):
                      "peak_source": peak_kind, "traffic": None,
                      "launches": prof["hmv_launches"], "ms_total": prof["hmv_ms"]},
         "phases_ms_per_step": {"hmatvec": prof["hmv_ms"] / args.steps, "assembly": prof["assemble_ms"] / args.steps},
+        "aca": {"pivot_reuse": not args.no_aca_reuse, "blocks": prof["aca_blocks"],
+                "stepped": prof["aca_stepped"]},
         "gpu_launches": prof["kernel_launches"],
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -350,6 +357,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--guess", default="sem", choices=["sem", "mlp", "zero"])
+    ap.add_argument("--no-aca-reuse", action="store_true",
+                    help="assemble every frequency with a fresh ACA (no reuse of the previous pivots)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one frequency (assembly + one solve) and exit; for profiler captures")
     args = ap.parse_args()

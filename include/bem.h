@@ -222,6 +222,24 @@ int bem_sem_guess(bem_ctx* ctx, int32_t K, const double* X, const double* b, dou
  * Errors: STATE (not assembled, or complex128 operator), INVALID_ARG. */
 int bem_apply_noalloc(bem_ctx* ctx, const float* x_dev, float* y_dev);
 
+/* Cross-frequency reuse of the ACA pivots (default on). The paper assembles
+ * every frequency from scratch; with reuse, each assembly after the first on
+ * a mesh starts every admissible block from the pivot rows and columns ACA
+ * chose at the previous assembly: it evaluates them at the new s, forms the
+ * cross approximation through them (an LU of the r x r pivot block without
+ * pivoting), keeps the leading pivots that are still within a factor 10 of
+ * their residual row's largest entry, applies ACA's stopping test
+ * |u_l| |v_l| <= aca_tol ||S_l||_F to the reused steps, and continues with
+ * ACA steps where it is not met. */
+int bem_set_aca_reuse(bem_ctx* ctx, int on);
+/* Admissible blocks of the current mesh after the last assembly: *count =
+ * number of blocks; for the first min(nmax, count) blocks info[4b..4b+3] =
+ * rows (elements), columns (elements), rank, and the rank the reused pivots
+ * settled on their own (equal to the rank when no ACA step was needed; -1
+ * when the last assembly did not reuse pivots). nmax = 0 queries the count.
+ * Errors: STATE (not assembled). */
+int bem_far_block_info(bem_ctx* ctx, int64_t nmax, int32_t* info, int64_t* count);
+
 /* ---- learned initial guess (BEM_GUESS_MLP) ---------------------------------
  * The paper's extrapolation (Sec. 4.2) fits a_k^(0) in the span of the last
  * K solutions. The learned guess adds one candidate column p_k to that span,
@@ -266,6 +284,8 @@ typedef struct bem_profile {
   int64_t assemble_calls;   /* operator assemblies */
   double assemble_ms;       /* summed CUDA-event time of assembly (RHS, singular, near, ACA) */
   int64_t kernel_launches;  /* kernels launched by the library since profiling was (re)enabled */
+  int64_t aca_blocks;       /* admissible blocks assembled */
+  int64_t aca_stepped;      /* of which took ACA steps (were not settled by pivot reuse alone) */
 } bem_profile;
 
 /* Enable (1) or disable (0) event timing of the H-matrix products and of

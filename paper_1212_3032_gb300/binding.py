@@ -30,7 +30,8 @@ EXPORTED = [
     "bem_assemble", "bem_operator_rows", "bem_apply", "bem_rhs", "bem_solve_assembled", "bem_sem_guess",
     "bem_set_profiling", "bem_get_profile", "bem_apply_noalloc",
     "bem_mlp_num_params", "bem_mlp_init", "bem_mlp_set_training", "bem_mlp_set_weights", "bem_mlp_get_weights",
-    "bem_mlp_forward", "bem_mlp_gradient", "bem_mlp_train_step",
+    "bem_mlp_forward", "bem_mlp_gradient", "bem_mlp_train_step", "bem_set_aca_reuse",
+    "bem_far_block_info",
 ]
 
 
@@ -62,7 +63,8 @@ class FreqStats(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("hmv_launches", ctypes.c_int64), ("hmv_ms", ctypes.c_double), ("hmv_bytes", ctypes.c_double),
                 ("assemble_calls", ctypes.c_int64), ("assemble_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("aca_blocks", ctypes.c_int64),
+                ("aca_stepped", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -105,6 +107,8 @@ def load_library(path: str = LIB_PATH):
         "bem_set_profiling": (ctypes.c_int, [P, ctypes.c_int]),
         "bem_apply_noalloc": (ctypes.c_int, [P, P, P]),
         "bem_get_profile": (ctypes.c_int, [P, ctypes.POINTER(Profile)]),
+        "bem_set_aca_reuse": (ctypes.c_int, [P, ctypes.c_int]),
+        "bem_far_block_info": (ctypes.c_int, [P, I64, P, P]),
         "bem_mlp_num_params": (I64, []),
         "bem_mlp_init": (ctypes.c_int, [P, ctypes.c_uint64]),
         "bem_mlp_set_training": (ctypes.c_int, [P, I32, D]),
@@ -369,6 +373,18 @@ class Context:
     # --- measurement -------------------------------------------------------
     def set_profiling(self, on: bool):
         self._check(self.lib.bem_set_profiling(self.h, 1 if on else 0))
+
+    def set_aca_reuse(self, on: bool):
+        self._check(self.lib.bem_set_aca_reuse(self.h, 1 if on else 0))
+
+    def far_block_info(self):
+        """(nblocks, 4) int32: rows, cols (elements), rank, rank settled by reused pivots (-1: no reuse)."""
+        n = ctypes.c_int64()
+        self._check(self.lib.bem_far_block_info(self.h, 0, None, ctypes.byref(n)))
+        info = np.zeros((n.value, 4), dtype=np.int32)
+        if n.value:
+            self._check(self.lib.bem_far_block_info(self.h, n.value, _ptr(info), ctypes.byref(n)))
+        return info
 
     def get_profile(self):
         p = Profile()

@@ -386,6 +386,7 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   if (!(o.eta_adm > 0)) return fail(ctx, BEM_ERR_INVALID_ARG, "eta_adm must be > 0");
   ctx->have_mesh = false;
   ctx->assembled = false;
+  ctx->aca_warm_ok = false;
   ctx->nf = 0;
   ctx->mesh_opts = o;
   ctx->ne = ne;
@@ -623,17 +624,29 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
     if (nnb) BEM_CUDA_TRY(cudaMemcpyAsync(ctx->poff.p, po.data(), nnb * sizeof(long long), cudaMemcpyHostToDevice, st));
     launch_pair_sort(ctx->near_d.p, nnb, ctx->ef.p, ctx->ed.p, ctx->poff.p, ctx->plist.p, ctx->pcount.p, st);
     CK("pair_sort");
-    // far right-hand-side items: (far block, first row), 8 rows each
-    std::vector<int> items;
-    for (size_t b = 0; b < ctx->far_h.size(); ++b)
-      for (int r = 0; r < ctx->far_h[b].nr; r += 8) {
-        items.push_back((int)b);
-        items.push_back(r);
-      }
-    ctx->nrhs_items = (int)(items.size() / 2);
-    BEM_CUDA_TRY(ctx->rhs_items.alloc(std::max<size_t>(2, items.size())));
-    if (!items.empty())
-      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->rhs_items.p, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    // far right-hand side: per leaf, the column ranges of its far panels;
+    // per element, its leaf
+    std::vector<int> rng, rptr(L + 1, 0), eleaf(ne, 0);
+    for (int l = 0; l < L; ++l) {
+      rptr[l] = (int)(rng.size() / 2);
+      for (int p = pptr[l]; p < pptr[l + 1]; ++p)
+        if (pan[p].kind == 1) {
+          const FarBlk& fb = ctx->far_h[pan[p].xoff];
+          rng.push_back(fb.c0);
+          rng.push_back(fb.nc);
+        }
+      for (int e = r0[l]; e < r0[l] + nr[l]; ++e) eleaf[e] = l;
+    }
+    rptr[L] = (int)(rng.size() / 2);
+    BEM_CUDA_TRY(ctx->rhs_rng.alloc(std::max<size_t>(2, rng.size())));
+    BEM_CUDA_TRY(ctx->rhs_rptr.alloc(L + 1));
+    BEM_CUDA_TRY(ctx->elem_leaf.alloc(std::max(1, ne)));
+    if (!rng.empty())
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->rhs_rng.p, rng.data(), rng.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->rhs_rptr.p, rptr.data(), (L + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->elem_leaf.p, eleaf.data(), ne * sizeof(int), cudaMemcpyHostToDevice, st));
+    // the host vectors above must outlive the copies
+    BEM_CUDA_TRY(cudaStreamSynchronize(st));
   }
 
   // singular and near-singular pairs of the near blocks
@@ -653,6 +666,20 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   BEM_CUDA_TRY(ctx->sing.alloc(std::max(1, ctx->nsing)));
   launch_sing_fill(ctx->near_d.p, nnb, ctx->ed.p, cnt.p, ctx->sing.p, st);
   CK("sing_fill");
+  if (ctx->nsing) {
+    // self pairs first (stable), so that the half-warps of one warp mostly
+    // run the same rule
+    std::vector<SingPair> sp(ctx->nsing), spo;
+    BEM_CUDA_TRY(cudaMemcpyAsync(sp.data(), ctx->sing.p, sp.size() * sizeof(SingPair), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA_TRY(cudaStreamSynchronize(st));
+    spo.reserve(sp.size());
+    for (const SingPair& q : sp)
+      if (q.self) spo.push_back(q);
+    for (const SingPair& q : sp)
+      if (!q.self) spo.push_back(q);
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->sing.p, spo.data(), spo.size() * sizeof(SingPair), cudaMemcpyHostToDevice, st));
+    BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
   ctx->sing_static.release();
   BEM_CUDA_TRY(cudaStreamSynchronize(st));
   ctx->have_mesh = true;
@@ -711,6 +738,46 @@ int check_ready(bem_ctx* ctx) {
   return BEM_OK;
 }
 
+// Far-field blocks at the current s: reuse of the previous assembly's pivots
+// where available, then ACA steps for every block not yet converged.
+template <typename R, typename Op>
+int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, const bem_opts& o) {
+  cudaStream_t st = ctx->stream;
+  const size_t nf = ctx->far_h.size();
+  BEM_CUDA_TRY(ctx->piv_i.ensure(std::max(1, ctx->t_entries)));
+  BEM_CUDA_TRY(ctx->piv_j.ensure(std::max(1, ctx->t_entries)));
+  BEM_CUDA_TRY(ctx->aca_kstart.ensure(std::max<size_t>(1, nf)));
+  BEM_CUDA_TRY(ctx->aca_done.ensure(std::max<size_t>(1, nf)));
+  BEM_CUDA_TRY(ctx->aca_norm0.ensure(std::max<size_t>(1, nf)));
+  AcaState S{nullptr, nullptr, nullptr, ctx->piv_i.p, ctx->piv_j.p};
+  const bool warm = ctx->aca_reuse && ctx->aca_warm_ok && nf > 0;
+  ctx->aca_last_warm = warm;
+  if (warm) {
+    BEM_CUDA_TRY((launch_aca_warm<R, Op>(ctx->far_d.p, (int)nf, ctx->ef.p, ctx->ed.p, ctx->bc.p, P, U, V,
+                                         ctx->rank.p, ctx->piv_i.p, ctx->piv_j.p, ctx->aca_kstart.p,
+                                         ctx->aca_norm0.p, ctx->aca_done.p, o.aca_tol, ctx->aca_tau, st)));
+    S.kstart = ctx->aca_kstart.p;
+    S.norm0 = ctx->aca_norm0.p;
+    S.done = ctx->aca_done.p;
+  }
+  launch_aca<R, Op>(ctx->far_d.p, ctx->far_small.p, ctx->nfar_small, ctx->far_large.p, ctx->nfar_large, ctx->ef.p,
+                    ctx->ed.p, ctx->bc.p, P, U, V, ctx->rank.p, ctx->aca_fail.p, o.aca_tol, S, st);
+  CK("aca");
+  if (ctx->profiling && nf) {
+    ctx->prof_aca_blocks += (long long)nf;
+    if (warm) {
+      std::vector<int> dn(nf);
+      BEM_CUDA_TRY(cudaMemcpyAsync(dn.data(), ctx->aca_done.p, nf * sizeof(int), cudaMemcpyDeviceToHost, st));
+      BEM_CUDA_TRY(cudaStreamSynchronize(st));
+      for (size_t b = 0; b < nf; ++b) ctx->prof_aca_continued += dn[b] ? 0 : 1;
+    } else {
+      ctx->prof_aca_continued += (long long)nf;
+    }
+  }
+  ctx->aca_warm_ok = true;
+  return BEM_OK;
+}
+
 // Operator at s: right-hand side contributions optional (pattern/b may be null).
 int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const double* pattern_tree,
                   c128 pk, c128* b) {
@@ -729,10 +796,10 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
   if (b) {
     BEM_CUDA_TRY(cudaMemsetAsync(b, 0, ctx->N * sizeof(c128), st));
     if (is_mixed(ctx))
-      launch_rhs_far<float>(ctx->rhs_items.p, ctx->nrhs_items, ctx->far_d.p, ctx->ef.p, ctx->ed.p, ctx->bc.p,
+      launch_rhs_far<float>(ctx->rhs_rng.p, ctx->rhs_rptr.p, ctx->elem_leaf.p, ctx->ne, ctx->ef.p, ctx->ed.p, ctx->bc.p,
                             ctx->patf.p, ctx->pattern.p, make_params<float>(ctx, sre, sim), pk, b, st);
     else
-      launch_rhs_far<double>(ctx->rhs_items.p, ctx->nrhs_items, ctx->far_d.p, ctx->ef.p, ctx->ed.p, ctx->bc.p,
+      launch_rhs_far<double>(ctx->rhs_rng.p, ctx->rhs_rptr.p, ctx->elem_leaf.p, ctx->ne, ctx->ef.p, ctx->ed.p, ctx->bc.p,
                              ctx->patf.p, ctx->pattern.p, Pd, pk, b, st);
     CK("rhs_far");
   }
@@ -756,10 +823,7 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
                                     ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, ctx->near32.p,
                                     b ? ctx->patf.p : nullptr, b ? ctx->pattern.p : nullptr, pk, b, st);
     CK("near_regular");
-    launch_aca<float, c64>(ctx->far_d.p, ctx->far_small.p, ctx->nfar_small, ctx->far_large.p, ctx->nfar_large,
-                           ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, ctx->u32.p, ctx->v32.p, ctx->rank.p, ctx->aca_fail.p,
-                           o.aca_tol, st);
-    CK("aca");
+    TRY((run_aca<float, c64>(ctx, Pf, ctx->u32.p, ctx->v32.p, o)));
     long long n9 = 9LL * ctx->ne;
     count_if(true);
     k_pinv_cast<<<(unsigned)((n9 + 255) / 256), 256, 0, st>>>(ctx->prec_inv.p, ctx->prec_inv32.p, n9);
@@ -781,10 +845,7 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
                                       ctx->poff.p, ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd, ctx->near64.p,
                                       b ? ctx->patf.p : nullptr, b ? ctx->pattern.p : nullptr, pk, b, st);
     CK("near_regular");
-    launch_aca<double, c128>(ctx->far_d.p, ctx->far_small.p, ctx->nfar_small, ctx->far_large.p, ctx->nfar_large,
-                             ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd, ctx->u64.p, ctx->v64.p, ctx->rank.p,
-                             ctx->aca_fail.p, o.aca_tol, st);
-    CK("aca");
+    TRY((run_aca<double, c128>(ctx, Pd, ctx->u64.p, ctx->v64.p, o)));
   }
   prof_end(ctx, ev, 1, 0.0);
   ctx->assembled = true;
@@ -1250,7 +1311,7 @@ extern "C" int bem_rhs(bem_ctx* ctx, double p_re, double p_im, const double* pat
   BEM_CUDA_TRY(cudaMemsetAsync(bd.p, 0, ctx->N * sizeof(c128), ctx->stream));
   if (is_mixed(ctx)) {
     KParams<float> Pf = make_params<float>(ctx, ctx->s_re, ctx->s_im);
-    launch_rhs_far<float>(ctx->rhs_items.p, ctx->nrhs_items, ctx->far_d.p, ctx->ef.p, ctx->ed.p, ctx->bc.p,
+    launch_rhs_far<float>(ctx->rhs_rng.p, ctx->rhs_rptr.p, ctx->elem_leaf.p, ctx->ne, ctx->ef.p, ctx->ed.p, ctx->bc.p,
                           ctx->patf.p, ctx->pattern.p, Pf, pk, bd.p, ctx->stream);
     launch_near_regular<float, c64>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->max_nr, ctx->plist.p, ctx->poff.p,
                                     ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, (c64*)nullptr, ctx->patf.p,
@@ -1258,7 +1319,7 @@ extern "C" int bem_rhs(bem_ctx* ctx, double p_re, double p_im, const double* pat
     launch_sing<float, c64>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pf,
                             nullptr, nullptr, ctx->pattern.p, pk, bd.p, ctx->status.p, ctx->stream);
   } else {
-    launch_rhs_far<double>(ctx->rhs_items.p, ctx->nrhs_items, ctx->far_d.p, ctx->ef.p, ctx->ed.p, ctx->bc.p,
+    launch_rhs_far<double>(ctx->rhs_rng.p, ctx->rhs_rptr.p, ctx->elem_leaf.p, ctx->ne, ctx->ef.p, ctx->ed.p, ctx->bc.p,
                            ctx->patf.p, ctx->pattern.p, Pd, pk, bd.p, ctx->stream);
     launch_near_regular<double, c128>(ctx->near_d.p, (int)ctx->near_h.size(), ctx->max_nr, ctx->plist.p,
                                       ctx->poff.p, ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd,
@@ -1585,7 +1646,39 @@ extern "C" int bem_set_profiling(bem_ctx* ctx, int on) {
   ctx->profiling = on != 0;
   ctx->prof_hmv_launches = ctx->prof_asm_calls = 0;
   ctx->prof_hmv_ms = ctx->prof_hmv_bytes = ctx->prof_asm_ms = 0;
+  ctx->prof_aca_blocks = ctx->prof_aca_continued = 0;
   ctx->launches_at_reset = launch_count();
+  return BEM_OK;
+}
+
+extern "C" int bem_far_block_info(bem_ctx* ctx, int64_t nmax, int32_t* info, int64_t* count) {
+  if (!ctx || !count || nmax < 0 || (nmax > 0 && !info)) return BEM_ERR_INVALID_ARG;
+  const int64_t nf = (int64_t)ctx->far_h.size();
+  *count = nf;
+  if (nmax == 0 || nf == 0) return BEM_OK;
+  if (!ctx->assembled) return fail(ctx, BEM_ERR_STATE, "operator not assembled");
+  TRY(set_device(ctx));
+  std::vector<int> rk(nf), ks(nf, -1), dn(nf, 0);
+  cudaStream_t st = ctx->stream;
+  BEM_CUDA_TRY(cudaMemcpyAsync(rk.data(), ctx->rank.p, nf * sizeof(int), cudaMemcpyDeviceToHost, st));
+  const bool warm = ctx->aca_kstart.n >= (size_t)nf && ctx->aca_last_warm;
+  if (warm) {
+    BEM_CUDA_TRY(cudaMemcpyAsync(ks.data(), ctx->aca_kstart.p, nf * sizeof(int), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA_TRY(cudaMemcpyAsync(dn.data(), ctx->aca_done.p, nf * sizeof(int), cudaMemcpyDeviceToHost, st));
+  }
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int64_t b = 0; b < std::min(nmax, nf); ++b) {
+    info[4 * b + 0] = ctx->far_h[b].nr;
+    info[4 * b + 1] = ctx->far_h[b].nc;
+    info[4 * b + 2] = rk[b];
+    info[4 * b + 3] = warm ? (dn[b] ? rk[b] : ks[b]) : -1;
+  }
+  return BEM_OK;
+}
+
+extern "C" int bem_set_aca_reuse(bem_ctx* ctx, int on) {
+  if (!ctx) return BEM_ERR_INVALID_ARG;
+  ctx->aca_reuse = on != 0;
   return BEM_OK;
 }
 
@@ -1600,5 +1693,7 @@ extern "C" int bem_get_profile(bem_ctx* ctx, bem_profile* out) {
   out->assemble_calls = ctx->prof_asm_calls;
   out->assemble_ms = ctx->prof_asm_ms;
   out->kernel_launches = launch_count() - ctx->launches_at_reset;
+  out->aca_blocks = ctx->prof_aca_blocks;
+  out->aca_stepped = ctx->prof_aca_continued;
   return BEM_OK;
 }

@@ -622,9 +622,6 @@ __global__ void __launch_bounds__(256) k_near_regular(const NearBlk* __restrict_
 // far-field share of the right-hand side, on the fly: one warp per row of an
 // admissible block (items of 8 rows); traction-loaded columns need U only
 // ---------------------------------------------------------------------------
-struct RhsItem {
-  int blk, il0;
-};
 
 // ---------------------------------------------------------------------------
 // polar parameters of the self rule: per element, per triangle (c, p_k, p_k+1):
@@ -680,93 +677,138 @@ template <typename R> __device__ __forceinline__ R wred(R v) {
   return v;
 }
 
+// One half-warp (16 lanes) per singular or near-singular pair: the 16 points
+// of the near-singular remainder rule one per lane, the 144 of the self rule
+// nine per lane. The 15 complex accumulators (U: 6, T: 9) are reduced with a
+// butterfly reduce-scatter (lane l ends with accumulator l), the FP64
+// epilogue (static parts, free term, storage, right-hand side) is spread over
+// the lanes. Self pairs come first in the list so that half-warps of one warp
+// mostly follow the same branch.
+template <typename R>
+__device__ __forceinline__ cplx<R> shfl_xor_c(cplx<R> v, int o) {
+  return mk<R>(__shfl_xor_sync(0xffffffffu, v.re, o), __shfl_xor_sync(0xffffffffu, v.im, o));
+}
+
 template <typename R, typename Op>
-__global__ void k_sing(const SingPair* __restrict__ pairs, int npairs, const ElemD* __restrict__ ed,
-                       const double* __restrict__ polar, const signed char* __restrict__ bc,
-                       const double* __restrict__ stat, KParams<R> P, Op* __restrict__ near,
-                       c128* __restrict__ pinv, const double* __restrict__ pattern, c128 pk, c128* __restrict__ b,
-                       int* __restrict__ status) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= npairs) return;
-  SingPair sp = pairs[warp];
-  const ElemD& E = ed[sp.e];
-  const ElemD& I = ed[sp.i];
-  R n[3] = {R(E.n[0]), R(E.n[1]), R(E.n[2])};
+__global__ void __launch_bounds__(256) k_sing(const SingPair* __restrict__ pairs, int npairs,
+                                              const ElemD* __restrict__ ed, const double* __restrict__ polar,
+                                              const signed char* __restrict__ bc, const double* __restrict__ stat,
+                                              KParams<R> P, Op* __restrict__ near, c128* __restrict__ pinv,
+                                              const double* __restrict__ pattern, c128 pk, c128* __restrict__ b,
+                                              int* __restrict__ status) {
+  __shared__ c128 sh[16][16];
+  const int pid = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int hl = threadIdx.x & 15, slot = threadIdx.x >> 4;
+  const bool active = pid < npairs;
+  SingPair sp{0, 0, 0, 0, 0};
   UTAcc<R> acc;
   acc.zero();
-  if (sp.self) {
-    for (int q = lane; q < 3 * SELF_NT * SELF_NR; q += 32) {
-      int sub = q / (SELF_NT * SELF_NR);
-      int m = (q / SELF_NR) % SELF_NT, l = q % SELF_NR;
-      const double* ps = polar + 27LL * sp.e + 9 * sub;
-      R d = R(ps[0]), tha = R(ps[7]), dth = R(ps[8]);
-      R th = tha + dth * gl_x<R>(SELF_NT, m);
-      R wth = dth * gl_w<R>(SELF_NT, m);
-      R sn, cs;
-      sincos_r(th, &sn, &cs);
-      R Rr = d / cs;
-      R r = Rr * gl_x<R>(SELF_NR, l);
-      R w = wth * Rr * gl_w<R>(SELF_NR, l) * r;
+  if (active) {
+    sp = pairs[pid];
+    const ElemD& E = ed[sp.e];
+    const ElemD& I = ed[sp.i];
+    R n[3] = {R(E.n[0]), R(E.n[1]), R(E.n[2])};
+    if (sp.self) {
+      for (int q = hl; q < 3 * SELF_NT * SELF_NR; q += 16) {
+        int sub = q / (SELF_NT * SELF_NR);
+        int m = (q / SELF_NR) % SELF_NT, l = q % SELF_NR;
+        const double* ps = polar + 27LL * sp.e + 9 * sub;
+        R d = R(ps[0]), tha = R(ps[7]), dth = R(ps[8]);
+        R th = tha + dth * gl_x<R>(SELF_NT, m);
+        R wth = dth * gl_w<R>(SELF_NT, m);
+        R sn, cs;
+        sincos_r(th, &sn, &cs);
+        R Rr = d / cs;
+        R r = Rr * gl_x<R>(SELF_NR, l);
+        R w = wth * Rr * gl_w<R>(SELF_NR, l) * r;
+        R rv[3];
+        for (int a = 0; a < 3; ++a) rv[a] = r * (cs * R(ps[1 + a]) + sn * R(ps[4 + a]));
+        accumulate_point<R, false>(acc, rv[0], rv[1], rv[2], n[0], n[1], n[2], w, P);
+      }
+    } else {
+      int ia = hl / NEAR_Q_REM, ib = hl % NEAR_Q_REM;
+      R u = gl_x<R>(NEAR_Q_REM, ia), v = (R(1) - u) * gl_x<R>(NEAR_Q_REM, ib);
+      R w = R(E.area2) * gl_w<R>(NEAR_Q_REM, ia) * gl_w<R>(NEAR_Q_REM, ib) * (R(1) - u);
       R rv[3];
-      for (int a = 0; a < 3; ++a) rv[a] = r * (cs * R(ps[1 + a]) + sn * R(ps[4 + a]));
+      for (int k = 0; k < 3; ++k)
+        rv[k] = R(E.p0[k] - I.c[k]) + u * R(E.p1[k] - E.p0[k]) + v * R(E.p2[k] - E.p0[k]);
       accumulate_point<R, false>(acc, rv[0], rv[1], rv[2], n[0], n[1], n[2], w, P);
     }
-  } else if (lane < NEAR_Q_REM * NEAR_Q_REM) {
-    int ia = lane / NEAR_Q_REM, ib = lane % NEAR_Q_REM;
-    R u = gl_x<R>(NEAR_Q_REM, ia), v = (R(1) - u) * gl_x<R>(NEAR_Q_REM, ib);
-    R w = R(E.area2) * gl_w<R>(NEAR_Q_REM, ia) * gl_w<R>(NEAR_Q_REM, ib) * (R(1) - u);
-    R rv[3];
-    for (int k = 0; k < 3; ++k)
-      rv[k] = R(E.p0[k] - I.c[k]) + u * R(E.p1[k] - E.p0[k]) + v * R(E.p2[k] - E.p0[k]);
-    accumulate_point<R, false>(acc, rv[0], rv[1], rv[2], n[0], n[1], n[2], w, P);
   }
+  // butterfly reduce-scatter over the half-warp: value index = lane
+  cplx<R> v16[16];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    acc.u[k].re = wred(acc.u[k].re);
-    acc.u[k].im = wred(acc.u[k].im);
-  }
+  for (int k = 0; k < 6; ++k) v16[k] = acc.u[k];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    acc.t[k].re = wred(acc.t[k].re);
-    acc.t[k].im = wred(acc.t[k].im);
-  }
-  if (lane != 0) return;
-  const double* st = stat + 18 * (long long)warp;
-  c128 U[9], T[9];
-  for (int a = 0; a < 3; ++a)
-    for (int c = 0; c < 3; ++c) {
-      cplx<R> uu = acc.U(a, c), tt = acc.t[3 * a + c];
-      U[3 * a + c] = c128{(double)uu.re + st[3 * a + c], (double)uu.im};
-      T[3 * a + c] = c128{(double)tt.re + st[9 + 3 * a + c], (double)tt.im};
+  for (int k = 0; k < 9; ++k) v16[6 + k] = acc.t[k];
+  v16[15] = mk<R>(0, 0);
+  cplx<R> w8[8], w4[4], w2[2];
+  {
+    const bool hi = hl & 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      cplx<R> keep = hi ? v16[8 + k] : v16[k], give = hi ? v16[k] : v16[8 + k];
+      w8[k] = keep + shfl_xor_c(give, 8);
     }
-  if (sp.self)
-    for (int a = 0; a < 3; ++a) T[4 * a].re += 0.5;  // free term c_ij = delta_ij / 2
-  bool trac = bc[sp.e] == BEM_BC_TRACTION;
-  c128 Ablk[9];
-  for (int k = 0; k < 9; ++k) Ablk[k] = trac ? T[k] : -U[k];
-  if (near) {
-    for (int a = 0; a < 3; ++a)
-      for (int c = 0; c < 3; ++c) near[sp.entry + (long long)c * sp.ld + a] = to_op<Op>(Ablk[3 * a + c]);
   }
-  if (sp.self && pinv) {
-    c128 Ai[9];
+  {
+    const bool hi = hl & 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      cplx<R> keep = hi ? w8[4 + k] : w8[k], give = hi ? w8[k] : w8[4 + k];
+      w4[k] = keep + shfl_xor_c(give, 4);
+    }
+  }
+  {
+    const bool hi = hl & 2;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      cplx<R> keep = hi ? w4[2 + k] : w4[k], give = hi ? w4[k] : w4[2 + k];
+      w2[k] = keep + shfl_xor_c(give, 2);
+    }
+  }
+  cplx<R> mine;
+  {
+    const bool hi = hl & 1;
+    cplx<R> keep = hi ? w2[1] : w2[0], give = hi ? w2[0] : w2[1];
+    mine = keep + shfl_xor_c(give, 1);
+  }
+  // FP64: add the static (Kelvin) part of accumulator hl and stage it
+  const double* st = stat + 18LL * (active ? pid : 0);
+  if (active && hl < 15) {
+    const int uac[6] = {0, 1, 2, 4, 5, 8};  // (a, c) of the symmetric U entries: 3a + c
+    double sre = hl < 6 ? st[uac[hl < 6 ? hl : 0]] : st[9 + (hl - 6)];
+    c128 val = c128{(double)mine.re + sre, (double)mine.im};
+    if (sp.self && hl >= 6 && ((hl - 6) % 4) == 0) val.re += 0.5;  // free term c_ij = delta_ij / 2
+    sh[slot][hl] = val;
+  }
+  __syncwarp();
+  if (!active) return;
+  const bool trac = bc[sp.e] == BEM_BC_TRACTION;
+  const int uidx[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};  // (a, c) -> symmetric U accumulator
+  if (near && hl < 9) {
+    const int a = hl / 3, c = hl % 3;
+    c128 A = trac ? sh[slot][6 + hl] : -sh[slot][uidx[hl]];
+    near[sp.entry + (long long)c * sp.ld + a] = to_op<Op>(A);
+  }
+  if (sp.self && pinv && hl == 0) {
+    c128 Ablk[9], Ai[9];
+    for (int k = 0; k < 9; ++k) Ablk[k] = trac ? sh[slot][6 + k] : -sh[slot][uidx[k]];
     if (!inv3(Ablk, Ai)) atomicExch(status, 3);
     for (int k = 0; k < 9; ++k) pinv[9 * (long long)sp.i + k] = Ai[k];
   }
-  if (b) {
+  if (b && hl < 3) {
     const double* pt = pattern + 3 * (long long)sp.e;
     if (pt[0] != 0.0 || pt[1] != 0.0 || pt[2] != 0.0) {
-      for (int a = 0; a < 3; ++a) {
-        c128 s = mk<double>(0, 0);
-        for (int c = 0; c < 3; ++c) {
-          c128 Bv = trac ? U[3 * a + c] : -T[3 * a + c];
-          cfmr(s, Bv, pt[c]);
-        }
-        s = s * pk;
-        atomicAdd(&b[3 * (long long)sp.i + a].re, s.re);
-        atomicAdd(&b[3 * (long long)sp.i + a].im, s.im);
+      const int a = hl;
+      c128 sacc = mk<double>(0, 0);
+      for (int c = 0; c < 3; ++c) {
+        c128 Bv = trac ? sh[slot][uidx[3 * a + c]] : -sh[slot][6 + 3 * a + c];
+        cfmr(sacc, Bv, pt[c]);
       }
+      sacc = sacc * pk;
+      atomicAdd(&b[3 * (long long)sp.i + a].re, sacc.re);
+      atomicAdd(&b[3 * (long long)sp.i + a].im, sacc.im);
     }
   }
 }
@@ -802,21 +844,38 @@ __device__ __forceinline__ void regular_pair_u(cplx<R>* u, const PairGeo<R>& g, 
   }
 }
 
+// One warp per row element i: every far column element of i's leaf (the
+// column ranges of the admissible blocks whose row cluster holds the leaf),
+// lanes striding over the concatenated ranges; one reduction and one
+// (non-atomic) update of b per row. b must not be written concurrently: the
+// kernel runs first after b is zeroed.
 template <typename R>
-__global__ void __launch_bounds__(256) k_rhs_far(const RhsItem* __restrict__ items, const FarBlk* __restrict__ far,
+__global__ void __launch_bounds__(256) k_rhs_far(const int* __restrict__ rng, const int* __restrict__ rptr,
+                                                 const int* __restrict__ elem_leaf, int ne,
                                                  const ElemF* __restrict__ ef, const ElemD* __restrict__ ed,
                                                  const signed char* __restrict__ bc, const float* __restrict__ patf,
                                                  const double* __restrict__ patd, KParams<R> P, c128 pk,
                                                  c128* __restrict__ b) {
-  const RhsItem it = items[blockIdx.x];
-  const FarBlk B = far[it.blk];
-  const int il = it.il0 + (threadIdx.x >> 5);
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (il >= B.nr) return;
-  const int i = B.r0 + il;
+  if (i >= ne) return;
+  const int leaf = elem_leaf[i];
+  const int q0 = rptr[leaf], q1 = rptr[leaf + 1];
   cplx<R> s[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
-  for (int el = lane; el < B.nc; el += 32) {
-    const int e = B.c0 + el;
+  // lane-strided walk over the concatenation of the ranges [c0, c0 + nc)
+  int q = q0, base = 0;
+  int c0 = q < q1 ? rng[2 * q] : 0, nc = q < q1 ? rng[2 * q + 1] : 0;
+  for (int v = lane;; v += 32) {
+    while (q < q1 && v >= base + nc) {
+      base += nc;
+      ++q;
+      if (q < q1) {
+        c0 = rng[2 * q];
+        nc = rng[2 * q + 1];
+      }
+    }
+    if (q >= q1) break;
+    const int e = c0 + (v - base);
     R p3[3];
     if (sizeof(R) == 4) {
       p3[0] = R(patf[3 * e]);
@@ -850,14 +909,57 @@ __global__ void __launch_bounds__(256) k_rhs_far(const RhsItem* __restrict__ ite
         for (int c = 0; c < 3; ++c) cfmr(s[a], -acc.t[3 * a + c], p3[c]);
     }
   }
+  R red[6];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    R re = wred(s[a].re), im = wred(s[a].im);
-    if (lane == 0 && (re != R(0) || im != R(0))) {
-      c128 v = c128{(double)re, (double)im} * pk;
-      atomicAdd(&b[3LL * i + a].re, v.re);
-      atomicAdd(&b[3LL * i + a].im, v.im);
-    }
+    red[2 * a] = wred(s[a].re);
+    red[2 * a + 1] = wred(s[a].im);
+  }
+  if (lane < 3) {
+    R re = lane == 0 ? red[0] : (lane == 1 ? red[2] : red[4]);
+    R im = lane == 0 ? red[1] : (lane == 1 ? red[3] : red[5]);
+    c128 v = c128{(double)re, (double)im} * pk;
+    c128& t = b[3LL * i + lane];
+    t = c128{t.re + v.re, t.im + v.im};
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Entries of an admissible block as they enter the system matrix: the column
+// element's boundary condition selects T (traction prescribed: unknown
+// displacement) or -U (displacement prescribed: unknown traction).
+// aca_row3: row component ia of collocation element ie against element e
+// (three columns); aca_col3: column component jc of element je against
+// collocation element i (three rows).
+// ---------------------------------------------------------------------------
+template <typename R, typename T>
+__device__ __forceinline__ void aca_row3(const ElemF* ef, const ElemD* ed, const signed char* bc,
+                                         const KParams<R>& P, int ie, int ia, int e, cplx<T> out[3]) {
+  PairGeo<R> g;
+  int band;
+  pair_geo(ef, ed, ie, e, g, band);
+  UTAcc<R> acc;
+  regular_pair<R>(acc, g, band, P);
+  bool trac = bc[e] == BEM_BC_TRACTION;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cplx<R> v = trac ? acc.t[3 * ia + c] : -acc.U(ia, c);
+    out[c] = mk<T>(T(v.re), T(v.im));
+  }
+}
+template <typename R, typename T>
+__device__ __forceinline__ void aca_col3(const ElemF* ef, const ElemD* ed, const signed char* bc,
+                                         const KParams<R>& P, int i, int je, int jc, cplx<T> out[3]) {
+  PairGeo<R> g;
+  int band;
+  pair_geo(ef, ed, i, je, g, band);
+  UTAcc<R> acc;
+  regular_pair<R>(acc, g, band, P);
+  bool trac = bc[je] == BEM_BC_TRACTION;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cplx<R> v = trac ? acc.t[3 * a + jc] : -acc.U(a, jc);
+    out[a] = mk<T>(T(v.re), T(v.im));
   }
 }
 
@@ -920,38 +1022,56 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
                                                      const ElemD* __restrict__ ed,
                                                      const signed char* __restrict__ bc, KParams<R> P,
                                                      Op* __restrict__ Ustore, Op* __restrict__ Vstore,
-                                                     int* __restrict__ rank, int* __restrict__ fails, double eps_d) {
+                                                     int* __restrict__ rank, int* __restrict__ fails, double eps_d,
+                                                     AcaState st) {
   using T = decltype(Op{}.re);
   const T eps = T(eps_d);
   const int bi = list[blockIdx.x];
+  if (st.done && st.done[bi]) return;
   FarBlk B = blks[bi];
   const int m = 3 * B.nr, n = 3 * B.nc;
   Op* Ub = Ustore + B.uoff;
   Op* Vb = Vstore + B.voff;
+  int* piv_i = st.piv_i + B.toff;
+  int* piv_j = st.piv_j + B.toff;
   __shared__ AcaShared<T> sh;
   const int rmax = min(B.rmax, ACA_RMAX);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int k = 0;
+  int k = st.kstart ? min(st.kstart[bi], rmax) : 0;
   int istar = 0;
-  T normS2 = 0;
+  T normS2 = k ? T(st.norm0[bi]) : T(0);
   bool converged = false;
+  if (k > 0) {
+    // continue from a reused cross approximation of rank k: its pivot rows
+    // are used, the next row is the largest entry of u_{k-1} outside them
+    for (int l = threadIdx.x; l < k; l += blockDim.x) sh.rows_used[l] = piv_i[l];
+    const int prev = piv_i[k - 1];
+    T bu = T(-1);
+    int inext = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      if (i == prev) continue;
+      Op u = Ub[(long long)(k - 1) * m + i];
+      T a = u.re * u.re + u.im * u.im;
+      if (a > bu) {
+        bu = a;
+        inext = i;
+      }
+    }
+    aca_argmax(bu, inext, sh);
+    if (!(bu > T(0))) {
+      if (threadIdx.x == 0) rank[bi] = k;
+      return;
+    }
+    istar = inext;
+    __syncthreads();
+  }
   while (k < rmax) {
     // --- residual row istar -> V[:, k]
     int ie = B.r0 + istar / 3, ia = istar % 3;
     for (int el = threadIdx.x; el < B.nc; el += blockDim.x) {
       int e = B.c0 + el;
-      PairGeo<R> g;
-      int band;
-      pair_geo(ef, ed, ie, e, g, band);
-      UTAcc<R> acc;
-      regular_pair<R>(acc, g, band, P);
-      bool trac = bc[e] == BEM_BC_TRACTION;
       cplx<T> vv[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        cplx<R> v = trac ? acc.t[3 * ia + c] : -acc.U(ia, c);
-        vv[c] = mk<T>(T(v.re), T(v.im));
-      }
+      aca_row3<R, T>(ef, ed, bc, P, ie, ia, e, vv);
       const Op* vrow = Vb + 3 * el;
 #pragma unroll 4
       for (int l = 0; l < k; ++l) {
@@ -989,23 +1109,17 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
       Op v = Vb[(long long)k * n + j];
       Vb[(long long)k * n + j] = to_op<Op>(mk<T>(v.re, v.im) * ipiv);
     }
+    if (threadIdx.x == 0) {
+      piv_i[k] = istar;
+      piv_j[k] = jstar;
+    }
     __syncthreads();
     // --- residual column jstar -> U[:, k]
     int je = B.c0 + jstar / 3, jc = jstar % 3;
-    bool trac = bc[je] == BEM_BC_TRACTION;
     for (int il = threadIdx.x; il < B.nr; il += blockDim.x) {
       int i = B.r0 + il;
-      PairGeo<R> g;
-      int band;
-      pair_geo(ef, ed, i, je, g, band);
-      UTAcc<R> acc;
-      regular_pair<R>(acc, g, band, P);
       cplx<T> uu[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        cplx<R> v = trac ? acc.t[3 * a + jc] : -acc.U(a, jc);
-        uu[a] = mk<T>(T(v.re), T(v.im));
-      }
+      aca_col3<R, T>(ef, ed, bc, P, i, je, jc, uu);
       const Op* ucol = Ub + 3 * il;
 #pragma unroll 4
       for (int l = 0; l < k; ++l) {
@@ -1116,12 +1230,13 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
                                                               const signed char* __restrict__ bc, KParams<R> P,
                                                               Op* __restrict__ Ustore, Op* __restrict__ Vstore,
                                                               int* __restrict__ rank, int* __restrict__ fails,
-                                                              double eps_d) {
+                                                              double eps_d, AcaState st) {
   using T = decltype(Op{}.re);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * ACAW_WARPS + wid;
   if (item >= count) return;
   const int bi = list[item];
+  if (st.done && st.done[bi]) return;
   __shared__ int rows_used_all[ACAW_WARPS][ACA_RMAX];
   int* rows_used = rows_used_all[wid];
   const T eps = T(eps_d);
@@ -1129,26 +1244,42 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
   const int m = 3 * B.nr, n = 3 * B.nc;
   Op* Ub = Ustore + B.uoff;
   Op* Vb = Vstore + B.voff;
+  int* piv_i = st.piv_i + B.toff;
+  int* piv_j = st.piv_j + B.toff;
   const int rmax = min(B.rmax, ACA_RMAX);
-  int k = 0, istar = 0;
-  T normS2 = 0;
+  int k = st.kstart ? min(st.kstart[bi], rmax) : 0;
+  int istar = 0;
+  T normS2 = k ? T(st.norm0[bi]) : T(0);
   bool converged = false;
+  if (k > 0) {
+    // continue from a reused cross approximation of rank k (see k_aca)
+    for (int l = lane; l < k; l += 32) rows_used[l] = piv_i[l];
+    const int prev = piv_i[k - 1];
+    T bu = T(-1);
+    int inext = 0;
+    for (int i = lane; i < m; i += 32) {
+      if (i == prev) continue;
+      Op u = Ub[(long long)(k - 1) * m + i];
+      T a = u.re * u.re + u.im * u.im;
+      if (a > bu) {
+        bu = a;
+        inext = i;
+      }
+    }
+    warp_argmax(bu, inext);
+    if (!(bu > T(0))) {
+      if (lane == 0) rank[bi] = k;
+      return;
+    }
+    istar = inext;
+    __syncwarp();
+  }
   while (k < rmax) {
     int ie = B.r0 + istar / 3, ia = istar % 3;
     for (int el = lane; el < B.nc; el += 32) {
       int e = B.c0 + el;
-      PairGeo<R> g;
-      int band;
-      pair_geo(ef, ed, ie, e, g, band);
-      UTAcc<R> acc;
-      regular_pair<R>(acc, g, band, P);
-      bool trac = bc[e] == BEM_BC_TRACTION;
       cplx<T> vv[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        cplx<R> v = trac ? acc.t[3 * ia + c] : -acc.U(ia, c);
-        vv[c] = mk<T>(T(v.re), T(v.im));
-      }
+      aca_row3<R, T>(ef, ed, bc, P, ie, ia, e, vv);
       const Op* vrow = Vb + 3 * el;
 #pragma unroll 4
       for (int l = 0; l < k; ++l) {
@@ -1186,22 +1317,16 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
       Op v = Vb[(long long)k * n + j];
       Vb[(long long)k * n + j] = to_op<Op>(mk<T>(v.re, v.im) * ipiv);
     }
+    if (lane == 0) {
+      piv_i[k] = istar;
+      piv_j[k] = jstar;
+    }
     __syncwarp();
     int je = B.c0 + jstar / 3, jc = jstar % 3;
-    bool trac = bc[je] == BEM_BC_TRACTION;
     for (int il = lane; il < B.nr; il += 32) {
       int i = B.r0 + il;
-      PairGeo<R> g;
-      int band;
-      pair_geo(ef, ed, i, je, g, band);
-      UTAcc<R> acc;
-      regular_pair<R>(acc, g, band, P);
       cplx<T> uu[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        cplx<R> v = trac ? acc.t[3 * a + jc] : -acc.U(a, jc);
-        uu[a] = mk<T>(T(v.re), T(v.im));
-      }
+      aca_col3<R, T>(ef, ed, bc, P, i, je, jc, uu);
       const Op* ucol = Ub + 3 * il;
 #pragma unroll 4
       for (int l = 0; l < k; ++l) {
@@ -1265,6 +1390,270 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
 }
 
 // ---------------------------------------------------------------------------
+// Cross-frequency reuse of the ACA pivots (not in the paper; its Sec. 5 names
+// the per-frequency assembly as the cost to cut).
+//
+// With the pivot rows I = (i_1..i_r) and columns J = (j_1..j_r) that ACA chose
+// for a block at the previous frequency, the cross approximation through the
+// same pivots at the new s is
+//     A ~ C P^{-1} R,  C = A(:, J), R = A(I, :), P = A(I, J) = L Uh
+// (LU without pivoting, in the pivot order), which is exactly what ACA
+// produces when it visits those pivots in that order. Stored as
+//     U = C Uh^{-1},  V^T = L^{-1} R,
+// step l of which equals ACA's step l (u_l v_l^T). Evaluating C and R is one
+// fully parallel pass; the two triangular solves run per block from shared
+// memory. Pivot l is kept only while it is still near-maximal in its residual
+// row (|Uh_ll| >= tau max_j |(L^{-1} R)_lj|); the usual stopping test
+// |u_l| |v_l| <= eps ||S_l|| then picks the rank. Blocks that do not meet it
+// continue with ordinary ACA steps from there (k_aca / k_aca_warp).
+// ---------------------------------------------------------------------------
+constexpr int WARM_THREADS = 256;
+
+// Pivot rows into V[:, l] and pivot columns into U[:, l], l < rank of the
+// previous frequency.
+template <typename R, typename Op>
+__global__ void __launch_bounds__(WARM_THREADS) k_aca_warm_eval(const FarBlk* __restrict__ blks,
+                                                                const ElemF* __restrict__ ef,
+                                                                const ElemD* __restrict__ ed,
+                                                                const signed char* __restrict__ bc, KParams<R> P,
+                                                                Op* __restrict__ Ustore, Op* __restrict__ Vstore,
+                                                                const int* __restrict__ rank,
+                                                                const int* __restrict__ piv_i,
+                                                                const int* __restrict__ piv_j) {
+  using T = decltype(Op{}.re);
+  const int bi = blockIdx.x;
+  const int r = rank[bi];
+  if (r <= 0 || r > WARM_RMAX) return;
+  const FarBlk B = blks[bi];
+  const int m = 3 * B.nr, n = 3 * B.nc;
+  Op* Ub = Ustore + B.uoff;
+  Op* Vb = Vstore + B.voff;
+  const int* pi = piv_i + B.toff;
+  const int* pj = piv_j + B.toff;
+  const int nrow = r * B.nc, total = nrow + r * B.nr;  // r <= rmax: within the block's U, V storage
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    cplx<T> v[3];
+    if (idx < nrow) {
+      int l = idx / B.nc, el = idx - l * B.nc;
+      int istar = pi[l];
+      aca_row3<R, T>(ef, ed, bc, P, B.r0 + istar / 3, istar % 3, B.c0 + el, v);
+      Op* dst = Vb + (long long)l * n + 3 * el;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dst[c] = to_op<Op>(v[c]);
+    } else {
+      int q = idx - nrow;
+      int l = q / B.nr, il = q - l * B.nr;
+      int jstar = pj[l];
+      aca_col3<R, T>(ef, ed, bc, P, B.r0 + il, B.c0 + jstar / 3, jstar % 3, v);
+      Op* dst = Ub + (long long)l * m + 3 * il;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dst[a] = to_op<Op>(v[a]);
+    }
+  }
+}
+
+constexpr int WARM_SOLVE_THREADS = 128;
+constexpr int WARM_CH = 8;  // rows of a triangular solve held in registers at a time
+
+template <typename T> __device__ __forceinline__ void smem_max(T* a, T v);
+template <> __device__ __forceinline__ void smem_max<float>(float* a, float v) {
+  atomicMax(reinterpret_cast<int*>(a), __float_as_int(v));  // v >= 0: integer order = float order
+}
+template <> __device__ __forceinline__ void smem_max<double>(double* a, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename T> __device__ __forceinline__ T wmaxT(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Per block: LU of P, V^T = L^{-1} R and U = C Uh^{-1} in place, the pivot
+// test, and the ACA stopping test over the reused steps. Writes the state the
+// ACA kernels continue from. One launch per rank class: this one handles the
+// blocks with RLO < r <= RCAP, its shared memory sized for RCAP. Blocks with
+// nothing to reuse (r <= 0) are written as cold starts by the launch with
+// RLO = 0, blocks above the last class's RCAP by the LAST launch.
+template <typename Op, int RLO, int RCAP, bool LAST>
+__global__ void __launch_bounds__(WARM_SOLVE_THREADS) k_aca_warm_solve(const FarBlk* __restrict__ blks,
+                                                                       Op* __restrict__ Ustore,
+                                                                       Op* __restrict__ Vstore,
+                                                                       int* __restrict__ rank,
+                                                                       const int* __restrict__ piv_i,
+                                                                       const int* __restrict__ piv_j,
+                                                                       int* __restrict__ kstart,
+                                                                       double* __restrict__ norm0,
+                                                                       int* __restrict__ done, double eps_d,
+                                                                       double tau_d) {
+  using T = decltype(Op{}.re);
+  using C = cplx<T>;
+  constexpr int NW = WARM_SOLVE_THREADS / 32;
+  extern __shared__ __align__(16) unsigned char warm_smem[];
+  C* Ps = reinterpret_cast<C*>(warm_smem);                 // r x r, row-major
+  T* rowmax = reinterpret_cast<T*>(Ps + RCAP * RCAP);
+  T* nv2w = rowmax + RCAP;                                 // [l][warp]
+  T* nu2w = nv2w + RCAP * NW;
+  __shared__ int sh_rp, sh_ls;
+  const int bi = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int r = rank[bi];
+  if (r <= RLO || r > RCAP) {
+    if (((RLO == 0 && r <= 0) || (LAST && r > RCAP)) && tid == 0) {
+      kstart[bi] = 0;
+      norm0[bi] = 0.0;
+      done[bi] = 0;
+    }
+    return;
+  }
+  const FarBlk B = blks[bi];
+  const int m = 3 * B.nr, n = 3 * B.nc;
+  Op* Ub = Ustore + B.uoff;
+  Op* Vb = Vstore + B.voff;
+  const int* pi = piv_i + B.toff;
+  const int* pj = piv_j + B.toff;
+  for (int idx = tid; idx < r * r; idx += blockDim.x) {
+    int l = idx / r, q = idx - l * r;
+    Op v = Vb[(long long)l * n + pj[q]];
+    Ps[idx] = mk<T>(v.re, v.im);
+  }
+  for (int l = tid; l < RCAP; l += blockDim.x) {
+    rowmax[l] = T(0);
+    for (int w = 0; w < NW; ++w) nv2w[l * NW + w] = nu2w[l * NW + w] = T(0);
+  }
+  if (tid == 0) sh_rp = r;
+  __syncthreads();
+  // LU without pivoting, stopped at the first zero (or non-finite) pivot
+  for (int l = 0; l < r; ++l) {
+    C d = Ps[l * r + l];
+    if (!(abs2(d) > T(0))) {  // uniform: every thread reads the same value
+      if (tid == 0) sh_rp = l;
+      break;
+    }
+    C id = inv(d);
+    for (int p = l + 1 + tid; p < r; p += blockDim.x) Ps[p * r + l] = Ps[p * r + l] * id;
+    __syncthreads();
+    const int w = r - l - 1;
+    for (int idx = tid; idx < w * w; idx += blockDim.x) {
+      int p = l + 1 + idx / w, q = l + 1 + idx % w;
+      Ps[p * r + q] = Ps[p * r + q] - Ps[p * r + l] * Ps[l * r + q];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  const int rp = sh_rp;
+  // V^T <- L^{-1} R column by column; residual-row maxima and norms per row
+  for (int j0 = 0; j0 < n; j0 += blockDim.x) {
+    const int j = j0 + tid;
+    const bool act = j < n;
+    for (int c0 = 0; c0 < rp; c0 += WARM_CH) {
+      C acc[WARM_CH];
+#pragma unroll
+      for (int t = 0; t < WARM_CH; ++t) {
+        Op v = (act && c0 + t < rp) ? Vb[(long long)(c0 + t) * n + j] : Op{};
+        acc[t] = mk<T>(v.re, v.im);
+      }
+#pragma unroll 4
+      for (int q = 0; q < c0; ++q) {
+        Op xv = act ? Vb[(long long)q * n + j] : Op{};
+        C x = mk<T>(xv.re, xv.im);
+#pragma unroll
+        for (int t = 0; t < WARM_CH; ++t)
+          if (c0 + t < rp) acc[t] = acc[t] - Ps[(c0 + t) * r + q] * x;
+      }
+#pragma unroll
+      for (int t = 0; t < WARM_CH; ++t) {
+        if (c0 + t >= rp) break;
+#pragma unroll
+        for (int u = 0; u < t; ++u) acc[t] = acc[t] - Ps[(c0 + t) * r + c0 + u] * acc[u];
+        if (act) Vb[(long long)(c0 + t) * n + j] = to_op<Op>(acc[t]);
+        T a2 = act ? abs2(acc[t]) : T(0);
+        T mx = wmaxT(a2);
+        T sm = wsumT(a2);
+        if (lane == 0) {
+          smem_max(&rowmax[c0 + t], mx);
+          nv2w[(c0 + t) * NW + wid] += sm;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const T tau2 = T(tau_d * tau_d);
+    int ls = rp;
+    for (int l = 0; l < rp; ++l)
+      if (abs2(Ps[l * r + l]) < tau2 * rowmax[l]) {
+        ls = l;
+        break;
+      }
+    sh_ls = ls;
+  }
+  __syncthreads();
+  const int ls = sh_ls;
+  // U <- C Uh^{-1} row by row
+  for (int i0 = 0; i0 < m; i0 += blockDim.x) {
+    const int i = i0 + tid;
+    const bool act = i < m;
+    for (int c0 = 0; c0 < ls; c0 += WARM_CH) {
+      C acc[WARM_CH];
+#pragma unroll
+      for (int t = 0; t < WARM_CH; ++t) {
+        Op v = (act && c0 + t < ls) ? Ub[(long long)(c0 + t) * m + i] : Op{};
+        acc[t] = mk<T>(v.re, v.im);
+      }
+#pragma unroll 4
+      for (int p = 0; p < c0; ++p) {
+        Op xv = act ? Ub[(long long)p * m + i] : Op{};
+        C x = mk<T>(xv.re, xv.im);
+#pragma unroll
+        for (int t = 0; t < WARM_CH; ++t)
+          if (c0 + t < ls) acc[t] = acc[t] - x * Ps[p * r + c0 + t];
+      }
+#pragma unroll
+      for (int t = 0; t < WARM_CH; ++t) {
+        if (c0 + t >= ls) break;
+#pragma unroll
+        for (int u = 0; u < t; ++u) acc[t] = acc[t] - acc[u] * Ps[(c0 + u) * r + c0 + t];
+        acc[t] = acc[t] * inv(Ps[(c0 + t) * r + c0 + t]);
+        if (act) Ub[(long long)(c0 + t) * m + i] = to_op<Op>(acc[t]);
+        T sm = wsumT(act ? abs2(acc[t]) : T(0));
+        if (lane == 0) nu2w[(c0 + t) * NW + wid] += sm;
+      }
+    }
+  }
+  __syncthreads();
+  // earlier pivot rows are represented exactly: zero them as ACA does
+  for (int idx = tid; idx < ls * ls; idx += blockDim.x) {
+    int q = idx / ls, p = idx % ls;
+    if (p < q) Ub[(long long)q * m + pi[p]] = Op{};
+  }
+  if (tid == 0) {
+    const T eps2 = T(eps_d * eps_d);
+    T S = 0;
+    int kc = ls;
+    int conv = 0;
+    for (int l = 0; l < ls; ++l) {
+      T nu = 0, nv = 0;
+      for (int w = 0; w < NW; ++w) {
+        nu += nu2w[l * NW + w];
+        nv += nv2w[l * NW + w];
+      }
+      T term = nu * nv;
+      S += term;
+      if (term <= eps2 * S) {
+        kc = l + 1;
+        conv = 1;
+        break;
+      }
+    }
+    kstart[bi] = kc;
+    norm0[bi] = double(S);
+    done[bi] = conv;
+    if (conv) rank[bi] = kc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 void launch_centroids(const double* xyz, long long nv, const int* tri, int ne, double* cen, double* h,
@@ -1310,25 +1699,60 @@ void launch_sing(const SingPair* pairs, int n, const ElemD* ed, const double* po
                  const double* stat, const KParams<R>& P, Op* near, c128* pinv, const double* pattern, c128 pk,
                  c128* b, int* status, cudaStream_t st) {
   if (count_if(n))
-    k_sing<R, Op><<<(n + 3) / 4, 128, 0, st>>>(pairs, n, ed, polar, bc, stat, P, near, pinv, pattern, pk, b, status);
+    k_sing<R, Op><<<(n + 15) / 16, 256, 0, st>>>(pairs, n, ed, polar, bc, stat, P, near, pinv, pattern, pk, b, status);
 }
 template <typename R>
-void launch_rhs_far(const void* items, int nitems, const FarBlk* far, const ElemF* ef, const ElemD* ed,
+void launch_rhs_far(const int* rng, const int* rptr, const int* elem_leaf, int ne, const ElemF* ef, const ElemD* ed,
                     const signed char* bc, const float* patf, const double* patd, const KParams<R>& P, c128 pk,
                     c128* b, cudaStream_t st) {
-  if (count_if(nitems))
-    k_rhs_far<R><<<nitems, 256, 0, st>>>(reinterpret_cast<const RhsItem*>(items), far, ef, ed, bc, patf, patd, P, pk,
-                                         b);
+  if (count_if(ne)) k_rhs_far<R><<<(ne + 7) / 8, 256, 0, st>>>(rng, rptr, elem_leaf, ne, ef, ed, bc, patf, patd, P, pk, b);
 }
 template <typename R, typename Op>
 void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int* large_list, int nlarge,
                 const ElemF* ef, const ElemD* ed, const signed char* bc, const KParams<R>& P, Op* U, Op* V, int* rank,
-                int* fails, double eps, cudaStream_t st) {
+                int* fails, double eps, const AcaState& state, cudaStream_t st) {
   if (count_if(nlarge))
-    k_aca<R, Op><<<nlarge, ACA_THREADS, 0, st>>>(large_list, blks, ef, ed, bc, P, U, V, rank, fails, eps);
+    k_aca<R, Op><<<nlarge, ACA_THREADS, 0, st>>>(large_list, blks, ef, ed, bc, P, U, V, rank, fails, eps, state);
   if (count_if(nsmall))
     k_aca_warp<R, Op><<<(nsmall + ACAW_WARPS - 1) / ACAW_WARPS, 32 * ACAW_WARPS, 0, st>>>(
-        small_list, nsmall, blks, ef, ed, bc, P, U, V, rank, fails, eps);
+        small_list, nsmall, blks, ef, ed, bc, P, U, V, rank, fails, eps, state);
+}
+
+template <typename Op> size_t warm_solve_smem(int rcap) {
+  using T = decltype(Op{}.re);
+  return sizeof(cplx<T>) * rcap * rcap + sizeof(T) * rcap * (1 + 2 * (WARM_SOLVE_THREADS / 32));
+}
+
+template <typename Op, int RLO, int RCAP, bool LAST>
+cudaError_t launch_warm_solve(const FarBlk* blks, int nfar, Op* U, Op* V, int* rank, const int* piv_i,
+                              const int* piv_j, int* kstart, double* norm0, int* done, double eps, double tau,
+                              cudaStream_t st) {
+  const size_t sm = warm_solve_smem<Op>(RCAP);
+  static_assert(sizeof(Op) * RCAP * RCAP <= 200 * 1024, "pivot block must fit in shared memory");
+  cudaError_t e = cudaFuncSetAttribute(k_aca_warm_solve<Op, RLO, RCAP, LAST>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  count_if(true);
+  k_aca_warm_solve<Op, RLO, RCAP, LAST><<<nfar, WARM_SOLVE_THREADS, sm, st>>>(blks, U, V, rank, piv_i, piv_j,
+                                                                              kstart, norm0, done, eps, tau);
+  return cudaGetLastError();
+}
+
+template <typename R, typename Op>
+cudaError_t launch_aca_warm(const FarBlk* blks, int nfar, const ElemF* ef, const ElemD* ed, const signed char* bc,
+                            const KParams<R>& P, Op* U, Op* V, int* rank, int* piv_i, int* piv_j, int* kstart,
+                            double* norm0, int* done, double eps, double tau, cudaStream_t st) {
+  if (!nfar) return cudaSuccess;
+  count_if(true);
+  k_aca_warm_eval<R, Op><<<nfar, WARM_THREADS, 0, st>>>(blks, ef, ed, bc, P, U, V, rank, piv_i, piv_j);
+  // rank classes (0, 64] and (64, 128]; complex128 pivot blocks above rank
+  // 112 do not fit in shared memory and restart ACA
+  constexpr int RTOP = sizeof(Op) == 8 ? WARM_RMAX : 112;
+  cudaError_t e = launch_warm_solve<Op, 0, WARM_SPLIT, false>(blks, nfar, U, V, rank, piv_i, piv_j, kstart, norm0,
+                                                              done, eps, tau, st);
+  if (e != cudaSuccess) return e;
+  return launch_warm_solve<Op, WARM_SPLIT, RTOP, true>(blks, nfar, U, V, rank, piv_i, piv_j, kstart, norm0, done,
+                                                       eps, tau, st);
 }
 
 template void launch_near_regular<float, c64>(const NearBlk*, int, int, const unsigned*, const long long*,
@@ -1345,15 +1769,23 @@ template void launch_sing<float, c64>(const SingPair*, int, const ElemD*, const 
 template void launch_sing<double, c128>(const SingPair*, int, const ElemD*, const double*, const signed char*,
                                         const double*, const KParams<double>&, c128*, c128*, const double*, c128,
                                         c128*, int*, cudaStream_t);
-template void launch_rhs_far<float>(const void*, int, const FarBlk*, const ElemF*, const ElemD*, const signed char*,
-                                    const float*, const double*, const KParams<float>&, c128, c128*, cudaStream_t);
-template void launch_rhs_far<double>(const void*, int, const FarBlk*, const ElemF*, const ElemD*, const signed char*,
-                                     const float*, const double*, const KParams<double>&, c128, c128*, cudaStream_t);
+template void launch_rhs_far<float>(const int*, const int*, const int*, int, const ElemF*, const ElemD*,
+                                     const signed char*, const float*, const double*, const KParams<float>&, c128,
+                                     c128*, cudaStream_t);
+template void launch_rhs_far<double>(const int*, const int*, const int*, int, const ElemF*, const ElemD*,
+                                      const signed char*, const float*, const double*, const KParams<double>&, c128,
+                                      c128*, cudaStream_t);
 template void launch_aca<float, c64>(const FarBlk*, const int*, int, const int*, int, const ElemF*, const ElemD*,
                                      const signed char*, const KParams<float>&, c64*, c64*, int*, int*, double,
-                                     cudaStream_t);
+                                     const AcaState&, cudaStream_t);
 template void launch_aca<double, c128>(const FarBlk*, const int*, int, const int*, int, const ElemF*,
                                        const ElemD*, const signed char*, const KParams<double>&, c128*, c128*, int*,
-                                       int*, double, cudaStream_t);
+                                       int*, double, const AcaState&, cudaStream_t);
+template cudaError_t launch_aca_warm<float, c64>(const FarBlk*, int, const ElemF*, const ElemD*, const signed char*,
+                                                 const KParams<float>&, c64*, c64*, int*, int*, int*, int*, double*,
+                                                 int*, double, double, cudaStream_t);
+template cudaError_t launch_aca_warm<double, c128>(const FarBlk*, int, const ElemF*, const ElemD*,
+                                                   const signed char*, const KParams<double>&, c128*, c128*, int*,
+                                                   int*, int*, int*, double*, int*, double, double, cudaStream_t);
 
 }  // namespace bem

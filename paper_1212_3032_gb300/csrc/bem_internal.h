@@ -79,6 +79,19 @@ struct SingPair {
   int self;         // 1 for i == e
 };
 
+// Start state of the ACA kernels (cross-frequency pivot reuse). Pivots are
+// recorded for every block at offset FarBlk::toff; kstart / norm0 / done may
+// be null (every block starts from rank 0).
+constexpr int WARM_RMAX = 128;  // largest reused rank (= the rank cap)
+constexpr int WARM_SPLIT = 64;  // rank classes of the reuse solve: (0, 64] and above
+struct AcaState {
+  const int* kstart;    // per far block: rank to continue from
+  const double* norm0;  // per far block: ||S||_F^2 estimate at that rank
+  const int* done;      // per far block: 1 = converged already (skip)
+  int* piv_i;           // pivot row of each step (block-local scalar index)
+  int* piv_j;           // pivot column of each step
+};
+
 template <typename T> struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
@@ -165,8 +178,9 @@ struct bem_ctx {
   bem::DevBuf<long long> poff;        // per near block: offset of its sorted pair list
   bem::DevBuf<unsigned> plist;        // sorted regular pairs of the near blocks
   bem::DevBuf<int> pcount;            // regular pairs per near block
-  int nrhs_items = 0;
-  bem::DevBuf<int> rhs_items;         // (far block, first row) pairs for the far RHS
+  bem::DevBuf<int> rhs_rng;           // far RHS: (c0, nc) column ranges of each leaf's far panels
+  bem::DevBuf<int> rhs_rptr;          // CSR of those ranges over leaves
+  bem::DevBuf<int> elem_leaf;         // leaf of each element (tree order)
   bem::DevBuf<float> patf;            // prescribed pattern (tree order, FP32)
   int nfar_small = 0, nfar_large = 0;
   bem::DevBuf<int> far_small, far_large;  // admissible block indices by size class
@@ -187,6 +201,16 @@ struct bem_ctx {
   bem::DevBuf<bem::c128> near64, u64, v64, t64;
   bem::DevBuf<int> rank;
   bem::DevBuf<int> aca_fail;
+  // cross-frequency reuse of ACA pivots
+  bool aca_reuse = true;               // bem_set_aca_reuse
+  bool aca_warm_ok = false;            // pivots of a previous assembly of this mesh are stored
+  bool aca_last_warm = false;          // the last assembly started from reused pivots
+  double aca_tau = 0.1;                // pivot test of the reused steps
+  bem::DevBuf<int> piv_i, piv_j;       // t_entries each
+  bem::DevBuf<int> aca_kstart, aca_done;
+  bem::DevBuf<double> aca_norm0;
+  long long prof_aca_blocks = 0;       // far blocks assembled (profiling)
+  long long prof_aca_continued = 0;    // of which took ACA steps (not settled by reuse alone)
   bem::DevBuf<int> status;             // singular 3x3 diagonal block flag
   bem::DevBuf<bem::c128> prec_inv;     // ne x 9 inverse diagonal blocks
   bem::DevBuf<bem::c64> prec_inv32;

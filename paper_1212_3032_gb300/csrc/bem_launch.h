@@ -29,16 +29,27 @@ template <typename R, typename Op>
 void launch_sing(const SingPair* pairs, int n, const ElemD* ed, const double* polar, const signed char* bc,
                  const double* stat, const KParams<R>& P, Op* near, c128* pinv, const double* pattern, c128 pk,
                  c128* b, int* status, cudaStream_t st);
-// Far blocks' share of b += pk * B(s) pattern (items: far block, first row of 8).
+// Far blocks' share of b += pk * B(s) pattern, one warp per row element:
+// rng holds (c0, nc) column ranges, rptr the ranges of each leaf, elem_leaf
+// the leaf of each element (tree order). Must be the first writer of b after
+// it is zeroed (plain read-modify-write per row).
 template <typename R>
-void launch_rhs_far(const void* items, int nitems, const FarBlk* far, const ElemF* ef, const ElemD* ed,
+void launch_rhs_far(const int* rng, const int* rptr, const int* elem_leaf, int ne, const ElemF* ef, const ElemD* ed,
                     const signed char* bc, const float* patf, const double* patd, const KParams<R>& P, c128 pk,
                     c128* b, cudaStream_t st);
 // Admissible blocks split in two lists: small ones one warp each, large ones one CTA each.
 template <typename R, typename Op>
 void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int* large_list, int nlarge,
                 const ElemF* ef, const ElemD* ed, const signed char* bc, const KParams<R>& P, Op* U, Op* V, int* rank,
-                int* fails, double eps, cudaStream_t st);
+                int* fails, double eps, const AcaState& state, cudaStream_t st);
+// Reuse of the previous assembly's pivots: evaluates the pivot rows and
+// columns at the new s, forms the cross approximation through them and
+// writes the start state (kstart, norm0, done) for launch_aca. rank holds the
+// previous ranks on entry and the new rank of every converged block on exit.
+template <typename R, typename Op>
+cudaError_t launch_aca_warm(const FarBlk* blks, int nfar, const ElemF* ef, const ElemD* ed, const signed char* bc,
+                            const KParams<R>& P, Op* U, Op* V, int* rank, int* piv_i, int* piv_j, int* kstart,
+                            double* norm0, int* done, double eps, double tau, cudaStream_t st);
 
 // ---- solver (bem_solve.cu) ----
 // H-matrix product y = A x for nrhs right-hand sides (x, y: nrhs vectors of

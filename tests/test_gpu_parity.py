@@ -131,11 +131,15 @@ def test_mixed_bc_rows_and_rhs(ctx, B, prec, tol):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_hmatrix_rows_match_oracle(ctx, B, prec):
-    mesh = inputs.cavity_problem(7)                       # 980 elements, ragged leaves
+    # 980 elements, leaf 32: 708 dense near blocks, 316 ACA blocks, ragged leaves
+    mesh = inputs.cavity_problem(7)
     aca_tol = 1e-5
-    o = _mesh_ctx(ctx, B, mesh, dense=0, precision=prec, aca_tol=aca_tol, leaf_size=64)
+    o = _mesh_ctx(ctx, B, mesh, dense=0, precision=prec, aca_tol=aca_tol, leaf_size=32)
     s = 0.625 + 3.0j
+    ctx.set_profiling(True)
     ctx.assemble(s, o)
+    assert ctx.get_profile()["aca_blocks"] > 300
+    ctx.set_profiling(False)
     g = bem.geometry(mesh.xyz, mesh.tri)
     rows_e = np.array([0, 333, 979])
     A_ref, _ = bem.system_rows(g, mesh.bc_type, np.zeros((mesh.ne, 3)), s, MAT, rows=rows_e)
@@ -149,6 +153,86 @@ def test_hmatrix_rows_match_oracle(ctx, B, prec):
     y = ctx.apply(x)
     rows = ctx.operator_rows(np.arange(0, 3 * mesh.ne, 97))
     assert _rel(y[::97], rows @ x) <= (2e-6 if prec == 0 else 1e-12)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_hmatrix_rows_after_pivot_reuse(ctx, B, prec):
+    """Assemblies that start from the previous frequency's ACA pivots meet the
+    same accuracy as a fresh ACA, for a neighbouring frequency and after a
+    large jump in s (where most reused pivots fail the pivot test)."""
+    mesh = inputs.cavity_problem(7)
+    aca_tol = 1e-5
+    o = _mesh_ctx(ctx, B, mesh, dense=0, precision=prec, aca_tol=aca_tol, leaf_size=32)
+    g = bem.geometry(mesh.xyz, mesh.tri)
+    rows_e = np.array([0, 333, 979])
+    ctx.set_aca_reuse(True)
+    ctx.assemble(0.625 + 2.8j, o)                         # cold: first assembly on this mesh
+    for s in (0.625 + 3.0j, 0.3 + 9.0j):
+        ctx.set_profiling(True)
+        ctx.assemble(s, o)                                # warm
+        prof = ctx.get_profile()
+        ctx.set_profiling(False)
+        assert prof["aca_blocks"] > 0
+        if s == 0.625 + 3.0j:
+            # a neighbouring frequency: reuse settles a good share of the blocks
+            assert prof["aca_stepped"] < 0.75 * prof["aca_blocks"]
+        A_ref, _ = bem.system_rows(g, mesh.bc_type, np.zeros((mesh.ne, 3)), s, MAT, rows=rows_e)
+        for m, e in enumerate(rows_e):
+            got = ctx.operator_rows(3 * e + np.arange(3))
+            for a in range(3):
+                assert _rel(got[a], A_ref[3 * m + a]) <= 30 * aca_tol, (s, e, a)
+        rng = np.random.default_rng(4)
+        x = rng.normal(size=3 * mesh.ne) + 1j * rng.normal(size=3 * mesh.ne)
+        y = ctx.apply(x)
+        rows = ctx.operator_rows(np.arange(0, 3 * mesh.ne, 97))
+        assert _rel(y[::97], rows @ x) <= (2e-6 if prec == 0 else 1e-12)
+
+
+def test_pivot_reuse_switch(ctx, B):
+    """With reuse off every assembly is a fresh ACA (all blocks stepped)."""
+    mesh = inputs.cavity_problem(7)
+    o = _mesh_ctx(ctx, B, mesh, dense=0, precision=0, aca_tol=1e-5, leaf_size=32)
+    ctx.set_aca_reuse(False)
+    try:
+        ctx.assemble(0.625 + 2.8j, o)
+        ctx.set_profiling(True)
+        ctx.assemble(0.625 + 3.0j, o)
+        prof = ctx.get_profile()
+        ctx.set_profiling(False)
+        assert prof["aca_stepped"] == prof["aca_blocks"] > 0
+    finally:
+        ctx.set_aca_reuse(True)
+
+
+@pytest.mark.parametrize("k", [64, 128])
+def test_hmatrix_full_size_sampled_rows(ctx, B, k):
+    """The 5,120-element cavity at the benchmark's settings (leaf 64, ACA
+    1e-5, complex64 mixed precision): 4,874 admissible blocks, 246 of them
+    above 256 elements (one CTA each), the rest one warp each. Sampled rows
+    match the oracle at frequency k (fresh ACA) and at k + 1 (pivot reuse)."""
+    mesh = inputs.cavity_problem(16)
+    aca_tol = 1e-5
+    o = _mesh_ctx(ctx, B, mesh, dense=0, precision=0, aca_tol=aca_tol, leaf_size=64)
+    T = 64.0
+    g = bem.geometry(mesh.xyz, mesh.tri)
+    rows_e = np.array([0, 1, 777, 2500, 2501, 4095, 5000, 5119])
+    for kk, warm in ((k, False), (k + 1, True)):
+        s = 5.0 / T + 1j * kk * 2 * math.pi / T
+        ctx.set_profiling(True)
+        ctx.assemble(s, o)
+        prof = ctx.get_profile()
+        ctx.set_profiling(False)
+        assert prof["aca_blocks"] == 4874
+        if warm:
+            assert prof["aca_stepped"] < prof["aca_blocks"]
+        A_ref, b_ref = bem.system_rows(g, mesh.bc_type, mesh.pattern.astype(complex), s, MAT, rows=rows_e)
+        got = ctx.operator_rows((3 * rows_e[:, None] + np.arange(3)).ravel())
+        for q in range(3 * len(rows_e)):
+            assert _rel(got[q], A_ref[q]) <= 30 * aca_tol, (kk, q)
+        # right-hand side: near, singular and far (on-the-fly) contributions
+        b = ctx.rhs(1.0, mesh.pattern)
+        b_sel = b[(3 * rows_e[:, None] + np.arange(3)).ravel()]
+        assert _rel(b_sel, b_ref) <= 2e-5, kk
 
 
 # ---------------------------------------------------------------------------

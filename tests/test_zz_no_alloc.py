@@ -22,10 +22,10 @@ def test_apply_noalloc_matches_apply():
     from paper_1212_3032_gb300 import binding, build
 
     build.build()
-    mesh = inputs.cavity_problem(7)  # 980 triangles: dense near blocks and ACA blocks
+    mesh = inputs.cavity_problem(7)  # 980 triangles, leaf 32: dense near blocks and ACA blocks
     with binding.Context(0) as ctx:
         ctx.set_material(1.0, 0.25, 1.0)
-        o = binding.default_opts(leaf_size=64, aca_tol=1e-5, precision=binding.PREC_C64_MIXED)
+        o = binding.default_opts(leaf_size=32, aca_tol=1e-5, precision=binding.PREC_C64_MIXED)
         ctx.mesh(mesh.xyz, mesh.tri, mesh.bc_type, o)
         ctx.assemble(0.625 + 3.0j, o)
         rng = np.random.default_rng(11)
