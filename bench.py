@@ -255,6 +255,7 @@ def run_ours(args, cfg):
     total_ms = 0.0
     unconverged = 0
     iters = 0
+    phase_ms = {"assemble_ms": 0.0, "guess_ms": 0.0, "solve_ms": 0.0}
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         for _ in range(args.steps):
@@ -268,6 +269,8 @@ def run_ours(args, cfg):
             total_ms += e0.elapsed_time(e1)
             unconverged += sum(1 for s in stats if not s["converged"])
             iters += sum(s["iters"] for s in stats)
+            for key in ("assemble_ms", "guess_ms", "solve_ms"):
+                phase_ms[key] += sum(s[key] for s in stats)
         torch.cuda.synchronize()
     prof = ctx.get_profile()
     ctx.set_profiling(False)
@@ -334,7 +337,10 @@ def run_ours(args, cfg):
                      "peak": peak, "unit": "GB/s", "frac": (hmv_gbs / peak) if hmv_gbs else None,
                      "peak_source": peak_kind, "traffic": None,
                      "launches": prof["hmv_launches"], "ms_total": prof["hmv_ms"]},
-        "phases_ms_per_step": {"hmatvec": prof["hmv_ms"] / args.steps, "assembly": prof["assemble_ms"] / args.steps},
+        "phases_ms_per_step": {"assembly": phase_ms["assemble_ms"] / args.steps,
+                               "initial_guess": phase_ms["guess_ms"] / args.steps,
+                               "gmres": phase_ms["solve_ms"] / args.steps,
+                               "gmres_hmatvec": prof["hmv_ms"] / args.steps},
         "aca": {"pivot_reuse": not args.no_aca_reuse, "blocks": prof["aca_blocks"],
                 "stepped": prof["aca_stepped"]},
         "gpu_launches": prof["kernel_launches"],

@@ -230,7 +230,10 @@ int bem_apply_noalloc(bem_ctx* ctx, const float* x_dev, float* y_dev);
  * pivoting), keeps the leading pivots that are still within a factor 10 of
  * their residual row's largest entry, applies ACA's stopping test
  * |u_l| |v_l| <= aca_tol ||S_l||_F to the reused steps, and continues with
- * ACA steps where it is not met. */
+ * ACA steps where it is not met. ACA records two spare pivots past its
+ * stopping point (their factor columns are stored but not used), so that a
+ * block whose rank grows by one or two between frequencies is settled by
+ * the reuse alone. */
 int bem_set_aca_reuse(bem_ctx* ctx, int on);
 /* Admissible blocks of the current mesh after the last assembly: *count =
  * number of blocks; for the first min(nmax, count) blocks info[4b..4b+3] =

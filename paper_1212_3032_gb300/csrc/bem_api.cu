@@ -258,9 +258,16 @@ void prof_end(bem_ctx* ctx, cudaEvent_t a, int kind, double bytes) {
   cudaEventRecord(b, ctx->stream);
   ctx->pending.push_back({a, b, bytes, kind});
 }
-// Folds completed timings into the counters (call after a stream sync).
+// Folds completed timings into the counters; timings whose end event has not
+// completed yet stay pending (after a stream sync every one has completed).
 void prof_harvest(bem_ctx* ctx) {
-  for (auto& p : ctx->pending) {
+  size_t keep = 0;
+  for (size_t k = 0; k < ctx->pending.size(); ++k) {
+    auto& p = ctx->pending[k];
+    if (cudaEventQuery(p.b) == cudaErrorNotReady) {
+      ctx->pending[keep++] = p;
+      continue;
+    }
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       if (p.kind == 0) {
@@ -275,7 +282,8 @@ void prof_harvest(bem_ctx* ctx) {
     ctx->event_pool.push_back(p.a);
     ctx->event_pool.push_back(p.b);
   }
-  ctx->pending.clear();
+  ctx->pending.resize(keep);
+  cudaGetLastError();  // a not-ready query leaves no sticky error; clear the last-error slot
 }
 
 // Algorithmic bytes of one H-matrix product: every stored operator entry in
@@ -335,6 +343,8 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->host_red) cudaFreeHost(ctx->host_red);
+  if (ctx->host_cols) cudaFreeHost(ctx->host_cols);
+  for (cudaEvent_t e : ctx->col_events) cudaEventDestroy(e);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -749,13 +759,15 @@ int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, const bem_opts& o) 
   BEM_CUDA_TRY(ctx->aca_kstart.ensure(std::max<size_t>(1, nf)));
   BEM_CUDA_TRY(ctx->aca_done.ensure(std::max<size_t>(1, nf)));
   BEM_CUDA_TRY(ctx->aca_norm0.ensure(std::max<size_t>(1, nf)));
-  AcaState S{nullptr, nullptr, nullptr, ctx->piv_i.p, ctx->piv_j.p};
+  BEM_CUDA_TRY(ctx->aca_npiv.ensure(std::max<size_t>(1, nf)));
+  AcaState S{nullptr, nullptr, nullptr, ctx->piv_i.p, ctx->piv_j.p, ctx->aca_npiv.p};
   const bool warm = ctx->aca_reuse && ctx->aca_warm_ok && nf > 0;
   ctx->aca_last_warm = warm;
   if (warm) {
     BEM_CUDA_TRY((launch_aca_warm<R, Op>(ctx->far_d.p, (int)nf, ctx->ef.p, ctx->ed.p, ctx->bc.p, P, U, V,
-                                         ctx->rank.p, ctx->piv_i.p, ctx->piv_j.p, ctx->aca_kstart.p,
-                                         ctx->aca_norm0.p, ctx->aca_done.p, o.aca_tol, ctx->aca_tau, st)));
+                                         ctx->rank.p, ctx->aca_npiv.p, ctx->piv_i.p, ctx->piv_j.p,
+                                         ctx->aca_kstart.p, ctx->aca_norm0.p, ctx->aca_done.p, o.aca_tol,
+                                         ctx->aca_tau, st)));
     S.kstart = ctx->aca_kstart.p;
     S.norm0 = ctx->aca_norm0.p;
     S.done = ctx->aca_done.p;
@@ -958,6 +970,23 @@ template <typename Pm> const Pm* basis_pinv(bem_ctx* ctx);
 template <> const c64* basis_pinv<c64>(bem_ctx* ctx) { return ctx->prec_inv32.p; }
 template <> const c128* basis_pinv<c128>(bem_ctx* ctx) { return ctx->prec_inv.p; }
 
+// Pinned host slots for ncomplex values and nev timing-free events.
+int ensure_host_cols(bem_ctx* ctx, long long ncomplex, int nev) {
+  if ((size_t)ncomplex > ctx->host_cols_n) {
+    if (ctx->host_cols) cudaFreeHost(ctx->host_cols);
+    ctx->host_cols = nullptr;
+    ctx->host_cols_n = 0;
+    BEM_CUDA_TRY(cudaMallocHost(&ctx->host_cols, ncomplex * 2 * sizeof(double)));
+    ctx->host_cols_n = ncomplex;
+  }
+  while ((int)ctx->col_events.size() < nev) {
+    cudaEvent_t e;
+    BEM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->col_events.push_back(e);
+  }
+  return BEM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // GMRES (Sec. 5): right block-Jacobi preconditioning; each restart cycle
 // starts from the true residual r = b - A x accumulated in FP64 (x in FP64),
@@ -977,9 +1006,13 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
   BEM_CUDA_TRY(ctx->r64.ensure(N));
   BEM_CUDA_TRY(ctx->y64.ensure(N));
   BEM_CUDA_TRY(ctx->tmp64.ensure(2 * N));
-  BEM_CUDA_TRY(ctx->red.ensure(2LL * 64 * (m + 2) * 2 + 8 * (m + 4)));
+  // Hessenberg columns: one slot per Arnoldi step [h1 (m+1) | h2 (m+1) | nrm2]
+  const long long slot_len = 2LL * (m + 1) + 1;
+  BEM_CUDA_TRY(ctx->red.ensure(2LL * 64 * (m + 2) * 2 + 2 * slot_len * (m + 1) + 8));
   c128* part = reinterpret_cast<c128*>(ctx->red.p);
-  c128* hdev = part + 64LL * (m + 2);  // [h1 (m+1) | h2 (m+1) | nrm2]
+  c128* hdev = part + 64LL * (m + 2);
+  TRY(ensure_host_cols(ctx, slot_len * (m + 1), m + 1));
+  double* hcol = ctx->host_cols;
   const Pm* pinv = basis_pinv<Pm>(ctx);
   Vb* V = Vbuf.p;
   int its = 0, cycles = 0;
@@ -988,6 +1021,38 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
   const double inner_floor = mixed ? 2e-6 : 1e-13;
   std::vector<std::complex<double>> H((m + 1) * m), cs(m), sn(m), g(m + 1);
   double* hh = ctx->host_red;
+  // one Arnoldi step j: V_{j+1} and column j of H (copied to host slot j, event j)
+  auto enqueue = [&](int j) -> int {
+    Vb* vj = V + (long long)j * N;
+    c128* hd = hdev + j * slot_len;
+    launch_precond<Pm, Vb, Vb>(pinv, vj, zbuf.p, ctx->ne, st);
+    cudaEvent_t ev = prof_begin(ctx);
+    if (mixed)
+      launch_hmatvec<c64, c64, c64, float>(ctx, ctx->near32.p, ctx->u32.p, ctx->v32.p,
+                                           reinterpret_cast<cplx<float>*>(ctx->t32.p),
+                                           reinterpret_cast<const c64*>(zbuf.p), reinterpret_cast<c64*>(wbuf.p), 1,
+                                           st);
+    else
+      launch_hmatvec<c128, c128, c128, double>(ctx, ctx->near64.p, ctx->u64.p, ctx->v64.p,
+                                               reinterpret_cast<cplx<double>*>(ctx->t64.p),
+                                               reinterpret_cast<const c128*>(zbuf.p),
+                                               reinterpret_cast<c128*>(wbuf.p), 1, st);
+    CK("arnoldi matvec");
+    prof_end(ctx, ev, 0, hmv_bytes(ctx, sizeof(Vb), sizeof(Vb), sizeof(Vb), 1, ctx->used_lowrank));
+    for (int pass = 0; pass < 2; ++pass) {
+      int nb = launch_dots<Vb, Vb>(V, N, j + 1, wbuf.p, N, part, st);
+      launch_dots_final(part, nb, j + 1, hd + pass * (m + 1), st);
+      launch_update<Vb, Vb>(V, N, j + 1, hd + pass * (m + 1), wbuf.p, N, st);
+    }
+    int nb = launch_dots<Vb, Vb>(wbuf.p, N, 1, wbuf.p, N, part, st);
+    launch_dots_final(part, nb, 1, hd + 2 * (m + 1), st);
+    launch_scale<Vb, Vb>(wbuf.p, V + (long long)(j + 1) * N, N, reinterpret_cast<const double*>(hd + 2 * (m + 1)),
+                         st);
+    CK("arnoldi");
+    BEM_CUDA_TRY(cudaMemcpyAsync(hcol + 2 * j * slot_len, hd, slot_len * sizeof(c128), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA_TRY(cudaEventRecord(ctx->col_events[j], st));
+    return BEM_OK;
+  };
   while (true) {
     // true residual, FP64 sums (FP32 products when the tolerance allows)
     if (mixed && o.tol >= 1e-6) TRY(apply_fast(ctx, x, ctx->y64.p, 1));
@@ -1014,38 +1079,27 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
     g[0] = rnorm;
     double target = std::max(0.5 * o.tol * bnorm, inner_floor * rnorm);
     int jdone = 0;
+    // Arnoldi steps are enqueued one ahead of the host's Givens rotations
+    // (the Krylov basis does not depend on them), except where the residual
+    // trend predicts convergence at the step in flight; a step enqueued past
+    // convergence is discarded.
+    TRY(enqueue(0));
+    int enq = 1;
+    double gprev = rnorm, gcur = rnorm;
     for (int j = 0; j < m; ++j) {
-      Vb* vj = V + (long long)j * N;
-      launch_precond<Pm, Vb, Vb>(pinv, vj, zbuf.p, ctx->ne, st);
-      cudaEvent_t ev = prof_begin(ctx);
-      if (mixed)
-        launch_hmatvec<c64, c64, c64, float>(ctx, ctx->near32.p, ctx->u32.p, ctx->v32.p,
-                                             reinterpret_cast<cplx<float>*>(ctx->t32.p),
-                                             reinterpret_cast<const c64*>(zbuf.p), reinterpret_cast<c64*>(wbuf.p), 1,
-                                             st);
-      else
-        launch_hmatvec<c128, c128, c128, double>(ctx, ctx->near64.p, ctx->u64.p, ctx->v64.p,
-                                                 reinterpret_cast<cplx<double>*>(ctx->t64.p),
-                                                 reinterpret_cast<const c128*>(zbuf.p),
-                                                 reinterpret_cast<c128*>(wbuf.p), 1, st);
-      CK("arnoldi matvec");
-      prof_end(ctx, ev, 0, hmv_bytes(ctx, sizeof(Vb), sizeof(Vb), sizeof(Vb), 1, ctx->used_lowrank));
-      for (int pass = 0; pass < 2; ++pass) {
-        int nb = launch_dots<Vb, Vb>(V, N, j + 1, wbuf.p, N, part, st);
-        launch_dots_final(part, nb, j + 1, hdev + pass * (m + 1), st);
-        launch_update<Vb, Vb>(V, N, j + 1, hdev + pass * (m + 1), wbuf.p, N, st);
+      if (enq == j + 1 && j + 1 < m && its + 1 < o.max_iters) {
+        double rho = (j >= 1 && gprev > 0) ? gcur / gprev : 1.0;
+        if (gcur * rho > target) {
+          TRY(enqueue(j + 1));
+          ++enq;
+        }
       }
-      int nb = launch_dots<Vb, Vb>(wbuf.p, N, 1, wbuf.p, N, part, st);
-      launch_dots_final(part, nb, 1, hdev + 2 * (m + 1), st);
-      launch_scale<Vb, Vb>(wbuf.p, V + (long long)(j + 1) * N, N, reinterpret_cast<const double*>(hdev + 2 * (m + 1)),
-                           st);
-      CK("arnoldi");
-      BEM_CUDA_TRY(cudaMemcpyAsync(hh, hdev, (2 * (m + 1) + 1) * sizeof(c128), cudaMemcpyDeviceToHost, st));
-      BEM_CUDA_TRY(cudaStreamSynchronize(st));
+      BEM_CUDA_TRY(cudaEventSynchronize(ctx->col_events[j]));
       prof_harvest(ctx);
+      const double* hj = hcol + 2 * j * slot_len;
       for (int i = 0; i <= j; ++i)
-        H[i * m + j] = std::complex<double>(hh[2 * i] + hh[2 * (m + 1 + i)], hh[2 * i + 1] + hh[2 * (m + 1 + i) + 1]);
-      double hn = std::sqrt(std::max(0.0, hh[4 * (m + 1)]));
+        H[i * m + j] = std::complex<double>(hj[2 * i] + hj[2 * (m + 1 + i)], hj[2 * i + 1] + hj[2 * (m + 1 + i) + 1]);
+      double hn = std::sqrt(std::max(0.0, hj[4 * (m + 1)]));
       H[(j + 1) * m + j] = hn;
       // Givens (G = [[conj c, conj s], [-s, c]])
       for (int i = 0; i < j; ++i) {
@@ -1063,7 +1117,13 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
       g[j] = std::conj(cs[j]) * g[j];
       ++its;
       jdone = j + 1;
-      if (std::abs(g[j + 1]) <= target || its >= o.max_iters || hn == 0.0) break;
+      gprev = gcur;
+      gcur = std::abs(g[j + 1]);
+      if (gcur <= target || its >= o.max_iters || hn == 0.0) break;
+      if (enq == j + 1 && j + 1 < m) {
+        TRY(enqueue(j + 1));
+        ++enq;
+      }
     }
     // y = H^{-1} g ; x += M^{-1} V y
     std::vector<std::complex<double>> y(jdone);

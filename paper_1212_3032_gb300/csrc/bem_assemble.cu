@@ -974,6 +974,7 @@ __device__ __forceinline__ void aca_col3(const ElemF* ef, const ElemD* ed, const
 constexpr int ACA_THREADS = 128;
 constexpr int ACA_WARPS = ACA_THREADS / 32;
 constexpr int ACA_RMAX = 128;
+constexpr int ACA_EXTRA = 2;  // pivots recorded past the stopping point (spares for the next frequency)
 
 template <typename T> struct AcaShared {
   T dot[2][1][ACA_WARPS];  // per-warp partial norms
@@ -1040,7 +1041,6 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
   int k = st.kstart ? min(st.kstart[bi], rmax) : 0;
   int istar = 0;
   T normS2 = k ? T(st.norm0[bi]) : T(0);
-  bool converged = false;
   if (k > 0) {
     // continue from a reused cross approximation of rank k: its pivot rows
     // are used, the next row is the largest entry of u_{k-1} outside them
@@ -1059,12 +1059,16 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
     }
     aca_argmax(bu, inext, sh);
     if (!(bu > T(0))) {
-      if (threadIdx.x == 0) rank[bi] = k;
+      if (threadIdx.x == 0) {
+        rank[bi] = k;
+        st.npiv[bi] = k;
+      }
       return;
     }
     istar = inext;
     __syncthreads();
   }
+  int kconv = -1;  // rank at which the stopping test first held
   while (k < rmax) {
     // --- residual row istar -> V[:, k]
     int ie = B.r0 + istar / 3, ia = istar % 3;
@@ -1099,7 +1103,7 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
     }
     aca_argmax(best, jstar, sh);
     if (!(best > T(0))) {
-      converged = true;  // zero residual row: the block is represented exactly
+      if (kconv < 0) kconv = k;  // zero residual row: the block is represented exactly
       break;
     }
     Op pv = Vb[(long long)k * n + jstar];
@@ -1173,10 +1177,9 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
     normS2 = sh.scal[0];
     T term = sh.scal[1];
     ++k;
-    if (term <= eps * eps * normS2) {
-      converged = true;
-      break;
-    }
+    if (kconv < 0 && term <= eps * eps * normS2) kconv = k;
+    // ACA_EXTRA steps past the stopping point record spare pivots for reuse
+    if (kconv >= 0 && k >= kconv + ACA_EXTRA) break;
     // --- next pivot row: largest entry of u_k outside the rows used so far
     T bu = T(-1);
     int inext = 0;
@@ -1191,15 +1194,16 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
     }
     aca_argmax(bu, inext, sh);
     if (!(bu > T(0))) {
-      converged = true;
+      if (kconv < 0) kconv = k;
       break;
     }
     istar = inext;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    rank[bi] = k;
-    if (!converged) atomicAdd(fails, 1);
+    rank[bi] = kconv >= 0 ? kconv : k;
+    st.npiv[bi] = k;
+    if (kconv < 0) atomicAdd(fails, 1);
   }
 }
 
@@ -1250,7 +1254,6 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
   int k = st.kstart ? min(st.kstart[bi], rmax) : 0;
   int istar = 0;
   T normS2 = k ? T(st.norm0[bi]) : T(0);
-  bool converged = false;
   if (k > 0) {
     // continue from a reused cross approximation of rank k (see k_aca)
     for (int l = lane; l < k; l += 32) rows_used[l] = piv_i[l];
@@ -1268,12 +1271,16 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
     }
     warp_argmax(bu, inext);
     if (!(bu > T(0))) {
-      if (lane == 0) rank[bi] = k;
+      if (lane == 0) {
+        rank[bi] = k;
+        st.npiv[bi] = k;
+      }
       return;
     }
     istar = inext;
     __syncwarp();
   }
+  int kconv = -1;
   while (k < rmax) {
     int ie = B.r0 + istar / 3, ia = istar % 3;
     for (int el = lane; el < B.nc; el += 32) {
@@ -1307,7 +1314,7 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
     }
     warp_argmax(best, jstar);
     if (!(best > T(0))) {
-      converged = true;
+      if (kconv < 0) kconv = k;
       break;
     }
     Op pv = Vb[(long long)k * n + jstar];
@@ -1360,10 +1367,8 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
     nv2 = wsumT(nv2);
     normS2 += nu2 * nv2;
     ++k;
-    if (nu2 * nv2 <= eps * eps * normS2) {
-      converged = true;
-      break;
-    }
+    if (kconv < 0 && nu2 * nv2 <= eps * eps * normS2) kconv = k;
+    if (kconv >= 0 && k >= kconv + ACA_EXTRA) break;
     T bu = T(-1);
     int inext = 0;
     for (int i = lane; i < m; i += 32) {
@@ -1377,15 +1382,16 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
     }
     warp_argmax(bu, inext);
     if (!(bu > T(0))) {
-      converged = true;
+      if (kconv < 0) kconv = k;
       break;
     }
     istar = inext;
     __syncwarp();
   }
   if (lane == 0) {
-    rank[bi] = k;
-    if (!converged) atomicAdd(fails, 1);
+    rank[bi] = kconv >= 0 ? kconv : k;
+    st.npiv[bi] = k;
+    if (kconv < 0) atomicAdd(fails, 1);
   }
 }
 
@@ -1409,20 +1415,20 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
 // ---------------------------------------------------------------------------
 constexpr int WARM_THREADS = 256;
 
-// Pivot rows into V[:, l] and pivot columns into U[:, l], l < rank of the
-// previous frequency.
+// Pivot rows into V[:, l] and pivot columns into U[:, l], l < the pivot count
+// of the previous frequency (its rank plus spares).
 template <typename R, typename Op>
 __global__ void __launch_bounds__(WARM_THREADS) k_aca_warm_eval(const FarBlk* __restrict__ blks,
                                                                 const ElemF* __restrict__ ef,
                                                                 const ElemD* __restrict__ ed,
                                                                 const signed char* __restrict__ bc, KParams<R> P,
                                                                 Op* __restrict__ Ustore, Op* __restrict__ Vstore,
-                                                                const int* __restrict__ rank,
+                                                                const int* __restrict__ npiv,
                                                                 const int* __restrict__ piv_i,
                                                                 const int* __restrict__ piv_j) {
   using T = decltype(Op{}.re);
   const int bi = blockIdx.x;
-  const int r = rank[bi];
+  const int r = npiv[bi];
   if (r <= 0 || r > WARM_RMAX) return;
   const FarBlk B = blks[bi];
   const int m = 3 * B.nr, n = 3 * B.nc;
@@ -1452,8 +1458,7 @@ __global__ void __launch_bounds__(WARM_THREADS) k_aca_warm_eval(const FarBlk* __
   }
 }
 
-constexpr int WARM_SOLVE_THREADS = 128;
-constexpr int WARM_CH = 8;  // rows of a triangular solve held in registers at a time
+constexpr int WARM_CW = 2;  // columns (rows) of the right-hand sides per thread
 
 template <typename T> __device__ __forceinline__ void smem_max(T* a, T v);
 template <> __device__ __forceinline__ void smem_max<float>(float* a, float v) {
@@ -1469,26 +1474,144 @@ template <typename T> __device__ __forceinline__ T wmaxT(T v) {
   return v;
 }
 
+// In-place triangular solve of the rows [0, nrow) of X (row l at X + l * ldx,
+// columns [0, ncol)) against the r x r matrix in shared memory Ps:
+//   LOWER: X <- L^{-1} X, L unit lower (Ps[l r + q], q < l), one column of X
+//          per thread lane of work;
+//   else:  X <- X Uh^{-1} with X stored transposed (column l at X + l * ldx,
+//          rows [0, ncol)), Uh upper (Ps[p r + l], p <= l).
+// Per row l: max over the columns of |x_l|^2 into rowmax[l] (if given) and the
+// sum into sum_w[l * NW + warp] (fixed order within a warp). A thread holds a
+// CH x WARM_CW tile in registers; earlier rows are re-read from X.
+template <typename Op, int NT, int CH, bool LOWER>
+__device__ __forceinline__ void warm_trsm(Op* X, long long ldx, int ncol, int nrow, const cplx<decltype(Op{}.re)>* Ps,
+                                          int r, decltype(Op{}.re)* rowmax, decltype(Op{}.re)* sum_w) {
+  using T = decltype(Op{}.re);
+  using C = cplx<T>;
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int j0 = 0; j0 < ncol; j0 += NT * WARM_CW) {
+    if (j0 + wid * 32 >= ncol) continue;  // warp-uniform: this warp has no column in this pass
+    int jc[WARM_CW];
+    bool act[WARM_CW];
+#pragma unroll
+    for (int c = 0; c < WARM_CW; ++c) {
+      jc[c] = j0 + tid + c * NT;
+      act[c] = jc[c] < ncol;
+    }
+    const bool any2 = j0 + NT + wid * 32 < ncol;  // warp-uniform: second column set in use
+    for (int c0 = 0; c0 < nrow; c0 += CH) {
+      const int nv = min(CH, nrow - c0);
+      // row (LOWER) or column (upper) of the factor used for chunk row t,
+      // clamped into the r x r block: rows t >= nv are computed but not kept
+      int ft[CH];
+#pragma unroll
+      for (int t = 0; t < CH; ++t) ft[t] = min(c0 + t, r - 1);
+      C acc[CH][WARM_CW];
+#pragma unroll
+      for (int t = 0; t < CH; ++t)
+#pragma unroll
+        for (int c = 0; c < WARM_CW; ++c) {
+          Op v = (act[c] && t < nv) ? X[(long long)(c0 + t) * ldx + jc[c]] : Op{};
+          acc[t][c] = mk<T>(v.re, v.im);
+        }
+      if (any2) {
+#pragma unroll 2
+        for (int q = 0; q < c0; ++q) {
+          C x[WARM_CW];
+#pragma unroll
+          for (int c = 0; c < WARM_CW; ++c) {
+            Op xv = act[c] ? X[(long long)q * ldx + jc[c]] : Op{};
+            x[c] = mk<T>(xv.re, xv.im);
+          }
+#pragma unroll
+          for (int t = 0; t < CH; ++t) {
+            const C f = LOWER ? Ps[ft[t] * r + q] : Ps[q * r + ft[t]];
+#pragma unroll
+            for (int c = 0; c < WARM_CW; ++c) acc[t][c] = acc[t][c] - f * x[c];
+          }
+        }
+      } else {
+#pragma unroll 2
+        for (int q = 0; q < c0; ++q) {
+          Op xv = act[0] ? X[(long long)q * ldx + jc[0]] : Op{};
+          const C x0 = mk<T>(xv.re, xv.im);
+#pragma unroll
+          for (int t = 0; t < CH; ++t) {
+            const C f = LOWER ? Ps[ft[t] * r + q] : Ps[q * r + ft[t]];
+            acc[t][0] = acc[t][0] - f * x0;
+          }
+        }
+      }
+      // rows t >= nv are not stored; their factor reads are skipped below
+#pragma unroll
+      for (int t = 0; t < CH; ++t) {
+        const bool rv = t < nv;
+#pragma unroll
+        for (int u = 0; u < t; ++u) {
+          const C f = rv ? (LOWER ? Ps[(c0 + t) * r + c0 + u] : Ps[(c0 + u) * r + c0 + t]) : mk<T>(0, 0);
+#pragma unroll
+          for (int c = 0; c < WARM_CW; ++c) acc[t][c] = acc[t][c] - f * acc[u][c];
+        }
+        if (!LOWER) {
+          const C id = rv ? inv(Ps[(c0 + t) * r + c0 + t]) : mk<T>(0, 0);
+#pragma unroll
+          for (int c = 0; c < WARM_CW; ++c) acc[t][c] = acc[t][c] * id;
+        }
+      }
+      // stores and per-row reductions, CH rows at a time
+      T a2[CH], mx[CH];
+#pragma unroll
+      for (int t = 0; t < CH; ++t) {
+        a2[t] = 0;
+        mx[t] = 0;
+#pragma unroll
+        for (int c = 0; c < WARM_CW; ++c)
+          if (act[c] && t < nv) {
+            X[(long long)(c0 + t) * ldx + jc[c]] = to_op<Op>(acc[t][c]);
+            T e = abs2(acc[t][c]);
+            a2[t] += e;
+            mx[t] = max(mx[t], e);
+          }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int t = 0; t < CH; ++t) {
+          a2[t] += __shfl_xor_sync(0xffffffffu, a2[t], o);
+          if (rowmax) mx[t] = max(mx[t], __shfl_xor_sync(0xffffffffu, mx[t], o));
+        }
+      if (lane < CH && lane < nv) {
+        T sa = a2[0], sx = mx[0];
+#pragma unroll
+        for (int t = 1; t < CH; ++t)
+          if (lane == t) {
+            sa = a2[t];
+            sx = mx[t];
+          }
+        if (rowmax) smem_max(&rowmax[c0 + lane], sx);
+        sum_w[(c0 + lane) * NW + wid] += sa;
+      }
+    }
+  }
+}
+
 // Per block: LU of P, V^T = L^{-1} R and U = C Uh^{-1} in place, the pivot
 // test, and the ACA stopping test over the reused steps. Writes the state the
 // ACA kernels continue from. One launch per rank class: this one handles the
-// blocks with RLO < r <= RCAP, its shared memory sized for RCAP. Blocks with
-// nothing to reuse (r <= 0) are written as cold starts by the launch with
-// RLO = 0, blocks above the last class's RCAP by the LAST launch.
-template <typename Op, int RLO, int RCAP, bool LAST>
-__global__ void __launch_bounds__(WARM_SOLVE_THREADS) k_aca_warm_solve(const FarBlk* __restrict__ blks,
-                                                                       Op* __restrict__ Ustore,
-                                                                       Op* __restrict__ Vstore,
-                                                                       int* __restrict__ rank,
-                                                                       const int* __restrict__ piv_i,
-                                                                       const int* __restrict__ piv_j,
-                                                                       int* __restrict__ kstart,
-                                                                       double* __restrict__ norm0,
-                                                                       int* __restrict__ done, double eps_d,
-                                                                       double tau_d) {
+// blocks with RLO < r <= RCAP with NT threads, its shared memory sized for
+// RCAP. Blocks with nothing to reuse (r <= 0) are written as cold starts by
+// the launch with RLO = 0, blocks above the last class's RCAP by the LAST one.
+template <typename Op, int RLO, int RCAP, bool LAST, int NT, int CH>
+__global__ void __launch_bounds__(NT) k_aca_warm_solve(const FarBlk* __restrict__ blks, Op* __restrict__ Ustore,
+                                                       Op* __restrict__ Vstore, int* __restrict__ rank,
+                                                       int* __restrict__ npiv, const int* __restrict__ piv_i,
+                                                       const int* __restrict__ piv_j, int* __restrict__ kstart,
+                                                       double* __restrict__ norm0, int* __restrict__ done,
+                                                       double eps_d, double tau_d) {
   using T = decltype(Op{}.re);
   using C = cplx<T>;
-  constexpr int NW = WARM_SOLVE_THREADS / 32;
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char warm_smem[];
   C* Ps = reinterpret_cast<C*>(warm_smem);                 // r x r, row-major
   T* rowmax = reinterpret_cast<T*>(Ps + RCAP * RCAP);
@@ -1496,8 +1619,8 @@ __global__ void __launch_bounds__(WARM_SOLVE_THREADS) k_aca_warm_solve(const Far
   T* nu2w = nv2w + RCAP * NW;
   __shared__ int sh_rp, sh_ls;
   const int bi = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int r = rank[bi];
+  const int tid = threadIdx.x;
+  const int r = npiv[bi];
   if (r <= RLO || r > RCAP) {
     if (((RLO == 0 && r <= 0) || (LAST && r > RCAP)) && tid == 0) {
       kstart[bi] = 0;
@@ -1512,12 +1635,12 @@ __global__ void __launch_bounds__(WARM_SOLVE_THREADS) k_aca_warm_solve(const Far
   Op* Vb = Vstore + B.voff;
   const int* pi = piv_i + B.toff;
   const int* pj = piv_j + B.toff;
-  for (int idx = tid; idx < r * r; idx += blockDim.x) {
+  for (int idx = tid; idx < r * r; idx += NT) {
     int l = idx / r, q = idx - l * r;
     Op v = Vb[(long long)l * n + pj[q]];
     Ps[idx] = mk<T>(v.re, v.im);
   }
-  for (int l = tid; l < RCAP; l += blockDim.x) {
+  for (int l = tid; l < RCAP; l += NT) {
     rowmax[l] = T(0);
     for (int w = 0; w < NW; ++w) nv2w[l * NW + w] = nu2w[l * NW + w] = T(0);
   }
@@ -1531,52 +1654,19 @@ __global__ void __launch_bounds__(WARM_SOLVE_THREADS) k_aca_warm_solve(const Far
       break;
     }
     C id = inv(d);
-    for (int p = l + 1 + tid; p < r; p += blockDim.x) Ps[p * r + l] = Ps[p * r + l] * id;
+    for (int p = l + 1 + tid; p < r; p += NT) Ps[p * r + l] = Ps[p * r + l] * id;
     __syncthreads();
-    const int w = r - l - 1;
-    for (int idx = tid; idx < w * w; idx += blockDim.x) {
-      int p = l + 1 + idx / w, q = l + 1 + idx % w;
-      Ps[p * r + q] = Ps[p * r + q] - Ps[p * r + l] * Ps[l * r + q];
+    // trailing update: warps over rows, lanes over columns
+    for (int p = l + 1 + (tid >> 5); p < r; p += NW) {
+      const C lp = Ps[p * r + l];
+      for (int q = l + 1 + (tid & 31); q < r; q += 32) Ps[p * r + q] = Ps[p * r + q] - lp * Ps[l * r + q];
     }
     __syncthreads();
   }
   __syncthreads();
   const int rp = sh_rp;
-  // V^T <- L^{-1} R column by column; residual-row maxima and norms per row
-  for (int j0 = 0; j0 < n; j0 += blockDim.x) {
-    const int j = j0 + tid;
-    const bool act = j < n;
-    for (int c0 = 0; c0 < rp; c0 += WARM_CH) {
-      C acc[WARM_CH];
-#pragma unroll
-      for (int t = 0; t < WARM_CH; ++t) {
-        Op v = (act && c0 + t < rp) ? Vb[(long long)(c0 + t) * n + j] : Op{};
-        acc[t] = mk<T>(v.re, v.im);
-      }
-#pragma unroll 4
-      for (int q = 0; q < c0; ++q) {
-        Op xv = act ? Vb[(long long)q * n + j] : Op{};
-        C x = mk<T>(xv.re, xv.im);
-#pragma unroll
-        for (int t = 0; t < WARM_CH; ++t)
-          if (c0 + t < rp) acc[t] = acc[t] - Ps[(c0 + t) * r + q] * x;
-      }
-#pragma unroll
-      for (int t = 0; t < WARM_CH; ++t) {
-        if (c0 + t >= rp) break;
-#pragma unroll
-        for (int u = 0; u < t; ++u) acc[t] = acc[t] - Ps[(c0 + t) * r + c0 + u] * acc[u];
-        if (act) Vb[(long long)(c0 + t) * n + j] = to_op<Op>(acc[t]);
-        T a2 = act ? abs2(acc[t]) : T(0);
-        T mx = wmaxT(a2);
-        T sm = wsumT(a2);
-        if (lane == 0) {
-          smem_max(&rowmax[c0 + t], mx);
-          nv2w[(c0 + t) * NW + wid] += sm;
-        }
-      }
-    }
-  }
+  // V^T <- L^{-1} R (rows of R are the columns of V)
+  warm_trsm<Op, NT, CH, true>(Vb, n, n, rp, Ps, r, rowmax, nv2w);
   __syncthreads();
   if (tid == 0) {
     const T tau2 = T(tau_d * tau_d);
@@ -1590,40 +1680,11 @@ __global__ void __launch_bounds__(WARM_SOLVE_THREADS) k_aca_warm_solve(const Far
   }
   __syncthreads();
   const int ls = sh_ls;
-  // U <- C Uh^{-1} row by row
-  for (int i0 = 0; i0 < m; i0 += blockDim.x) {
-    const int i = i0 + tid;
-    const bool act = i < m;
-    for (int c0 = 0; c0 < ls; c0 += WARM_CH) {
-      C acc[WARM_CH];
-#pragma unroll
-      for (int t = 0; t < WARM_CH; ++t) {
-        Op v = (act && c0 + t < ls) ? Ub[(long long)(c0 + t) * m + i] : Op{};
-        acc[t] = mk<T>(v.re, v.im);
-      }
-#pragma unroll 4
-      for (int p = 0; p < c0; ++p) {
-        Op xv = act ? Ub[(long long)p * m + i] : Op{};
-        C x = mk<T>(xv.re, xv.im);
-#pragma unroll
-        for (int t = 0; t < WARM_CH; ++t)
-          if (c0 + t < ls) acc[t] = acc[t] - x * Ps[p * r + c0 + t];
-      }
-#pragma unroll
-      for (int t = 0; t < WARM_CH; ++t) {
-        if (c0 + t >= ls) break;
-#pragma unroll
-        for (int u = 0; u < t; ++u) acc[t] = acc[t] - acc[u] * Ps[(c0 + u) * r + c0 + t];
-        acc[t] = acc[t] * inv(Ps[(c0 + t) * r + c0 + t]);
-        if (act) Ub[(long long)(c0 + t) * m + i] = to_op<Op>(acc[t]);
-        T sm = wsumT(act ? abs2(acc[t]) : T(0));
-        if (lane == 0) nu2w[(c0 + t) * NW + wid] += sm;
-      }
-    }
-  }
+  // U <- C Uh^{-1} (columns of C stored as the columns of U)
+  warm_trsm<Op, NT, CH, false>(Ub, m, m, ls, Ps, r, nullptr, nu2w);
   __syncthreads();
   // earlier pivot rows are represented exactly: zero them as ACA does
-  for (int idx = tid; idx < ls * ls; idx += blockDim.x) {
+  for (int idx = tid; idx < ls * ls; idx += NT) {
     int q = idx / ls, p = idx % ls;
     if (p < q) Ub[(long long)q * m + pi[p]] = Op{};
   }
@@ -1649,7 +1710,10 @@ __global__ void __launch_bounds__(WARM_SOLVE_THREADS) k_aca_warm_solve(const Far
     kstart[bi] = kc;
     norm0[bi] = double(S);
     done[bi] = conv;
-    if (conv) rank[bi] = kc;
+    if (conv) {
+      rank[bi] = kc;
+      npiv[bi] = ls;  // the validated pivots past the rank stay as spares
+    }
   }
 }
 
@@ -1713,46 +1777,53 @@ void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int
                 int* fails, double eps, const AcaState& state, cudaStream_t st) {
   if (count_if(nlarge))
     k_aca<R, Op><<<nlarge, ACA_THREADS, 0, st>>>(large_list, blks, ef, ed, bc, P, U, V, rank, fails, eps, state);
-  if (count_if(nsmall))
+  if (!nsmall) return;
+  count_if(true);
+  if (state.done) {
+    // continuation after pivot reuse: few blocks, a few steps each; one CTA
+    // per block shortens each step (blocks already settled exit at once)
+    k_aca<R, Op><<<nsmall, ACA_THREADS, 0, st>>>(small_list, blks, ef, ed, bc, P, U, V, rank, fails, eps, state);
+  } else {
     k_aca_warp<R, Op><<<(nsmall + ACAW_WARPS - 1) / ACAW_WARPS, 32 * ACAW_WARPS, 0, st>>>(
         small_list, nsmall, blks, ef, ed, bc, P, U, V, rank, fails, eps, state);
+  }
 }
 
-template <typename Op> size_t warm_solve_smem(int rcap) {
+template <typename Op> size_t warm_solve_smem(int rcap, int nt) {
   using T = decltype(Op{}.re);
-  return sizeof(cplx<T>) * rcap * rcap + sizeof(T) * rcap * (1 + 2 * (WARM_SOLVE_THREADS / 32));
+  return sizeof(cplx<T>) * rcap * rcap + sizeof(T) * rcap * (1 + 2 * (nt / 32));
 }
 
-template <typename Op, int RLO, int RCAP, bool LAST>
-cudaError_t launch_warm_solve(const FarBlk* blks, int nfar, Op* U, Op* V, int* rank, const int* piv_i,
+template <typename Op, int RLO, int RCAP, bool LAST, int NT, int CH>
+cudaError_t launch_warm_solve(const FarBlk* blks, int nfar, Op* U, Op* V, int* rank, int* npiv, const int* piv_i,
                               const int* piv_j, int* kstart, double* norm0, int* done, double eps, double tau,
                               cudaStream_t st) {
-  const size_t sm = warm_solve_smem<Op>(RCAP);
+  const size_t sm = warm_solve_smem<Op>(RCAP, NT);
   static_assert(sizeof(Op) * RCAP * RCAP <= 200 * 1024, "pivot block must fit in shared memory");
-  cudaError_t e = cudaFuncSetAttribute(k_aca_warm_solve<Op, RLO, RCAP, LAST>,
+  cudaError_t e = cudaFuncSetAttribute(k_aca_warm_solve<Op, RLO, RCAP, LAST, NT, CH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   count_if(true);
-  k_aca_warm_solve<Op, RLO, RCAP, LAST><<<nfar, WARM_SOLVE_THREADS, sm, st>>>(blks, U, V, rank, piv_i, piv_j,
-                                                                              kstart, norm0, done, eps, tau);
+  k_aca_warm_solve<Op, RLO, RCAP, LAST, NT, CH><<<nfar, NT, sm, st>>>(blks, U, V, rank, npiv, piv_i, piv_j,
+                                                                      kstart, norm0, done, eps, tau);
   return cudaGetLastError();
 }
 
 template <typename R, typename Op>
 cudaError_t launch_aca_warm(const FarBlk* blks, int nfar, const ElemF* ef, const ElemD* ed, const signed char* bc,
-                            const KParams<R>& P, Op* U, Op* V, int* rank, int* piv_i, int* piv_j, int* kstart,
-                            double* norm0, int* done, double eps, double tau, cudaStream_t st) {
+                            const KParams<R>& P, Op* U, Op* V, int* rank, int* npiv, int* piv_i, int* piv_j,
+                            int* kstart, double* norm0, int* done, double eps, double tau, cudaStream_t st) {
   if (!nfar) return cudaSuccess;
   count_if(true);
-  k_aca_warm_eval<R, Op><<<nfar, WARM_THREADS, 0, st>>>(blks, ef, ed, bc, P, U, V, rank, piv_i, piv_j);
+  k_aca_warm_eval<R, Op><<<nfar, WARM_THREADS, 0, st>>>(blks, ef, ed, bc, P, U, V, npiv, piv_i, piv_j);
   // rank classes (0, 64] and (64, 128]; complex128 pivot blocks above rank
   // 112 do not fit in shared memory and restart ACA
   constexpr int RTOP = sizeof(Op) == 8 ? WARM_RMAX : 112;
-  cudaError_t e = launch_warm_solve<Op, 0, WARM_SPLIT, false>(blks, nfar, U, V, rank, piv_i, piv_j, kstart, norm0,
-                                                              done, eps, tau, st);
+  cudaError_t e = launch_warm_solve<Op, 0, WARM_SPLIT, false, 128, 8>(blks, nfar, U, V, rank, npiv, piv_i, piv_j,
+                                                                      kstart, norm0, done, eps, tau, st);
   if (e != cudaSuccess) return e;
-  return launch_warm_solve<Op, WARM_SPLIT, RTOP, true>(blks, nfar, U, V, rank, piv_i, piv_j, kstart, norm0, done,
-                                                       eps, tau, st);
+  return launch_warm_solve<Op, WARM_SPLIT, RTOP, true, 256, 16>(blks, nfar, U, V, rank, npiv, piv_i, piv_j, kstart,
+                                                                norm0, done, eps, tau, st);
 }
 
 template void launch_near_regular<float, c64>(const NearBlk*, int, int, const unsigned*, const long long*,
@@ -1782,10 +1853,11 @@ template void launch_aca<double, c128>(const FarBlk*, const int*, int, const int
                                        const ElemD*, const signed char*, const KParams<double>&, c128*, c128*, int*,
                                        int*, double, const AcaState&, cudaStream_t);
 template cudaError_t launch_aca_warm<float, c64>(const FarBlk*, int, const ElemF*, const ElemD*, const signed char*,
-                                                 const KParams<float>&, c64*, c64*, int*, int*, int*, int*, double*,
-                                                 int*, double, double, cudaStream_t);
+                                                 const KParams<float>&, c64*, c64*, int*, int*, int*, int*, int*,
+                                                 double*, int*, double, double, cudaStream_t);
 template cudaError_t launch_aca_warm<double, c128>(const FarBlk*, int, const ElemF*, const ElemD*,
                                                    const signed char*, const KParams<double>&, c128*, c128*, int*,
-                                                   int*, int*, int*, double*, int*, double, double, cudaStream_t);
+                                                   int*, int*, int*, int*, double*, int*, double, double,
+                                                   cudaStream_t);
 
 }  // namespace bem

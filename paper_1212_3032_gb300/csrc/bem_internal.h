@@ -90,6 +90,7 @@ struct AcaState {
   const int* done;      // per far block: 1 = converged already (skip)
   int* piv_i;           // pivot row of each step (block-local scalar index)
   int* piv_j;           // pivot column of each step
+  int* npiv;            // per far block: pivots recorded (rank plus spares)
 };
 
 template <typename T> struct DevBuf {
@@ -207,7 +208,7 @@ struct bem_ctx {
   bool aca_last_warm = false;          // the last assembly started from reused pivots
   double aca_tau = 0.1;                // pivot test of the reused steps
   bem::DevBuf<int> piv_i, piv_j;       // t_entries each
-  bem::DevBuf<int> aca_kstart, aca_done;
+  bem::DevBuf<int> aca_kstart, aca_done, aca_npiv;
   bem::DevBuf<double> aca_norm0;
   long long prof_aca_blocks = 0;       // far blocks assembled (profiling)
   long long prof_aca_continued = 0;    // of which took ACA steps (not settled by reuse alone)
@@ -223,6 +224,9 @@ struct bem_ctx {
   bem::DevBuf<double> red;             // reduction scratch
   bem::DevBuf<double> pattern;         // tree order ne x 3
   double* host_red = nullptr;          // pinned
+  double* host_cols = nullptr;         // pinned Hessenberg column slots of GMRES
+  size_t host_cols_n = 0;              // complex values it holds
+  std::vector<cudaEvent_t> col_events; // one per Arnoldi step of a cycle
 
   // event timing (bem_set_profiling)
   bool profiling = false;

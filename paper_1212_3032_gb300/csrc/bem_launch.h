@@ -44,12 +44,13 @@ void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int
                 int* fails, double eps, const AcaState& state, cudaStream_t st);
 // Reuse of the previous assembly's pivots: evaluates the pivot rows and
 // columns at the new s, forms the cross approximation through them and
-// writes the start state (kstart, norm0, done) for launch_aca. rank holds the
-// previous ranks on entry and the new rank of every converged block on exit.
+// writes the start state (kstart, norm0, done) for launch_aca. npiv holds the
+// previous pivot counts (rank plus spares); rank and npiv of every block
+// settled by the reuse are updated, the others by launch_aca.
 template <typename R, typename Op>
 cudaError_t launch_aca_warm(const FarBlk* blks, int nfar, const ElemF* ef, const ElemD* ed, const signed char* bc,
-                            const KParams<R>& P, Op* U, Op* V, int* rank, int* piv_i, int* piv_j, int* kstart,
-                            double* norm0, int* done, double eps, double tau, cudaStream_t st);
+                            const KParams<R>& P, Op* U, Op* V, int* rank, int* npiv, int* piv_i, int* piv_j,
+                            int* kstart, double* norm0, int* done, double eps, double tau, cudaStream_t st);
 
 // ---- solver (bem_solve.cu) ----
 // H-matrix product y = A x for nrhs right-hand sides (x, y: nrhs vectors of
