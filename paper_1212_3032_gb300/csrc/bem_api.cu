@@ -569,16 +569,21 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   tptr[L] = (int)tk.size();
   ctx->ntasks = (int)tk.size();
   {
-    std::vector<int> nt, ft;
-    for (int i = 0; i < (int)tk.size(); ++i) (tk[i].kind == 0 ? nt : ft).push_back(i);
-    ctx->n_near_tasks = (int)nt.size();
-    ctx->n_far_tasks = (int)ft.size();
-    BEM_CUDA_TRY(ctx->near_tasks.alloc(std::max<size_t>(1, nt.size())));
-    BEM_CUDA_TRY(ctx->far_tasks.alloc(std::max<size_t>(1, ft.size())));
-    if (!nt.empty())
-      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->near_tasks.p, nt.data(), nt.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (!ft.empty())
-      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->far_tasks.p, ft.data(), ft.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    std::vector<int> order(tk.size());
+    std::vector<long long> tcost(tk.size(), 0);  // stored entries read by each task
+    for (int i = 0; i < (int)tk.size(); ++i) {
+      order[i] = i;
+      for (int p = tk[i].p0; p < tk[i].p1; ++p)
+        tcost[i] += (long long)3 * nr[tk[i].leaf] *
+                    (pan[p].kind == 0 ? pan[p].ncols : ctx->far_h[pan[p].xoff].rmax);
+    }
+    std::sort(order.begin(), order.end(),
+              [&](int a, int b) { return tcost[a] != tcost[b] ? tcost[a] > tcost[b] : a < b; });
+    BEM_CUDA_TRY(ctx->task_order.alloc(std::max<size_t>(1, order.size())));
+    if (!order.empty())
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->task_order.p, order.data(), order.size() * sizeof(int),
+                                   cudaMemcpyHostToDevice, st));
+    BEM_CUDA_TRY(cudaStreamSynchronize(st));  // order outlives the copy
   }
   ctx->part_rows = slot;
   BEM_CUDA_TRY(ctx->tasks.alloc(std::max<size_t>(1, tk.size())));

@@ -171,8 +171,7 @@ struct bem_ctx {
   int ntasks = 0;
   long long part_rows = 0;            // rows of the partial buffer per right-hand side
   bem::DevBuf<bem::Task> tasks;
-  int n_near_tasks = 0, n_far_tasks = 0;
-  bem::DevBuf<int> near_tasks, far_tasks;  // task indices by kind
+  bem::DevBuf<int> task_order;        // task indices by size, largest first (launch order)
   bem::DevBuf<int> task_ptr;          // CSR of tasks over leaves
   bem::DevBuf<double> part;           // partial sums (sized for 4 rhs of complex FP64)
   int max_nr = 0;                     // largest leaf (elements)

@@ -217,6 +217,19 @@ __global__ void __launch_bounds__(HMV_THREADS, 2) k_hmv_tasks(
                              red);
 }
 
+// The same task kernel over a list of task indices (the launch order).
+template <typename Op, typename X, typename Acc, int NRHS>
+__global__ void __launch_bounds__(HMV_THREADS, 2) k_hmv_tasks_list(
+    const int* __restrict__ list, const Task* __restrict__ tasks, const int* __restrict__ leaf_nr,
+    const Panel* __restrict__ panels, const FarBlk* __restrict__ far, const int* __restrict__ rank,
+    const Op* __restrict__ near, const Op* __restrict__ U, const cplx<Acc>* __restrict__ t, int tstride,
+    const X* __restrict__ x, long long N, cplx<Acc>* __restrict__ part, long long pstride) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<Acc>* red = reinterpret_cast<cplx<Acc>*>(smem_raw);
+  hmv_task<Op, X, Acc, NRHS>(tasks[list[blockIdx.x]], leaf_nr, panels, far, rank, near, U, t, tstride, x, N, part,
+                             pstride, red);
+}
+
 // phase 3: y[rows of leaf] = sum over the leaf's tasks, in task order
 template <typename Acc, typename Y, int NRHS>
 __global__ void __launch_bounds__(256) k_hmv_reduce(const int* __restrict__ leaf_r0, const int* __restrict__ leaf_nr,
@@ -252,10 +265,12 @@ static void hmv_impl(const bem_ctx* ctx, const Op* near, const Op* U, const Op* 
                                                                        ctx->t_entries);
   cplx<Acc>* part = reinterpret_cast<cplx<Acc>*>(ctx->part.p);
   size_t sm = (size_t)2 * HMV_THREADS * NRHS * sizeof(cplx<Acc>);
-  count_if(true);
-  k_hmv_tasks<Op, X, Acc, NRHS><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
-      ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t, ctx->t_entries, x, ctx->N,
-      part, ctx->part_rows);
+  // every task, largest first (CTAs are dispatched in index order: the long
+  // tasks start early and the short ones fill the tail)
+  if (count_if(ctx->ntasks))
+    k_hmv_tasks_list<Op, X, Acc, NRHS><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
+        ctx->task_order.p, ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t,
+        ctx->t_entries, x, ctx->N, part, ctx->part_rows);
   count_if(true);
   k_hmv_reduce<Acc, Y, NRHS><<<ctx->nleaves, 256, 0, st>>>(ctx->leaf_r0.p, ctx->leaf_nr.p, ctx->task_ptr.p,
                                                           ctx->tasks.p, part, ctx->part_rows, ctx->N, y);
