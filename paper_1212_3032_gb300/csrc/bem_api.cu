@@ -230,7 +230,7 @@ int dot_host(bem_ctx* ctx, const A* a, const B* b, long long n, std::complex<dou
   return BEM_OK;
 }
 
-int ensure_static(bem_ctx* ctx);
+int ensure_static(bem_ctx* ctx, bool need_fp64);
 
 bool is_mixed(const bem_ctx* ctx) { return ctx->prec == BEM_PREC_C64_MIXED; }
 
@@ -738,12 +738,17 @@ extern "C" int bem_mesh(bem_ctx* ctx, const double* xyz, int64_t nv, const int32
 // ---------------------------------------------------------------------------
 namespace {
 
-int ensure_static(bem_ctx* ctx) {
-  if (ctx->sing_static.p || ctx->nsing == 0) return BEM_OK;
-  BEM_CUDA_TRY(ctx->sing_static.alloc(18LL * ctx->nsing));
+// Static parts, at the precision the operator needs: FP32 near-singular
+// rule for the complex64 operator, FP64 for complex128 (an FP64 set serves
+// both; an FP32 set is recomputed when the FP64 operator is assembled).
+int ensure_static(bem_ctx* ctx, bool need_fp64) {
+  if (ctx->nsing == 0) return BEM_OK;
+  if (ctx->sing_static.p && (ctx->static_fp64 || !need_fp64)) return BEM_OK;
+  if (!ctx->sing_static.p) BEM_CUDA_TRY(ctx->sing_static.alloc(18LL * ctx->nsing));
   KParams<double> P = make_params<double>(ctx, 0.0, 0.0);
-  launch_static(ctx->sing.p, ctx->nsing, ctx->ed.p, P, ctx->sing_static.p, ctx->stream);
+  launch_static(ctx->sing.p, ctx->nsing, ctx->ed.p, P, ctx->sing_static.p, !need_fp64, ctx->stream);
   CK("static");
+  ctx->static_fp64 = need_fp64;
   return BEM_OK;
 }
 
@@ -799,7 +804,7 @@ int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, const bem_opts& o) 
 int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const double* pattern_tree,
                   c128 pk, c128* b) {
   cudaStream_t st = ctx->stream;
-  TRY(ensure_static(ctx));
+  TRY(ensure_static(ctx, o.precision == BEM_PREC_C128));
   ctx->prec = o.precision;
   cudaEvent_t ev = prof_begin(ctx);
   size_t nf = ctx->far_h.size();
@@ -1016,6 +1021,10 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
   BEM_CUDA_TRY(ctx->red.ensure(2LL * 64 * (m + 2) * 2 + 2 * slot_len * (m + 1) + 8));
   c128* part = reinterpret_cast<c128*>(ctx->red.p);
   c128* hdev = part + 64LL * (m + 2);
+  if (m + 1 > 512) return fail(ctx, BEM_ERR_INVALID_ARG, "restart length above 511");
+  // partial sums of the cooperative orthogonalisation step
+  BEM_CUDA_TRY(ctx->orth_part.ensure((size_t)(2 * (m + 1) + 1) * arnoldi_orth_max_blocks()));
+  c128* orth_part = ctx->orth_part.p;
   TRY(ensure_host_cols(ctx, slot_len * (m + 1), m + 1));
   double* hcol = ctx->host_cols;
   const Pm* pinv = basis_pinv<Pm>(ctx);
@@ -1044,15 +1053,7 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
                                                reinterpret_cast<c128*>(wbuf.p), 1, st);
     CK("arnoldi matvec");
     prof_end(ctx, ev, 0, hmv_bytes(ctx, sizeof(Vb), sizeof(Vb), sizeof(Vb), 1, ctx->used_lowrank));
-    for (int pass = 0; pass < 2; ++pass) {
-      int nb = launch_dots<Vb, Vb>(V, N, j + 1, wbuf.p, N, part, st);
-      launch_dots_final(part, nb, j + 1, hd + pass * (m + 1), st);
-      launch_update<Vb, Vb>(V, N, j + 1, hd + pass * (m + 1), wbuf.p, N, st);
-    }
-    int nb = launch_dots<Vb, Vb>(wbuf.p, N, 1, wbuf.p, N, part, st);
-    launch_dots_final(part, nb, 1, hd + 2 * (m + 1), st);
-    launch_scale<Vb, Vb>(wbuf.p, V + (long long)(j + 1) * N, N, reinterpret_cast<const double*>(hd + 2 * (m + 1)),
-                         st);
+    BEM_CUDA_TRY(launch_arnoldi_orth<Vb>(V, N, j, wbuf.p, N, orth_part, hd, m, st));
     CK("arnoldi");
     BEM_CUDA_TRY(cudaMemcpyAsync(hcol + 2 * j * slot_len, hd, slot_len * sizeof(c128), cudaMemcpyDeviceToHost, st));
     BEM_CUDA_TRY(cudaEventRecord(ctx->col_events[j], st));

@@ -337,6 +337,11 @@ __device__ __forceinline__ const double* vtx(const ElemD& E, int k) {
   return k == 0 ? E.p0 : (k == 1 ? E.p1 : E.p2);
 }
 
+// Static (Kelvin) parts of the singular and near-singular pairs, once per
+// mesh: the self rule in FP64; the near-singular rule (64 children x 4 x 4)
+// in RN (FP64 for the complex128 operator; FP32 for the complex64 operator,
+// with the geometry taken relative to the collocation point in FP64 first).
+template <typename RN>
 __global__ void k_static(const SingPair* __restrict__ pairs, int npairs, const ElemD* __restrict__ ed,
                          KParams<double> P, double* __restrict__ out) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -369,14 +374,17 @@ __global__ void k_static(const SingPair* __restrict__ pairs, int npairs, const E
         }
     }
   } else {
-    // 64 children (3 midpoint-subdivision levels) x collapsed 4x4
+    // 64 children (3 midpoint-subdivision levels) x collapsed 4x4; vertices
+    // relative to the collocation point
+    RN usr[9], tsr[9];
+    for (int k = 0; k < 9; ++k) usr[k] = tsr[k] = RN(0);
     for (int q = lane; q < 64 * NEAR_Q * NEAR_Q; q += 32) {
       int child = q / (NEAR_Q * NEAR_Q), pt = q % (NEAR_Q * NEAR_Q);
-      double a[3], b[3], c[3];
+      RN a[3], b[3], c[3];
       for (int k = 0; k < 3; ++k) {
-        a[k] = E.p0[k];
-        b[k] = E.p1[k];
-        c[k] = E.p2[k];
+        a[k] = RN(E.p0[k] - I.c[k]);
+        b[k] = RN(E.p1[k] - I.c[k]);
+        c[k] = RN(E.p2[k] - I.c[k]);
       }
       int digits = child;
       int dig[NEAR_LEVELS];
@@ -385,14 +393,14 @@ __global__ void k_static(const SingPair* __restrict__ pairs, int npairs, const E
         digits >>= 2;
       }
       for (int l = 0; l < NEAR_LEVELS; ++l) {
-        double mab[3], mbc[3], mca[3];
+        RN mab[3], mbc[3], mca[3];
         for (int k = 0; k < 3; ++k) {
-          mab[k] = 0.5 * (a[k] + b[k]);
-          mbc[k] = 0.5 * (b[k] + c[k]);
-          mca[k] = 0.5 * (c[k] + a[k]);
+          mab[k] = RN(0.5) * (a[k] + b[k]);
+          mbc[k] = RN(0.5) * (b[k] + c[k]);
+          mca[k] = RN(0.5) * (c[k] + a[k]);
         }
         for (int k = 0; k < 3; ++k) {
-          double na, nb, nc;
+          RN na, nb, nc;
           switch (dig[l]) {
             case 0: na = a[k]; nb = mab[k]; nc = mca[k]; break;
             case 1: na = mab[k]; nb = b[k]; nc = mbc[k]; break;
@@ -404,20 +412,24 @@ __global__ void k_static(const SingPair* __restrict__ pairs, int npairs, const E
           c[k] = nc;
         }
       }
-      double e1[3], e2[3];
+      RN e1[3], e2[3];
       for (int k = 0; k < 3; ++k) {
         e1[k] = b[k] - a[k];
         e2[k] = c[k] - a[k];
       }
-      double cr0 = e1[1] * e2[2] - e1[2] * e2[1], cr1 = e1[2] * e2[0] - e1[0] * e2[2],
-             cr2 = e1[0] * e2[1] - e1[1] * e2[0];
-      double area2 = sqrt(cr0 * cr0 + cr1 * cr1 + cr2 * cr2);
+      RN cr0 = e1[1] * e2[2] - e1[2] * e2[1], cr1 = e1[2] * e2[0] - e1[0] * e2[2],
+         cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+      RN area2 = sqrt(cr0 * cr0 + cr1 * cr1 + cr2 * cr2);
       int ia = pt / NEAR_Q, ib = pt % NEAR_Q;
-      double u = gl_x<double>(NEAR_Q, ia), v = (1.0 - u) * gl_x<double>(NEAR_Q, ib);
-      double w = area2 * gl_w<double>(NEAR_Q, ia) * gl_w<double>(NEAR_Q, ib) * (1.0 - u);
-      double rv[3];
-      for (int k = 0; k < 3; ++k) rv[k] = a[k] + u * e1[k] + v * e2[k] - I.c[k];
-      add_kelvin(us, ts, rv[0], rv[1], rv[2], E.n[0], E.n[1], E.n[2], w, P);
+      RN u = gl_x<RN>(NEAR_Q, ia), v = (RN(1) - u) * gl_x<RN>(NEAR_Q, ib);
+      RN w = area2 * gl_w<RN>(NEAR_Q, ia) * gl_w<RN>(NEAR_Q, ib) * (RN(1) - u);
+      RN rv[3];
+      for (int k = 0; k < 3; ++k) rv[k] = a[k] + u * e1[k] + v * e2[k];
+      add_kelvin<RN>(usr, tsr, rv[0], rv[1], rv[2], RN(E.n[0]), RN(E.n[1]), RN(E.n[2]), w, P);
+    }
+    for (int k = 0; k < 9; ++k) {
+      us[k] = double(usr[k]);
+      ts[k] = double(tsr[k]);
     }
   }
   for (int k = 0; k < 9; ++k) {
@@ -1737,9 +1749,11 @@ void launch_sing_fill(const NearBlk* blks, int nblk, const ElemD* ed, const int*
                       cudaStream_t st) {
   if (count_if(nblk)) k_sing_fill<<<nblk, 256, 0, st>>>(blks, ed, offs, out);
 }
-void launch_static(const SingPair* pairs, int n, const ElemD* ed, const KParams<double>& P, double* out,
+void launch_static(const SingPair* pairs, int n, const ElemD* ed, const KParams<double>& P, double* out, bool fp32,
                    cudaStream_t st) {
-  if (count_if(n)) k_static<<<(n + 3) / 4, 128, 0, st>>>(pairs, n, ed, P, out);
+  if (!count_if(n)) return;
+  if (fp32) k_static<float><<<(n + 3) / 4, 128, 0, st>>>(pairs, n, ed, P, out);
+  else k_static<double><<<(n + 3) / 4, 128, 0, st>>>(pairs, n, ed, P, out);
 }
 void launch_pair_sort(const NearBlk* blks, int nblk, const ElemF* ef, const ElemD* ed, const long long* poff,
                       unsigned* plist, int* pcount, cudaStream_t st) {

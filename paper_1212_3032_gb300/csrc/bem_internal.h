@@ -189,6 +189,7 @@ struct bem_ctx {
   int nsing = 0;
   bem::DevBuf<bem::SingPair> sing;
   bem::DevBuf<double> sing_static;    // nsing x 18 (U* 9, T* 9)
+  bool static_fp64 = false;           // sing_static from the FP64 near-singular rule
   bem::DevBuf<int> loaded;            // tree elements with nonzero prescribed pattern
   int nloaded = 0;
 
@@ -221,6 +222,7 @@ struct bem_ctx {
   bem::DevBuf<bem::c64> w32;
   bem::DevBuf<bem::c128> w64, x64, r64, b64, y64, tmp64;
   bem::DevBuf<double> red;             // reduction scratch
+  bem::DevBuf<bem::c128> orth_part;    // partial sums of the Arnoldi orthogonalisation step
   bem::DevBuf<double> pattern;         // tree order ne x 3
   double* host_red = nullptr;          // pinned
   double* host_cols = nullptr;         // pinned Hessenberg column slots of GMRES

@@ -198,26 +198,27 @@ __device__ __forceinline__ void accumulate_point_u(cplx<R>* u, R rx, R ry, R rz,
   cfmr(u[5], cr, h[2] * h[2]);
 }
 
-// Adds w * (static Kelvin U*, T*) into real accumulators (18 doubles).
-__device__ __forceinline__ void add_kelvin(double* us, double* ts, double rx, double ry, double rz,
-                                           double nx, double ny, double nz, double w,
+// Adds w * (static Kelvin U*, T*) into real accumulators (9 + 9 entries),
+// evaluated in R (FP64, or FP32 for the complex64 operator).
+template <typename R>
+__device__ __forceinline__ void add_kelvin(R* us, R* ts, R rx, R ry, R rz, R nx, R ny, R nz, R w,
                                            const KParams<double>& P) {
-  double r2 = rx * rx + ry * ry + rz * rz;
-  double r = sqrt(r2);
-  double ir = 1.0 / r;
-  double h[3] = {rx * ir, ry * ir, rz * ir};
-  double n[3] = {nx, ny, nz};
-  double rn = h[0] * nx + h[1] * ny + h[2] * nz;
-  double nu = P.nu;
-  double su = P.kel_u * ir * w;
-  double st = -P.kel_t * ir * ir * w;
-  double a34 = 3.0 - 4.0 * nu, a12 = 1.0 - 2.0 * nu;
+  R r2 = rx * rx + ry * ry + rz * rz;
+  R r = sqrt(r2);
+  R ir = R(1) / r;
+  R h[3] = {rx * ir, ry * ir, rz * ir};
+  R n[3] = {nx, ny, nz};
+  R rn = h[0] * nx + h[1] * ny + h[2] * nz;
+  R nu = R(P.nu);
+  R su = R(P.kel_u) * ir * w;
+  R st = -R(P.kel_t) * ir * ir * w;
+  R a34 = R(3) - R(4) * nu, a12 = R(1) - R(2) * nu;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      us[3 * i + j] += su * ((i == j ? a34 : 0.0) + h[i] * h[j]);
-      double v = rn * ((i == j ? a12 : 0.0) + 3.0 * h[i] * h[j]) - a12 * (h[i] * n[j] - h[j] * n[i]);
+      us[3 * i + j] += su * ((i == j ? a34 : R(0)) + h[i] * h[j]);
+      R v = rn * ((i == j ? a12 : R(0)) + R(3) * h[i] * h[j]) - a12 * (h[i] * n[j] - h[j] * n[i]);
       ts[3 * i + j] += st * v;
     }
   }

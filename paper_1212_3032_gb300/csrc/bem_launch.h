@@ -13,7 +13,9 @@ void launch_geometry(const double* xyz, const int* tri, const int* perm, const s
 void launch_sing_count(const NearBlk* blks, int nblk, const ElemD* ed, int* count, cudaStream_t st);
 void launch_sing_fill(const NearBlk* blks, int nblk, const ElemD* ed, const int* offs, SingPair* out,
                       cudaStream_t st);
-void launch_static(const SingPair* pairs, int n, const ElemD* ed, const KParams<double>& P, double* out,
+// Static parts of the singular pairs; fp32: the near-singular rule in FP32
+// (enough for the complex64 operator), else FP64.
+void launch_static(const SingPair* pairs, int n, const ElemD* ed, const KParams<double>& P, double* out, bool fp32,
                    cudaStream_t st);
 void launch_pair_sort(const NearBlk* blks, int nblk, const ElemF* ef, const ElemD* ed, const long long* poff,
                       unsigned* plist, int* pcount, cudaStream_t st);
@@ -72,6 +74,14 @@ void launch_precond(const Pm* pinv, const V* v, Z* z, int ne, cudaStream_t st);
 // Partial dot products part[l * nblk + blk] of conj(V_l) . w, l < nvec (FP64)
 template <typename Vb, typename W>
 int launch_dots(const Vb* V, long long ldv, int nvec, const W* w, long long n, c128* part, cudaStream_t st);
+// One Arnoldi orthogonalisation step (CGS2 against V_0..V_j, norm, and
+// V_{j+1} = w / ||w||) in a single cooperative launch; hcol receives
+// [h1 (m+1) | h2 (m+1) | ||w||^2]; part needs (2 (j+1) + 1) x
+// arnoldi_orth_max_blocks() complex values.
+template <typename Vb>
+cudaError_t launch_arnoldi_orth(Vb* V, long long ldv, int j, Vb* w, long long n, c128* part, c128* hcol, int m,
+                                cudaStream_t st);
+int arnoldi_orth_max_blocks();
 // out[l] = sum_blk part[l * nblk + blk]
 void launch_dots_final(const c128* part, int nblk, int nvec, c128* out, cudaStream_t st);
 // w -= sum_l V_l h_l

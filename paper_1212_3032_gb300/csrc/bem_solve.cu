@@ -12,10 +12,14 @@
 //   k_hmv_reduce per leaf row, the task slots summed in a fixed order
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "bem_internal.h"
 #include "bem_launch.h"
 
 namespace bem {
+
+namespace cg = cooperative_groups;
 
 template <typename A, typename B> struct Promote;
 template <> struct Promote<float, float> { using type = float; };
@@ -449,6 +453,161 @@ void launch_scale(const W* w, Vb* v, long long n, const double* nrm2, cudaStream
 }
 template void launch_scale<c64, c64>(const c64*, c64*, long long, const double*, cudaStream_t);
 template void launch_scale<c128, c128>(const c128*, c128*, long long, const double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// One Arnoldi orthogonalisation step in one cooperative launch: classical
+// Gram-Schmidt twice against V_0..V_j, the norm, and V_{j+1} = w / ||w||.
+// Block b owns a slice of the rows; partial sums per block go to part and are
+// added in block order by every block after a grid barrier (the same result
+// in every block and on every run).
+// Arithmetic: with a complex64 basis, the products and each lane's short run
+// of sums (the slice / 32 elements it owns) are FP32, everything above that
+// FP64; with a complex128 basis, FP64 throughout. (FP64 throughput is a small
+// fraction of FP32 here; FP32 products of FP32 data keep the error at the
+// basis's own rounding level.)
+//   hcol: [h1 (m+1) | h2 (m+1) | ||w||^2], written by block 0
+// ---------------------------------------------------------------------------
+template <typename Vb>
+__device__ __forceinline__ void orth_partials(const Vb* __restrict__ V, long long ldv, int nvec,
+                                              const Vb* __restrict__ w, long long i0, long long i1,
+                                              c128* __restrict__ part) {
+  using T = decltype(Vb{}.re);
+  // warp k handles vectors l = k, k + nwarps, ...; lanes stride over the slice
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = wid; l < nvec; l += nw) {
+    const Vb* v = V + l * ldv;
+    T re = 0, im = 0;
+    for (long long i = i0 + lane; i < i1; i += 32) {
+      const Vb a = v[i], b = w[i];
+      re = fma(a.re, b.re, fma(a.im, b.im, re));  // conj(a) * b
+      im = fma(a.re, b.im, fma(-a.im, b.re, im));
+    }
+    double dre = wsum((double)re), dim = wsum((double)im);
+    if (lane == 0) part[(long long)l * gridDim.x + blockIdx.x] = c128{dre, dim};
+  }
+}
+// out[l] = sum_b part[l * nblk + b] for l < nvec, in block order (into shared memory)
+__device__ __forceinline__ void orth_sums(const c128* __restrict__ part, int nvec, c128* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nb = gridDim.x;
+  for (int l = wid; l < nvec; l += nw) {
+    double re = 0, im = 0;
+    for (int b = lane; b < nb; b += 32) {
+      re += part[(long long)l * nb + b].re;
+      im += part[(long long)l * nb + b].im;
+    }
+    re = wsum(re);
+    im = wsum(im);
+    if (lane == 0) out[l] = c128{re, im};
+  }
+}
+// w -= sum_l V_l h_l over the slice (h in the basis's precision: hT)
+template <typename Vb>
+__device__ __forceinline__ void orth_update(const Vb* __restrict__ V, long long ldv, int nvec,
+                                            const cplx<decltype(Vb{}.re)>* h, Vb* __restrict__ w, long long i0,
+                                            long long i1) {
+  using T = decltype(Vb{}.re);
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    T re = 0, im = 0;
+    for (int l = 0; l < nvec; ++l) {
+      const Vb a = V[l * ldv + i];
+      const cplx<T> c = h[l];
+      re = fma(a.re, c.re, fma(-a.im, c.im, re));
+      im = fma(a.re, c.im, fma(a.im, c.re, im));
+    }
+    Vb o = w[i];
+    o.re = o.re - re;
+    o.im = o.im - im;
+    w[i] = o;
+  }
+}
+
+constexpr int ORTH_THREADS = 256;
+constexpr int ORTH_MAXVEC = 513;  // shared-memory coefficient slots (restart + 1 <= 512)
+
+template <typename Vb>
+__global__ void __launch_bounds__(ORTH_THREADS) k_arnoldi_orth(Vb* __restrict__ V, long long ldv, int j,
+                                                               Vb* __restrict__ w, long long n,
+                                                               c128* __restrict__ part, c128* __restrict__ hcol,
+                                                               int m) {
+  using T = decltype(Vb{}.re);
+  cg::grid_group grid = cg::this_grid();
+  __shared__ c128 h[ORTH_MAXVEC];
+  __shared__ cplx<T> hT[ORTH_MAXVEC];
+  const int nvec = j + 1;
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long i0 = min(n, (long long)blockIdx.x * per), i1 = min(n, i0 + per);
+  c128* p1 = part;
+  c128* p2 = part + (long long)nvec * gridDim.x;
+  c128* p3 = p2 + (long long)nvec * gridDim.x;
+  orth_partials<Vb>(V, ldv, nvec, w, i0, i1, p1);
+  grid.sync();
+  orth_sums(p1, nvec, h);
+  __syncthreads();
+  for (int l = threadIdx.x; l < nvec; l += blockDim.x) {
+    hT[l] = mk<T>(T(h[l].re), T(h[l].im));
+    if (blockIdx.x == 0) hcol[l] = h[l];
+  }
+  __syncthreads();
+  orth_update<Vb>(V, ldv, nvec, hT, w, i0, i1);
+  __syncthreads();  // this block's slice of w is complete before its second pass reads it
+  orth_partials<Vb>(V, ldv, nvec, w, i0, i1, p2);
+  grid.sync();
+  orth_sums(p2, nvec, h);
+  __syncthreads();
+  for (int l = threadIdx.x; l < nvec; l += blockDim.x) {
+    hT[l] = mk<T>(T(h[l].re), T(h[l].im));
+    if (blockIdx.x == 0) hcol[m + 1 + l] = h[l];
+  }
+  __syncthreads();
+  orth_update<Vb>(V, ldv, nvec, hT, w, i0, i1);
+  __syncthreads();
+  orth_partials<Vb>(w, 0, 1, w, i0, i1, p3);  // ||w||^2 of the slice
+  grid.sync();
+  orth_sums(p3, 1, h);
+  __syncthreads();
+  const double nrm2 = h[0].re;
+  if (blockIdx.x == 0 && threadIdx.x == 0) hcol[2 * (m + 1)] = c128{nrm2, 0.0};
+  const T sc = T(nrm2 > 0 ? 1.0 / sqrt(nrm2) : 0.0);
+  Vb* vn = V + (long long)(j + 1) * ldv;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const Vb a = w[i];
+    Vb o;
+    o.re = a.re * sc;
+    o.im = a.im * sc;
+    vn[i] = o;
+  }
+}
+
+template <typename Vb>
+int orth_grid(long long n) {
+  static int cap[2] = {0, 0};  // resident blocks (per process; one device)
+  int& c = cap[sizeof(Vb) == 8 ? 0 : 1];
+  if (!c) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi_orth<Vb>, ORTH_THREADS, 0);
+    c = std::max(1, sms * std::max(1, per));
+  }
+  // about 256 rows per block, at most one wave of resident blocks
+  return (int)std::max<long long>(1, std::min<long long>(c, (n + 255) / 256));
+}
+
+template <typename Vb>
+cudaError_t launch_arnoldi_orth(Vb* V, long long ldv, int j, Vb* w, long long n, c128* part, c128* hcol, int m,
+                                cudaStream_t st) {
+  if (j + 1 > ORTH_MAXVEC) return cudaErrorInvalidValue;
+  const int nb = orth_grid<Vb>(n);
+  void* args[] = {&V, &ldv, &j, &w, &n, &part, &hcol, &m};
+  count_if(true);
+  return cudaLaunchCooperativeKernel((const void*)k_arnoldi_orth<Vb>, dim3(nb), dim3(ORTH_THREADS), args, 0, st);
+}
+template cudaError_t launch_arnoldi_orth<c64>(c64*, long long, int, c64*, long long, c128*, c128*, int,
+                                              cudaStream_t);
+template cudaError_t launch_arnoldi_orth<c128>(c128*, long long, int, c128*, long long, c128*, c128*, int,
+                                               cudaStream_t);
+int arnoldi_orth_max_blocks() { return std::max(orth_grid<c64>(1LL << 40), orth_grid<c128>(1LL << 40)); }
 
 __global__ void k_residual(const c128* __restrict__ b, const c128* __restrict__ y, c128* __restrict__ r, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
