@@ -255,6 +255,7 @@ def run_ours(args, cfg):
     total_ms = 0.0
     unconverged = 0
     iters = 0
+    cycles = 0
     phase_ms = {"assemble_ms": 0.0, "guess_ms": 0.0, "solve_ms": 0.0}
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -269,6 +270,7 @@ def run_ours(args, cfg):
             total_ms += e0.elapsed_time(e1)
             unconverged += sum(1 for s in stats if not s["converged"])
             iters += sum(s["iters"] for s in stats)
+            cycles += sum(s["cycles"] for s in stats)
             for key in ("assemble_ms", "guess_ms", "solve_ms"):
                 phase_ms[key] += sum(s[key] for s in stats)
         torch.cuda.synchronize()
@@ -330,7 +332,8 @@ def run_ours(args, cfg):
                    "aca_tol": cfg["aca_tol"], "leaf": cfg["leaf"], "gmres_tol": cfg["tol"],
                    "guess": GUESS_LABEL[args.guess],
                    "l2": "flushed (256 MB write) before every timed step"},
-        "gmres_iters_per_step": iters / args.steps, "unconverged": unconverged,
+        "gmres_iters_per_step": iters / args.steps, "gmres_cycles_per_step": cycles / args.steps,
+        "unconverged": unconverged,
         "guess_residual_mean": statistics.fmean(s["guess_residual"] for s in stats[1:]),
         "sem_residual_mean": statistics.fmean(s["sem_residual"] for s in stats[1:]),
         "roofline": {"kernel": "H-matrix product (k_hmv_t + k_hmv_tasks + k_hmv_reduce)", "bound": "hbm", "achieved": hmv_gbs,

@@ -41,6 +41,16 @@ __device__ __forceinline__ c128 ld_stream(const c128* p) {
   return c128{v.x, v.y};
 }
 
+// loads that bypass L1 (data written by other CTAs of the same launch)
+__device__ __forceinline__ cplx<float> ld_global_cg(const cplx<float>* p) {
+  float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return cplx<float>{v.x, v.y};
+}
+__device__ __forceinline__ cplx<double> ld_global_cg(const cplx<double>* p) {
+  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return cplx<double>{v.x, v.y};
+}
+
 template <typename Acc>
 __device__ __forceinline__ void cmac(cplx<Acc>& acc, const cplx<Acc>& a, const cplx<Acc>& b) {
   acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
@@ -221,17 +231,48 @@ __global__ void __launch_bounds__(HMV_THREADS, 2) k_hmv_tasks(
                              red);
 }
 
-// The same task kernel over a list of task indices (the launch order).
-template <typename Op, typename X, typename Acc, int NRHS>
+// The same task kernel over a list of task indices (the launch order), with
+// the per-leaf reduction fused in: the CTA that completes the last task of a
+// leaf (a per-leaf arrival counter) adds the leaf's task partials in task
+// order (FP64) and writes y; it then resets the counter for the next product.
+template <typename Op, typename X, typename Y, typename Acc, int NRHS>
 __global__ void __launch_bounds__(HMV_THREADS, 2) k_hmv_tasks_list(
     const int* __restrict__ list, const Task* __restrict__ tasks, const int* __restrict__ leaf_nr,
     const Panel* __restrict__ panels, const FarBlk* __restrict__ far, const int* __restrict__ rank,
     const Op* __restrict__ near, const Op* __restrict__ U, const cplx<Acc>* __restrict__ t, int tstride,
-    const X* __restrict__ x, long long N, cplx<Acc>* __restrict__ part, long long pstride) {
+    const X* __restrict__ x, long long N, cplx<Acc>* __restrict__ part, long long pstride,
+    const int* __restrict__ leaf_r0, const int* __restrict__ task_ptr, int* __restrict__ leaf_cnt,
+    Y* __restrict__ y) {
   extern __shared__ unsigned char smem_raw[];
   cplx<Acc>* red = reinterpret_cast<cplx<Acc>*>(smem_raw);
-  hmv_task<Op, X, Acc, NRHS>(tasks[list[blockIdx.x]], leaf_nr, panels, far, rank, near, U, t, tstride, x, N, part,
-                             pstride, red);
+  __shared__ int last;
+  const Task tk = tasks[list[blockIdx.x]];
+  hmv_task<Op, X, Acc, NRHS>(tk, leaf_nr, panels, far, rank, near, U, t, tstride, x, N, part, pstride, red);
+  __threadfence();  // this task's partials are visible before its arrival is counted
+  __syncthreads();
+  const int t0 = task_ptr[tk.leaf], t1 = task_ptr[tk.leaf + 1];
+  if (threadIdx.x == 0) last = atomicAdd(&leaf_cnt[tk.leaf], 1) == t1 - t0 - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int rows = 3 * leaf_nr[tk.leaf];
+  const long long row0 = 3LL * leaf_r0[tk.leaf];
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      cplx<double> sum{0, 0};
+      for (int k = t0; k < t1; ++k) {
+        const cplx<Acc> v = ld_global_cg(part + q * pstride + tasks[k].slot + r);
+        sum.re += v.re;
+        sum.im += v.im;
+      }
+      Y o;
+      o.re = decltype(o.re)(sum.re);
+      o.im = decltype(o.im)(sum.im);
+      y[q * N + row0 + r] = o;
+    }
+  }
+  if (threadIdx.x == 0) leaf_cnt[tk.leaf] = 0;
 }
 
 // phase 3: y[rows of leaf] = sum over the leaf's tasks, in task order
@@ -268,16 +309,13 @@ static void hmv_impl(const bem_ctx* ctx, const Op* near, const Op* U, const Op* 
   if (count_if(nfar)) k_hmv_t<Op, X, Acc, NRHS><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, V, x, ctx->N, t,
                                                                        ctx->t_entries);
   cplx<Acc>* part = reinterpret_cast<cplx<Acc>*>(ctx->part.p);
-  size_t sm = (size_t)2 * HMV_THREADS * NRHS * sizeof(cplx<Acc>);
+  size_t sm = (size_t)HMV_THREADS * NRHS * sizeof(cplx<Acc>);  // red: NRHS x G x rows <= NRHS x threads
   // every task, largest first (CTAs are dispatched in index order: the long
   // tasks start early and the short ones fill the tail)
   if (count_if(ctx->ntasks))
-    k_hmv_tasks_list<Op, X, Acc, NRHS><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
+    k_hmv_tasks_list<Op, X, Y, Acc, NRHS><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
         ctx->task_order.p, ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t,
-        ctx->t_entries, x, ctx->N, part, ctx->part_rows);
-  count_if(true);
-  k_hmv_reduce<Acc, Y, NRHS><<<ctx->nleaves, 256, 0, st>>>(ctx->leaf_r0.p, ctx->leaf_nr.p, ctx->task_ptr.p,
-                                                          ctx->tasks.p, part, ctx->part_rows, ctx->N, y);
+        ctx->t_entries, x, ctx->N, part, ctx->part_rows, ctx->leaf_r0.p, ctx->task_ptr.p, ctx->leaf_cnt.p, y);
 }
 
 template <typename Op, typename X, typename Y, typename Acc>
