@@ -1190,86 +1190,39 @@ int gmres(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq_stat
 // X: K vectors (device, stride N), in the order a_{k-1}, a_{k-2}, ...
 // extra (optional): one more candidate column after them (the learned
 // proposal), so that the fit over the larger span can only lower the residual.
-// res (optional): res[0] = ||b - A a0|| / ||b|| over the X columns alone,
-// res[1] = over every column, both from ||b||^2 - sum_i |q_i^H b|^2.
+// The products A X run as one multi-right-hand-side H-matrix product, the fit
+// as one cooperative kernel. With want_res, the residual estimates
+// (res[0]: X columns alone, res[1]: every column; see launch_sem_fit) are
+// copied to ctx->host_red + SEM_RES_SLOT, valid after the next stream sync.
 // ---------------------------------------------------------------------------
+constexpr int SEM_RES_SLOT = 4094;
 int sem_impl(bem_ctx* ctx, const c128* const* X, int K, const c128* b, c128* a0, const c128* extra = nullptr,
-             double* res = nullptr) {
+             bool want_res = false) {
   cudaStream_t st = ctx->stream;
   const long long N = ctx->N;
-  BEM_CUDA_TRY(cudaMemsetAsync(a0, 0, N * sizeof(c128), st));
-  if (res) res[0] = res[1] = 1.0;
+  if (want_res) ctx->host_red[SEM_RES_SLOT] = ctx->host_red[SEM_RES_SLOT + 1] = 1.0;
   const int C = K + (extra ? 1 : 0);
-  if (C <= 0) return BEM_OK;
-  auto column = [&](int c) { return c < K ? X[c] : extra; };
+  if (C <= 0) {
+    BEM_CUDA_TRY(cudaMemsetAsync(a0, 0, N * sizeof(c128), st));
+    return BEM_OK;
+  }
+  if (C > SEM_MAXC) return fail(ctx, BEM_ERR_INVALID_ARG, "too many extrapolation columns");
+  std::vector<const c128*> cols(C);
+  for (int c = 0; c < C; ++c) cols[c] = c < K ? X[c] : extra;
   BEM_CUDA_TRY(ctx->sem_work.ensure(3LL * C * N));
   c128* Xc = ctx->sem_work.p;
   c128* Y = Xc + (long long)C * N;
   c128* Q = Y + (long long)C * N;
   for (int q = 0; q < C; ++q)
-    BEM_CUDA_TRY(cudaMemcpyAsync(Xc + q * N, column(q), N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
+    BEM_CUDA_TRY(cudaMemcpyAsync(Xc + q * N, cols[q], N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
   for (int q = 0; q < C; q += 4) TRY(apply_fast(ctx, Xc + q * N, Y + q * N, std::min(4, C - q)));
-  BEM_CUDA_TRY(ctx->red.ensure(2LL * 64 * 8 * 2 + 64));
-  c128* part = reinterpret_cast<c128*>(ctx->red.p);
-  c128* hdev = part + 64 * 8;
-  std::vector<std::complex<double>> R(C * C, 0.0);
-  std::vector<int> keep;
-  double r00 = 0;
-  for (int c = 0; c < C; ++c) {
-    c128* qc = Q + (long long)keep.size() * N;
-    BEM_CUDA_TRY(cudaMemcpyAsync(qc, Y + c * N, N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
-    std::vector<std::complex<double>> col(keep.size(), 0.0);
-    for (int pass = 0; pass < 2 && !keep.empty(); ++pass) {
-      int nb = launch_dots<c128, c128>(Q, N, (int)keep.size(), qc, N, part, st);
-      launch_dots_final(part, nb, (int)keep.size(), hdev, st);
-      launch_update<c128, c128>(Q, N, (int)keep.size(), hdev, qc, N, st);
-      CK("sem qr");
-      std::vector<c128> h(keep.size());
-      BEM_CUDA_TRY(cudaMemcpyAsync(h.data(), hdev, keep.size() * sizeof(c128), cudaMemcpyDeviceToHost, st));
-      BEM_CUDA_TRY(cudaStreamSynchronize(st));
-      for (size_t i = 0; i < keep.size(); ++i) col[i] += std::complex<double>(h[i].re, h[i].im);
-    }
-    std::complex<double> nn;
-    TRY(dot_host(ctx, qc, qc, N, nn));
-    double nrm = std::sqrt(std::max(0.0, nn.real()));
-    if (keep.empty()) r00 = nrm;
-    if (!(nrm > 1e-12 * r00) || nrm == 0.0) continue;  // numerically dependent column: drop
-    launch_copy_cast(qc, qc, N, 1.0 / nrm, st);
-    int kk = (int)keep.size();
-    for (int i = 0; i < kk; ++i) R[i * C + kk] = col[i];
-    R[kk * C + kk] = nrm;
-    keep.push_back(c);
-  }
-  int kk = (int)keep.size();
-  if (kk == 0) return BEM_OK;
-  int nb = launch_dots<c128, c128>(Q, N, kk, b, N, part, st);
-  launch_dots_final(part, nb, kk, hdev, st);
-  CK("sem qhb");
-  std::vector<c128> qb(kk);
-  BEM_CUDA_TRY(cudaMemcpyAsync(qb.data(), hdev, kk * sizeof(c128), cudaMemcpyDeviceToHost, st));
-  BEM_CUDA_TRY(cudaStreamSynchronize(st));
-  if (res) {
-    std::complex<double> bb;
-    TRY(dot_host(ctx, b, b, N, bb));
-    double rem_x = bb.real(), rem_all = bb.real();
-    for (int i = 0; i < kk; ++i) {
-      double q2 = qb[i].re * qb[i].re + qb[i].im * qb[i].im;
-      rem_all -= q2;
-      if (keep[i] < K) rem_x -= q2;
-    }
-    if (bb.real() > 0) {
-      res[0] = std::sqrt(std::max(0.0, rem_x) / bb.real());
-      res[1] = std::sqrt(std::max(0.0, rem_all) / bb.real());
-    }
-  }
-  std::vector<std::complex<double>> sv(kk);
-  for (int i = kk - 1; i >= 0; --i) {
-    std::complex<double> v(qb[i].re, qb[i].im);
-    for (int j = i + 1; j < kk; ++j) v -= R[i * C + j] * sv[j];
-    sv[i] = v / R[i * C + i];
-  }
-  for (int i = 0; i < kk; ++i) launch_axpy(c128{sv[i].real(), sv[i].imag()}, column(keep[i]), a0, N, st);
-  CK("sem combine");
+  BEM_CUDA_TRY(ctx->sem_part.ensure((size_t)3 * (SEM_MAXC + 1) * arnoldi_orth_max_blocks()));
+  BEM_CUDA_TRY(ctx->sem_res.ensure(2));
+  BEM_CUDA_TRY(launch_sem_fit(cols.data(), C, K, Y, b, Q, ctx->sem_part.p, a0, ctx->sem_res.p, N, st));
+  CK("sem fit");
+  if (want_res)
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->host_red + SEM_RES_SLOT, ctx->sem_res.p, 2 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
   return BEM_OK;
 }
 
@@ -1547,17 +1500,17 @@ static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_de
     for (int q = 1; q <= 4 && q <= k; ++q) prev[q - 1] = ctx->sol.p + (long long)(k - q) * N;
     const c128* extra = nullptr;
     if (o.guess == BEM_GUESS_MLP && k >= 4) TRY(mlp_propose(ctx, prev, s.s_re * dt, s.s_im * dt, &extra));
-    double res[2] = {1.0, 1.0};
-    if (K > 0 || extra) {
-      TRY(sem_impl(ctx, prev, K, ctx->b64.p, xk, extra, res));
+    const bool fit = K > 0 || extra;
+    if (fit) {
+      TRY(sem_impl(ctx, prev, K, ctx->b64.p, xk, extra, true));
     } else {
       BEM_CUDA_TRY(cudaMemsetAsync(xk, 0, N * sizeof(c128), st));
     }
-    s.sem_residual = res[0];
     cudaEventRecord(t1.b, st);
     cudaEventRecord(t2.a, st);
     int rc = gmres(ctx, ctx->b64.p, xk, o, &s);
     cudaEventRecord(t2.b, st);
+    s.sem_residual = fit ? ctx->host_red[SEM_RES_SLOT] : 1.0;  // gmres synchronised the stream
     if (rc != BEM_OK && rc != BEM_ERR_NOT_CONVERGED) return rc;
     if (rc == BEM_ERR_NOT_CONVERGED) worst = rc;
     if (o.guess == BEM_GUESS_MLP && k >= 4)

@@ -249,6 +249,8 @@ struct bem_ctx {
   int mlp_steps = 4;       // Adam steps after each solved frequency
   double mlp_lr = 1e-3;
   bem::DevBuf<bem::c128> sem_work;     // extrapolation workspace (3 x columns x N)
+  bem::DevBuf<bem::c128> sem_part;     // its partial sums
+  bem::DevBuf<double> sem_res;         // its residual estimates
 
   // sweep results
   int n_omega = 0;

@@ -82,6 +82,13 @@ template <typename Vb>
 cudaError_t launch_arnoldi_orth(Vb* V, long long ldv, int j, Vb* w, long long n, c128* part, c128* hcol, int m,
                                 cudaStream_t st);
 int arnoldi_orth_max_blocks();
+// Solution extrapolation fit (Sec. 4.2) after Y = A X (C columns of n, c128):
+// CGS2 QR, s = R^{-1} Q^H b, a0 = X s, and the residual estimates res[0..1]
+// (device), in one cooperative launch. Q: C x n scratch; part: 3 (SEM_MAXC + 1)
+// x arnoldi_orth_max_blocks() complex values.
+constexpr int SEM_MAXC = 5;
+cudaError_t launch_sem_fit(const c128* const* X, int C, int K, const c128* Y, const c128* b, c128* Q, c128* part,
+                           c128* a0, double* res, long long n, cudaStream_t st);
 // out[l] = sum_blk part[l * nblk + blk]
 void launch_dots_final(const c128* part, int nblk, int nvec, c128* out, cudaStream_t st);
 // w -= sum_l V_l h_l

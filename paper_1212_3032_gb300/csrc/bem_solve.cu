@@ -647,6 +647,139 @@ template cudaError_t launch_arnoldi_orth<c128>(c128*, long long, int, c128*, lon
                                                cudaStream_t);
 int arnoldi_orth_max_blocks() { return std::max(orth_grid<c64>(1LL << 40), orth_grid<c128>(1LL << 40)); }
 
+// ---------------------------------------------------------------------------
+// Solution extrapolation (Sec. 4.2) after the products Y = A X, in one
+// cooperative launch: CGS2 QR of Y (FP64; a column whose norm after
+// orthogonalisation is <= 1e-12 of the first one's is dropped), s = R^{-1} Q^H b,
+// a0 = X s. Every block holds the same R, Q^H b and s (sums in block order).
+// res[0] = ||b - A a0|| / ||b|| over the columns before the extra one,
+// res[1] = over every column (from ||b||^2 - sum |q_i^H b|^2), by block 0.
+// ---------------------------------------------------------------------------
+struct SemCols {
+  const c128* x[SEM_MAXC];
+};
+
+__global__ void __launch_bounds__(ORTH_THREADS) k_sem_fit(SemCols X, int C, int K, const c128* __restrict__ Y,
+                                                          const c128* __restrict__ b, c128* __restrict__ Q,
+                                                          c128* __restrict__ part, c128* __restrict__ a0,
+                                                          double* __restrict__ res, long long n) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ c128 R[SEM_MAXC][SEM_MAXC];
+  __shared__ c128 h[SEM_MAXC + 1], hsum[SEM_MAXC], sv[SEM_MAXC];
+  __shared__ int keep[SEM_MAXC];
+  __shared__ int kept;
+  __shared__ double r00;
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long i0 = min(n, (long long)blockIdx.x * per), i1 = min(n, i0 + per);
+  // three partial-sum buffers used in rotation (a buffer is rewritten only
+  // after every block has passed the grid barrier that follows its sums)
+  c128* pb[3] = {part, part + (long long)(SEM_MAXC + 1) * gridDim.x, part + 2LL * (SEM_MAXC + 1) * gridDim.x};
+  int rot = 0;
+  if (threadIdx.x == 0) {
+    kept = 0;
+    r00 = 0;
+  }
+  __syncthreads();
+  for (int c = 0; c < C; ++c) {
+    const int kk = kept;
+    c128* qc = Q + (long long)kk * n;
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) qc[i] = Y[(long long)c * n + i];
+    if (threadIdx.x < SEM_MAXC) hsum[threadIdx.x] = c128{0, 0};
+    __syncthreads();
+    for (int pass = 0; pass < 2 && kk > 0; ++pass) {
+      c128* p = pb[rot];
+      rot = (rot + 1) % 3;
+      orth_partials<c128>(Q, n, kk, qc, i0, i1, p);
+      grid.sync();
+      orth_sums(p, kk, h);
+      __syncthreads();
+      if (threadIdx.x < kk) {
+        hsum[threadIdx.x].re += h[threadIdx.x].re;
+        hsum[threadIdx.x].im += h[threadIdx.x].im;
+      }
+      orth_update<c128>(Q, n, kk, h, qc, i0, i1);
+      __syncthreads();
+    }
+    c128* p = pb[rot];
+    rot = (rot + 1) % 3;
+    orth_partials<c128>(qc, 0, 1, qc, i0, i1, p);
+    grid.sync();
+    orth_sums(p, 1, h);
+    __syncthreads();
+    const double nrm = sqrt(fmax(0.0, h[0].re));
+    const double ref = kk == 0 ? nrm : r00;
+    if (nrm > 1e-12 * ref && nrm != 0.0) {  // uniform: every block has the same sums
+      const double sc = 1.0 / nrm;
+      for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) qc[i] = c128{qc[i].re * sc, qc[i].im * sc};
+      if (threadIdx.x == 0) {
+        for (int l = 0; l < kk; ++l) R[l][kk] = hsum[l];
+        R[kk][kk] = c128{nrm, 0.0};
+        keep[kk] = c;
+        if (kk == 0) r00 = nrm;
+        kept = kk + 1;
+      }
+    }
+    __syncthreads();
+  }
+  const int kk = kept;
+  if (kk == 0) {
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) a0[i] = c128{0, 0};
+    if (blockIdx.x == 0 && threadIdx.x == 0) res[0] = res[1] = 1.0;
+    return;
+  }
+  // Q^H b (vectors 0..kk-1) and ||b||^2 (slot kk) in one pass
+  c128* p = pb[rot];
+  orth_partials<c128>(Q, n, kk, b, i0, i1, p);
+  orth_partials<c128>(b, 0, 1, b, i0, i1, p + (long long)kk * gridDim.x);
+  grid.sync();
+  orth_sums(p, kk + 1, h);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = kk - 1; i >= 0; --i) {
+      c128 v = h[i];
+      for (int j2 = i + 1; j2 < kk; ++j2) {
+        const c128 rr = R[i][j2], sj = sv[j2];
+        v.re -= rr.re * sj.re - rr.im * sj.im;
+        v.im -= rr.re * sj.im + rr.im * sj.re;
+      }
+      const c128 d = R[i][i];  // real, positive
+      sv[i] = c128{v.re / d.re, v.im / d.re};
+    }
+    if (blockIdx.x == 0) {
+      const double bb = h[kk].re;
+      double rem_x = bb, rem_all = bb;
+      for (int i = 0; i < kk; ++i) {
+        const double q2 = h[i].re * h[i].re + h[i].im * h[i].im;
+        rem_all -= q2;
+        if (keep[i] < K) rem_x -= q2;
+      }
+      res[0] = bb > 0 ? sqrt(fmax(0.0, rem_x) / bb) : 1.0;
+      res[1] = bb > 0 ? sqrt(fmax(0.0, rem_all) / bb) : 1.0;
+    }
+  }
+  __syncthreads();
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    double re = 0, im = 0;
+    for (int l = 0; l < kk; ++l) {
+      const c128 xv = X.x[keep[l]][i], s2 = sv[l];
+      re += xv.re * s2.re - xv.im * s2.im;
+      im += xv.re * s2.im + xv.im * s2.re;
+    }
+    a0[i] = c128{re, im};
+  }
+}
+
+cudaError_t launch_sem_fit(const c128* const* X, int C, int K, const c128* Y, const c128* b, c128* Q, c128* part,
+                           c128* a0, double* res, long long n, cudaStream_t st) {
+  if (C < 1 || C > SEM_MAXC) return cudaErrorInvalidValue;
+  SemCols cols{};
+  for (int c = 0; c < C; ++c) cols.x[c] = X[c];
+  const int nb = orth_grid<c128>(n);
+  void* args[] = {&cols, &C, &K, &Y, &b, &Q, &part, &a0, &res, &n};
+  count_if(true);
+  return cudaLaunchCooperativeKernel((const void*)k_sem_fit, dim3(nb), dim3(ORTH_THREADS), args, 0, st);
+}
+
 __global__ void k_residual(const c128* __restrict__ b, const c128* __restrict__ y, c128* __restrict__ r, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
