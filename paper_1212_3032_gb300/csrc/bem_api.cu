@@ -311,6 +311,8 @@ extern "C" void bem_default_opts(bem_opts* o) {
   o->dense = 0;
 }
 
+extern "C" void bem_destroy(bem_ctx* ctx);
+
 extern "C" int bem_create(bem_ctx** out, int device, void* stream) {
   if (!out) return BEM_ERR_INVALID_ARG;
   *out = nullptr;
@@ -334,6 +336,12 @@ extern "C" int bem_create(bem_ctx** out, int device, void* stream) {
     delete ctx;
     return BEM_ERR_OOM;
   }
+  if (cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    bem_destroy(ctx);
+    return BEM_ERR_CUDA;
+  }
   *out = ctx;
   return BEM_OK;
 }
@@ -345,6 +353,12 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
   if (ctx->host_red) cudaFreeHost(ctx->host_red);
   if (ctx->host_cols) cudaFreeHost(ctx->host_cols);
   for (cudaEvent_t e : ctx->col_events) cudaEventDestroy(e);
+  if (ctx->aux_stream) {
+    cudaStreamSynchronize(ctx->aux_stream);
+    cudaStreamDestroy(ctx->aux_stream);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -763,8 +777,7 @@ int check_ready(bem_ctx* ctx) {
 // Far-field blocks at the current s: reuse of the previous assembly's pivots
 // where available, then ACA steps for every block not yet converged.
 template <typename R, typename Op>
-int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, const bem_opts& o) {
-  cudaStream_t st = ctx->stream;
+int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, const bem_opts& o, cudaStream_t st) {
   const size_t nf = ctx->far_h.size();
   BEM_CUDA_TRY(ctx->piv_i.ensure(std::max(1, ctx->t_entries)));
   BEM_CUDA_TRY(ctx->piv_j.ensure(std::max(1, ctx->t_entries)));
@@ -817,29 +830,47 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
   KParams<double> Pd = make_params<double>(ctx, sre, sim);
   BEM_CUDA_TRY(ctx->status.ensure(1));
   DevBuf<int>& status = ctx->status;
+  // The far field (ACA, latency-bound in its continuation steps) runs on the
+  // auxiliary stream while the right-hand side, the singular pairs and the
+  // near field run on the caller's stream; they write disjoint storage and
+  // join before the assembly ends.
+  const bool mixed = is_mixed(ctx);
+  KParams<float> Pf = make_params<float>(ctx, sre, sim);
+  if (mixed) {
+    if (ctx->near32.n < (size_t)std::max<long long>(1, ctx->near_entries)) ctx->near_zero_pending = true;
+    BEM_CUDA_TRY(ctx->near32.ensure(std::max<long long>(1, ctx->near_entries)));
+    BEM_CUDA_TRY(ctx->u32.ensure(std::max<long long>(1, ctx->u_entries)));
+    BEM_CUDA_TRY(ctx->v32.ensure(std::max<long long>(1, ctx->v_entries)));
+    BEM_CUDA_TRY(ctx->t32.ensure(4LL * std::max(1, ctx->t_entries)));
+    BEM_CUDA_TRY(ctx->prec_inv32.ensure(9LL * ctx->ne));
+  } else {
+    if (ctx->near64.n < (size_t)std::max<long long>(1, ctx->near_entries)) ctx->near_zero_pending = true;
+    BEM_CUDA_TRY(ctx->near64.ensure(std::max<long long>(1, ctx->near_entries)));
+    BEM_CUDA_TRY(ctx->u64.ensure(std::max<long long>(1, ctx->u_entries)));
+    BEM_CUDA_TRY(ctx->v64.ensure(std::max<long long>(1, ctx->v_entries)));
+  }
+  BEM_CUDA_TRY(ctx->t64.ensure(4LL * std::max(1, ctx->t_entries)));
+  cudaStream_t aux = ctx->aux_stream;
+  BEM_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
+  BEM_CUDA_TRY(cudaStreamWaitEvent(aux, ctx->ev_fork, 0));
+  if (mixed) TRY((run_aca<float, c64>(ctx, Pf, ctx->u32.p, ctx->v32.p, o, aux)));
+  else TRY((run_aca<double, c128>(ctx, Pd, ctx->u64.p, ctx->v64.p, o, aux)));
+  BEM_CUDA_TRY(cudaEventRecord(ctx->ev_join, aux));
   if (b) {
     BEM_CUDA_TRY(cudaMemsetAsync(b, 0, ctx->N * sizeof(c128), st));
-    if (is_mixed(ctx))
+    if (mixed)
       launch_rhs_far<float>(ctx->rhs_rng.p, ctx->rhs_rptr.p, ctx->elem_leaf.p, ctx->ne, ctx->ef.p, ctx->ed.p, ctx->bc.p,
-                            ctx->patf.p, ctx->pattern.p, make_params<float>(ctx, sre, sim), pk, b, st);
+                            ctx->patf.p, ctx->pattern.p, Pf, pk, b, st);
     else
       launch_rhs_far<double>(ctx->rhs_rng.p, ctx->rhs_rptr.p, ctx->elem_leaf.p, ctx->ne, ctx->ef.p, ctx->ed.p, ctx->bc.p,
                              ctx->patf.p, ctx->pattern.p, Pd, pk, b, st);
     CK("rhs_far");
   }
-  if (is_mixed(ctx)) {
-    if (ctx->near32.n < (size_t)std::max<long long>(1, ctx->near_entries)) ctx->near_zero_pending = true;
-    BEM_CUDA_TRY(ctx->near32.ensure(std::max<long long>(1, ctx->near_entries)));
+  if (mixed) {
     if (ctx->near_zero_pending) {
       BEM_CUDA_TRY(cudaMemsetAsync(ctx->near32.p, 0, ctx->near32.n * sizeof(c64), st));
       ctx->near_zero_pending = false;
     }
-    BEM_CUDA_TRY(ctx->u32.ensure(std::max<long long>(1, ctx->u_entries)));
-    BEM_CUDA_TRY(ctx->v32.ensure(std::max<long long>(1, ctx->v_entries)));
-    BEM_CUDA_TRY(ctx->t32.ensure(4LL * std::max(1, ctx->t_entries)));
-    BEM_CUDA_TRY(ctx->t64.ensure(4LL * std::max(1, ctx->t_entries)));
-    BEM_CUDA_TRY(ctx->prec_inv32.ensure(9LL * ctx->ne));
-    KParams<float> Pf = make_params<float>(ctx, sre, sim);
     launch_sing<float, c64>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pf,
                             ctx->near32.p, ctx->prec_inv.p, pattern_tree, pk, b, status.p, st);
     CK("sing");
@@ -847,21 +878,15 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
                                     ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, ctx->near32.p,
                                     b ? ctx->patf.p : nullptr, b ? ctx->pattern.p : nullptr, pk, b, st);
     CK("near_regular");
-    TRY((run_aca<float, c64>(ctx, Pf, ctx->u32.p, ctx->v32.p, o)));
     long long n9 = 9LL * ctx->ne;
     count_if(true);
     k_pinv_cast<<<(unsigned)((n9 + 255) / 256), 256, 0, st>>>(ctx->prec_inv.p, ctx->prec_inv32.p, n9);
     CK("pinv_cast");
   } else {
-    if (ctx->near64.n < (size_t)std::max<long long>(1, ctx->near_entries)) ctx->near_zero_pending = true;
-    BEM_CUDA_TRY(ctx->near64.ensure(std::max<long long>(1, ctx->near_entries)));
     if (ctx->near_zero_pending) {
       BEM_CUDA_TRY(cudaMemsetAsync(ctx->near64.p, 0, ctx->near64.n * sizeof(c128), st));
       ctx->near_zero_pending = false;
     }
-    BEM_CUDA_TRY(ctx->u64.ensure(std::max<long long>(1, ctx->u_entries)));
-    BEM_CUDA_TRY(ctx->v64.ensure(std::max<long long>(1, ctx->v_entries)));
-    BEM_CUDA_TRY(ctx->t64.ensure(4LL * std::max(1, ctx->t_entries)));
     launch_sing<double, c128>(ctx->sing.p, ctx->nsing, ctx->ed.p, ctx->polar.p, ctx->bc.p, ctx->sing_static.p, Pd,
                               ctx->near64.p, ctx->prec_inv.p, pattern_tree, pk, b, status.p, st);
     CK("sing");
@@ -869,8 +894,8 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
                                       ctx->poff.p, ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd, ctx->near64.p,
                                       b ? ctx->patf.p : nullptr, b ? ctx->pattern.p : nullptr, pk, b, st);
     CK("near_regular");
-    TRY((run_aca<double, c128>(ctx, Pd, ctx->u64.p, ctx->v64.p, o)));
   }
+  BEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   prof_end(ctx, ev, 1, 0.0);
   ctx->assembled = true;
   ctx->s_re = sre;

@@ -172,6 +172,8 @@ struct bem_ctx {
   long long part_rows = 0;            // rows of the partial buffer per right-hand side
   bem::DevBuf<bem::Task> tasks;
   bem::DevBuf<int> task_order;        // task indices by size, largest first (launch order)
+  cudaStream_t aux_stream = nullptr;  // the far-field assembly runs here, joined back to stream
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bem::DevBuf<int> leaf_cnt;          // per leaf: tasks completed in the current product (reset to 0 after it)
   bem::DevBuf<int> task_ptr;          // CSR of tasks over leaves
   bem::DevBuf<double> part;           // partial sums (sized for 4 rhs of complex FP64)
