@@ -252,11 +252,11 @@ cudaEvent_t prof_begin(bem_ctx* ctx) {
   cudaEventRecord(a, ctx->stream);
   return a;
 }
-void prof_end(bem_ctx* ctx, cudaEvent_t a, int kind, double bytes) {
+void prof_end(bem_ctx* ctx, cudaEvent_t a, int kind, double base = 0.0, double mult = 0.0) {
   if (!a) return;
   cudaEvent_t b = take_event(ctx);
   cudaEventRecord(b, ctx->stream);
-  ctx->pending.push_back({a, b, bytes, kind});
+  ctx->pending.push_back({a, b, base, mult, kind == 0 ? ctx->prof_slot : 0, kind});
 }
 // Folds completed timings into the counters; timings whose end event has not
 // completed yet stay pending (after a stream sync every one has completed).
@@ -272,7 +272,7 @@ void prof_harvest(bem_ctx* ctx) {
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       if (p.kind == 0) {
         ctx->prof_hmv_ms += ms;
-        ctx->prof_hmv_bytes += p.bytes;
+        ctx->prof_products.push_back({p.base, p.mult, p.slot});
         ctx->prof_hmv_launches += 1;
       } else {
         ctx->prof_asm_ms += ms;
@@ -287,9 +287,30 @@ void prof_harvest(bem_ctx* ctx) {
 }
 
 // Algorithmic bytes of one H-matrix product: every stored operator entry in
-// use (near blocks, U and V columns up to the rank), x read once, y written once.
-double hmv_bytes(const bem_ctx* ctx, int op_bytes, int x_bytes, int y_bytes, int nrhs, long long used_lowrank) {
-  return (double)op_bytes * (ctx->near_entries + used_lowrank) + (double)nrhs * ctx->N * (x_bytes + y_bytes);
+// use (near blocks, U and V columns up to the rank), x read once, y written
+// once; the low-rank entries are known on the device only (counted after each
+// assembly into prof_dev), so the product records base + mult x entries.
+void prof_end_hmv(bem_ctx* ctx, cudaEvent_t a, int op_bytes, int x_bytes, int y_bytes, int nrhs) {
+  prof_end(ctx, a, 0, (double)op_bytes * ctx->near_entries + (double)nrhs * ctx->N * (x_bytes + y_bytes),
+           (double)op_bytes);
+}
+
+constexpr int PROF_SLOTS = 1 << 16;
+
+__global__ void k_count_zero(const int* __restrict__ v, int n, long long* __restrict__ out) {
+  int c = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c += v[i] == 0;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)c);
+}
+__global__ void k_lowrank_entries(const int* __restrict__ rank, const FarBlk* __restrict__ far, int n,
+                                  long long* __restrict__ out) {
+  long long c = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    c += (long long)rank[i] * 3 * (far[i].nr + far[i].nc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)c);
 }
 
 }  // namespace
@@ -803,10 +824,10 @@ int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, const bem_opts& o, 
   if (ctx->profiling && nf) {
     ctx->prof_aca_blocks += (long long)nf;
     if (warm) {
-      std::vector<int> dn(nf);
-      BEM_CUDA_TRY(cudaMemcpyAsync(dn.data(), ctx->aca_done.p, nf * sizeof(int), cudaMemcpyDeviceToHost, st));
-      BEM_CUDA_TRY(cudaStreamSynchronize(st));
-      for (size_t b = 0; b < nf; ++b) ctx->prof_aca_continued += dn[b] ? 0 : 1;
+      count_if(true);
+      k_count_zero<<<std::min<int>(64, ((int)nf + 255) / 256), 256, 0, st>>>(ctx->aca_done.p, (int)nf,
+                                                                              ctx->prof_dev.p);
+      CK("count stepped");
     } else {
       ctx->prof_aca_continued += (long long)nf;
     }
@@ -896,17 +917,21 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
     CK("near_regular");
   }
   BEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
-  prof_end(ctx, ev, 1, 0.0);
+  prof_end(ctx, ev, 1);
   ctx->assembled = true;
   ctx->s_re = sre;
   ctx->s_im = sim;
   if (ctx->profiling) {
-    std::vector<int> rk(nf);
-    if (nf) BEM_CUDA_TRY(cudaMemcpyAsync(rk.data(), ctx->rank.p, nf * sizeof(int), cudaMemcpyDeviceToHost, st));
-    BEM_CUDA_TRY(cudaStreamSynchronize(st));
-    long long u = 0;
-    for (size_t b = 0; b < nf; ++b) u += (long long)rk[b] * 3 * (ctx->far_h[b].nr + ctx->far_h[b].nc);
-    ctx->used_lowrank = u;
+    // low-rank entries in use after this assembly, counted on the device
+    ctx->prof_slot = std::min(ctx->prof_nslots + 1, PROF_SLOTS - 1);
+    ctx->prof_nslots = ctx->prof_slot;
+    BEM_CUDA_TRY(cudaMemsetAsync(ctx->prof_dev.p + ctx->prof_slot, 0, sizeof(long long), st));
+    if (nf) {
+      count_if(true);
+      k_lowrank_entries<<<std::min<int>(64, ((int)nf + 255) / 256), 256, 0, st>>>(ctx->rank.p, ctx->far_d.p, (int)nf,
+                                                                                  ctx->prof_dev.p + ctx->prof_slot);
+      CK("count low-rank entries");
+    }
     prof_harvest(ctx);
   }
   return BEM_OK;
@@ -922,7 +947,7 @@ int apply64(bem_ctx* ctx, const c128* x, c128* y, int nrhs) {
     launch_hmatvec<c128, c128, c128, double>(ctx, ctx->near64.p, ctx->u64.p, ctx->v64.p,
                                              reinterpret_cast<cplx<double>*>(ctx->t64.p), x, y, nrhs, ctx->stream);
   CK("hmatvec64");
-  prof_end(ctx, ev, 0, hmv_bytes(ctx, is_mixed(ctx) ? 8 : 16, 16, 16, nrhs, ctx->used_lowrank));
+  prof_end_hmv(ctx, ev, is_mixed(ctx) ? 8 : 16, 16, 16, nrhs);
   return BEM_OK;
 }
 
@@ -943,7 +968,7 @@ int apply_fast(bem_ctx* ctx, const c128* x, c128* y, int nrhs) {
   launch_hmatvec<c64, c64, c128, float>(ctx, ctx->near32.p, ctx->u32.p, ctx->v32.p,
                                         reinterpret_cast<cplx<float>*>(ctx->t32.p), ctx->w32.p, y, nrhs, ctx->stream);
   CK("hmatvec_fast");
-  prof_end(ctx, ev, 0, hmv_bytes(ctx, 8, 8, 16, nrhs, ctx->used_lowrank));
+  prof_end_hmv(ctx, ev, 8, 8, 16, nrhs);
   return BEM_OK;
 }
 
@@ -1079,7 +1104,7 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
                                                reinterpret_cast<const c128*>(zbuf.p),
                                                reinterpret_cast<c128*>(wbuf.p), 1, st);
     CK("arnoldi matvec");
-    prof_end(ctx, ev, 0, hmv_bytes(ctx, sizeof(Vb), sizeof(Vb), sizeof(Vb), 1, ctx->used_lowrank));
+    prof_end_hmv(ctx, ev, sizeof(Vb), sizeof(Vb), sizeof(Vb), 1);
     BEM_CUDA_TRY(launch_arnoldi_orth<Vb>(V, N, j, wbuf.p, N, orth_part, hd, m, st));
     CK("arnoldi");
     BEM_CUDA_TRY(cudaMemcpyAsync(hcol + 2 * j * slot_len, hd, slot_len * sizeof(c128), cudaMemcpyDeviceToHost, st));
@@ -1695,8 +1720,25 @@ extern "C" int bem_set_profiling(bem_ctx* ctx, int on) {
   prof_harvest(ctx);
   ctx->profiling = on != 0;
   ctx->prof_hmv_launches = ctx->prof_asm_calls = 0;
-  ctx->prof_hmv_ms = ctx->prof_hmv_bytes = ctx->prof_asm_ms = 0;
+  ctx->prof_hmv_ms = ctx->prof_asm_ms = 0;
   ctx->prof_aca_blocks = ctx->prof_aca_continued = 0;
+  ctx->prof_products.clear();
+  ctx->prof_slot = ctx->prof_nslots = 0;
+  if (ctx->profiling) {
+    BEM_CUDA_TRY(ctx->prof_dev.ensure(PROF_SLOTS));
+    BEM_CUDA_TRY(cudaMemsetAsync(ctx->prof_dev.p, 0, PROF_SLOTS * sizeof(long long), ctx->stream));
+    if (ctx->assembled) {
+      // the operator assembled before profiling began is slot 1
+      ctx->prof_slot = ctx->prof_nslots = 1;
+      const int nf = (int)ctx->far_h.size();
+      if (nf) {
+        count_if(true);
+        k_lowrank_entries<<<std::min<int>(64, (nf + 255) / 256), 256, 0, ctx->stream>>>(ctx->rank.p, ctx->far_d.p,
+                                                                                       nf, ctx->prof_dev.p + 1);
+      }
+      BEM_CUDA_TRY(cudaGetLastError());
+    }
+  }
   ctx->launches_at_reset = launch_count();
   return BEM_OK;
 }
@@ -1737,13 +1779,18 @@ extern "C" int bem_get_profile(bem_ctx* ctx, bem_profile* out) {
   TRY(set_device(ctx));
   BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   prof_harvest(ctx);
+  std::vector<long long> lr(std::max(1, ctx->prof_nslots + 1), 0);
+  if (ctx->prof_dev.p && ctx->prof_nslots + 1 > 0)
+    BEM_CUDA_TRY(cudaMemcpy(lr.data(), ctx->prof_dev.p, lr.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+  double bytes = 0;
+  for (const auto& d : ctx->prof_products) bytes += d.base + d.mult * (d.slot > 0 ? (double)lr[d.slot] : 0.0);
   out->hmv_launches = ctx->prof_hmv_launches;
   out->hmv_ms = ctx->prof_hmv_ms;
-  out->hmv_bytes = ctx->prof_hmv_bytes;
+  out->hmv_bytes = bytes;
   out->assemble_calls = ctx->prof_asm_calls;
   out->assemble_ms = ctx->prof_asm_ms;
   out->kernel_launches = launch_count() - ctx->launches_at_reset;
   out->aca_blocks = ctx->prof_aca_blocks;
-  out->aca_stepped = ctx->prof_aca_continued;
+  out->aca_stepped = ctx->prof_aca_continued + (ctx->prof_dev.p ? lr[0] : 0);
   return BEM_OK;
 }

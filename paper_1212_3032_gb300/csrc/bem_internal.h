@@ -236,15 +236,25 @@ struct bem_ctx {
   bool profiling = false;
   struct Pending {
     cudaEvent_t a, b;
-    double bytes;
-    int kind;  // 0 H-matrix product, 1 assembly
+    double base, mult;  // bytes = base + mult x (low-rank entries in use at slot)
+    int slot;           // assembly slot of prof_dev holding those entries (0: none)
+    int kind;           // 0 H-matrix product, 1 assembly
   };
   std::vector<Pending> pending;
+  // profiling counters kept on the device, so that profiling adds no host
+  // synchronisation: prof_dev[0] = blocks that took ACA steps after reuse,
+  // prof_dev[s] (s >= 1) = low-rank entries in use after the s-th assembly
+  bem::DevBuf<long long> prof_dev;
+  int prof_slot = 0, prof_nslots = 0;
+  struct DoneProduct {
+    double base, mult;
+    int slot;
+  };
+  std::vector<DoneProduct> prof_products;  // timed products awaiting their byte counts
   std::vector<cudaEvent_t> event_pool;
   long long prof_hmv_launches = 0, prof_asm_calls = 0;
-  long long used_lowrank = 0;
-  long long launches_at_reset = 0;  // sum_b rank_b (3 nr_b + 3 nc_b) after the last ACA
-  double prof_hmv_ms = 0, prof_hmv_bytes = 0, prof_asm_ms = 0;
+  long long launches_at_reset = 0;  // library kernel launches counted when profiling was (re)enabled
+  double prof_hmv_ms = 0, prof_asm_ms = 0;
 
   // learned initial guess
   bem::MlpState* mlp = nullptr;
