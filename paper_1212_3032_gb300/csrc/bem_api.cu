@@ -246,17 +246,41 @@ cudaEvent_t take_event(bem_ctx* ctx) {
 }
 
 // Records the start of a timed region (returns the event or null).
-cudaEvent_t prof_begin(bem_ctx* ctx) {
+cudaEvent_t prof_begin(bem_ctx* ctx, cudaStream_t st = nullptr) {
   if (!ctx->profiling) return nullptr;
   cudaEvent_t a = take_event(ctx);
-  cudaEventRecord(a, ctx->stream);
+  cudaEventRecord(a, st ? st : ctx->stream);
   return a;
 }
-void prof_end(bem_ctx* ctx, cudaEvent_t a, int kind, double base = 0.0, double mult = 0.0) {
+void prof_end(bem_ctx* ctx, cudaEvent_t a, int kind, double base = 0.0, double mult = 0.0, cudaStream_t st = nullptr) {
   if (!a) return;
   cudaEvent_t b = take_event(ctx);
-  cudaEventRecord(b, ctx->stream);
+  cudaEventRecord(b, st ? st : ctx->stream);
   ctx->pending.push_back({a, b, base, mult, kind == 0 ? ctx->prof_slot : 0, kind});
+}
+
+// Exchanges the operator set in use with the other one (host pointers only:
+// work already enqueued keeps the buffers it was given).
+template <typename T> void swap_buf(DevBuf<T>& a, DevBuf<T>& b) {
+  std::swap(a.p, b.p);
+  std::swap(a.n, b.n);
+}
+void swap_ops(bem_ctx* ctx) {
+  OpSet& o = ctx->back;
+  swap_buf(ctx->near32, o.near32);
+  swap_buf(ctx->u32, o.u32);
+  swap_buf(ctx->v32, o.v32);
+  swap_buf(ctx->prec_inv32, o.prec_inv32);
+  swap_buf(ctx->near64, o.near64);
+  swap_buf(ctx->u64, o.u64);
+  swap_buf(ctx->v64, o.v64);
+  swap_buf(ctx->prec_inv, o.prec_inv);
+  swap_buf(ctx->b64, o.b64);
+  swap_buf(ctx->rank, o.rank);
+  swap_buf(ctx->aca_fail, o.aca_fail);
+  swap_buf(ctx->status, o.status);
+  std::swap(ctx->near_zero_pending, o.near_zero_pending);
+  std::swap(ctx->prof_slot, o.prof_slot);
 }
 // Folds completed timings into the counters; timings whose end event has not
 // completed yet stay pending (after a stream sync every one has completed).
@@ -358,8 +382,10 @@ extern "C" int bem_create(bem_ctx** out, int device, void* stream) {
     return BEM_ERR_OOM;
   }
   if (cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->asm_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_asm_done, cudaEventDisableTiming) != cudaSuccess) {
     bem_destroy(ctx);
     return BEM_ERR_CUDA;
   }
@@ -378,8 +404,13 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
     cudaStreamSynchronize(ctx->aux_stream);
     cudaStreamDestroy(ctx->aux_stream);
   }
+  if (ctx->asm_stream) {
+    cudaStreamSynchronize(ctx->asm_stream);
+    cudaStreamDestroy(ctx->asm_stream);
+  }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_asm_done) cudaEventDestroy(ctx->ev_asm_done);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -488,6 +519,7 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   }
   ctx->near_entries = noff;
   ctx->near_zero_pending = true;
+  ctx->back.near_zero_pending = true;  // the other operator set's padding rows too
   long long uoff = 0, voff = 0;
   int toff = 0;
   for (const BlockPair& bp : tr.far) {
@@ -838,11 +870,10 @@ int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, const bem_opts& o, 
 
 // Operator at s: right-hand side contributions optional (pattern/b may be null).
 int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const double* pattern_tree,
-                  c128 pk, c128* b) {
-  cudaStream_t st = ctx->stream;
+                  c128 pk, c128* b, cudaStream_t st) {
   TRY(ensure_static(ctx, o.precision == BEM_PREC_C128));
   ctx->prec = o.precision;
-  cudaEvent_t ev = prof_begin(ctx);
+  cudaEvent_t ev = prof_begin(ctx, st);
   size_t nf = ctx->far_h.size();
   BEM_CUDA_TRY(ctx->rank.ensure(std::max<size_t>(1, nf)));
   BEM_CUDA_TRY(ctx->aca_fail.ensure(1));
@@ -917,7 +948,7 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
     CK("near_regular");
   }
   BEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
-  prof_end(ctx, ev, 1);
+  prof_end(ctx, ev, 1, 0.0, 0.0, st);
   ctx->assembled = true;
   ctx->s_re = sre;
   ctx->s_im = sim;
@@ -1288,7 +1319,7 @@ extern "C" int bem_assemble(bem_ctx* ctx, double s_re, double s_im, const bem_op
   bem_opts o = ctx->mesh_opts;
   if (opts) o = *opts;
   if (!(s_re >= 0) || !std::isfinite(s_im)) return fail(ctx, BEM_ERR_INVALID_ARG, "need Re(s) >= 0");
-  TRY(assemble_impl(ctx, s_re, s_im, o, nullptr, c128{0, 0}, nullptr));
+  TRY(assemble_impl(ctx, s_re, s_im, o, nullptr, c128{0, 0}, nullptr, ctx->stream));
   BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return BEM_OK;
 }
@@ -1534,16 +1565,34 @@ static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_de
   const double dw = 2.0 * M_PI / T;
   const double dt = T / n_omega;
   int worst = BEM_OK;
-  Timer t0, t1, t2;
+  Timer ta[2], t1, t2;  // ta: assembly of frequency k in ta[k & 1]
+  // frequency 0 on the caller's stream; afterwards frequency k + 1 is
+  // assembled on asm_stream into the other operator set while the guess and
+  // GMRES of frequency k run on the caller's stream
+  cudaEventRecord(ta[0].a, st);
+  TRY(assemble_impl(ctx, ctx->eta, 0.0, o, ctx->pattern.p, ctx->Pk_host[0], ctx->b64.p, st));
+  cudaEventRecord(ta[0].b, st);
+  BEM_CUDA_TRY(cudaEventRecord(ctx->ev_asm_done, st));
   for (int k = 0; k < nf; ++k) {
     bem_freq_stats s{};
     s.k = k;
     s.s_re = ctx->eta;
     s.s_im = k * dw;
     c128* xk = ctx->sol.p + (long long)k * N;
-    cudaEventRecord(t0.a, st);
-    TRY(assemble_impl(ctx, s.s_re, s.s_im, o, ctx->pattern.p, ctx->Pk_host[k], ctx->b64.p));
-    cudaEventRecord(t0.b, st);
+    const bool next = k + 1 < nf;
+    if (next) {
+      // the other set was last used by frequency k - 1, which the host has
+      // seen complete (stream synchronised at the end of its iteration)
+      swap_ops(ctx);
+      BEM_CUDA_TRY(ctx->b64.ensure(N));
+      cudaStream_t as = ctx->asm_stream;
+      BEM_CUDA_TRY(cudaStreamWaitEvent(as, ctx->ev_asm_done, 0));  // keeps assemblies in order
+      cudaEventRecord(ta[(k + 1) & 1].a, as);
+      TRY(assemble_impl(ctx, ctx->eta, (k + 1) * dw, o, ctx->pattern.p, ctx->Pk_host[k + 1], ctx->b64.p, as));
+      cudaEventRecord(ta[(k + 1) & 1].b, as);
+      BEM_CUDA_TRY(cudaEventRecord(ctx->ev_asm_done, as));
+      swap_ops(ctx);
+    }
     cudaEventRecord(t1.a, st);
     int K = (o.guess != BEM_GUESS_ZERO) ? std::min(k, std::max(0, std::min(o.sem_k, 4))) : 0;
     const c128* prev[4] = {};
@@ -1569,7 +1618,7 @@ static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_de
     BEM_CUDA_TRY(cudaMemcpyAsync(&fails, ctx->aca_fail.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     BEM_CUDA_TRY(cudaStreamSynchronize(st));
     float ms;
-    cudaEventElapsedTime(&ms, t0.a, t0.b);
+    cudaEventElapsedTime(&ms, ta[k & 1].a, ta[k & 1].b);
     s.assemble_ms = ms;
     cudaEventElapsedTime(&ms, t1.a, t1.b);
     s.guess_ms = ms;
@@ -1579,6 +1628,11 @@ static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_de
     s.near_bytes = ctx->near_entries * (is_mixed(ctx) ? 8 : 16);
     if (stats) stats[k] = s;
     ctx->nf = k + 1;
+    if (next) {
+      // frequency k + 1's operator and right-hand side become the set in use
+      BEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_asm_done, 0));
+      swap_ops(ctx);
+    }
   }
   if (stats && !ctx->far_h.empty()) {
     std::vector<int> rk(ctx->far_h.size());

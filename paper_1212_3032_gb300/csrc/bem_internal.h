@@ -123,6 +123,17 @@ long long launch_count();
 
 struct MlpState;  // learned initial guess (bem_mlp.cu)
 
+// The storage of one assembled operator and its right-hand side. A sweep
+// keeps two: frequency k + 1 is assembled into one while GMRES runs on the
+// other (the context's fields hold the set in use; swap_ops exchanges them).
+struct OpSet {
+  DevBuf<c64> near32, u32, v32, prec_inv32;
+  DevBuf<c128> near64, u64, v64, prec_inv, b64;
+  DevBuf<int> rank, aca_fail, status;
+  bool near_zero_pending = true;
+  int prof_slot = 0;
+};
+
 // Host-side rule tables (Gauss-Legendre on [0,1], series coefficients).
 void make_rule_tables(RuleTables& t);
 
@@ -174,6 +185,9 @@ struct bem_ctx {
   bem::DevBuf<int> task_order;        // task indices by size, largest first (launch order)
   cudaStream_t aux_stream = nullptr;  // the far-field assembly runs here, joined back to stream
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t asm_stream = nullptr;  // a sweep assembles frequency k + 1 here while GMRES(k) runs
+  cudaEvent_t ev_asm_done = nullptr;
+  bem::OpSet back;                    // the operator set not in use (see swap_ops)
   bem::DevBuf<int> leaf_cnt;          // per leaf: tasks completed in the current product (reset to 0 after it)
   bem::DevBuf<int> task_ptr;          // CSR of tasks over leaves
   bem::DevBuf<double> part;           // partial sums (sized for 4 rhs of complex FP64)
