@@ -944,20 +944,45 @@ __global__ void __launch_bounds__(256) k_rhs_far(const int* __restrict__ rng, co
 // (three columns); aca_col3: column component jc of element je against
 // collocation element i (three rows).
 // ---------------------------------------------------------------------------
+// One line of a pair's block over the band's rule (one inlined evaluator).
+template <typename R>
+__device__ __forceinline__ void regular_pair_line(cplx<R> out[3], const PairGeo<R>& g, int band, const KParams<R>& P,
+                                                  bool useT, bool col, int idx) {
+  out[0] = out[1] = out[2] = mk<R>(0, 0);
+  const int Q = band == BAND_Q4 ? 4 : (band == BAND_Q2 ? 2 : 1);
+#pragma unroll 1
+  for (int p = 0; p < Q * Q; ++p) {
+    R rx, ry, rz, w;
+    if (Q == 1) {
+      rx = g.d[0];
+      ry = g.d[1];
+      rz = g.d[2];
+      w = R(0.5) * g.area2;
+    } else {
+      const int a = p / Q, b = p - (p / Q) * Q;
+      const R u = gl_x<R>(Q, a);
+      const R omu = R(1) - u;
+      const R v = omu * gl_x<R>(Q, b);
+      w = g.area2 * gl_w<R>(Q, a) * gl_w<R>(Q, b) * omu;
+      rx = g.o0[0] + u * g.e1[0] + v * g.e2[0];
+      ry = g.o0[1] + u * g.e1[1] + v * g.e2[1];
+      rz = g.o0[2] + u * g.e1[2] + v * g.e2[2];
+    }
+    accumulate_point_line<R>(out, rx, ry, rz, g.n[0], g.n[1], g.n[2], w, P, useT, col, idx);
+  }
+}
+
 template <typename R, typename T>
 __device__ __forceinline__ void aca_row3(const ElemF* ef, const ElemD* ed, const signed char* bc,
                                          const KParams<R>& P, int ie, int ia, int e, cplx<T> out[3]) {
   PairGeo<R> g;
   int band;
   pair_geo(ef, ed, ie, e, g, band);
-  UTAcc<R> acc;
-  regular_pair<R>(acc, g, band, P);
-  bool trac = bc[e] == BEM_BC_TRACTION;
+  const bool trac = bc[e] == BEM_BC_TRACTION;
+  cplx<R> v[3];
+  regular_pair_line<R>(v, g, band, P, trac, false, ia);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    cplx<R> v = trac ? acc.t[3 * ia + c] : -acc.U(ia, c);
-    out[c] = mk<T>(T(v.re), T(v.im));
-  }
+  for (int c = 0; c < 3; ++c) out[c] = trac ? mk<T>(T(v[c].re), T(v[c].im)) : mk<T>(T(-v[c].re), T(-v[c].im));
 }
 template <typename R, typename T>
 __device__ __forceinline__ void aca_col3(const ElemF* ef, const ElemD* ed, const signed char* bc,
@@ -965,14 +990,11 @@ __device__ __forceinline__ void aca_col3(const ElemF* ef, const ElemD* ed, const
   PairGeo<R> g;
   int band;
   pair_geo(ef, ed, i, je, g, band);
-  UTAcc<R> acc;
-  regular_pair<R>(acc, g, band, P);
-  bool trac = bc[je] == BEM_BC_TRACTION;
+  const bool trac = bc[je] == BEM_BC_TRACTION;
+  cplx<R> v[3];
+  regular_pair_line<R>(v, g, band, P, trac, true, jc);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    cplx<R> v = trac ? acc.t[3 * a + jc] : -acc.U(a, jc);
-    out[a] = mk<T>(T(v.re), T(v.im));
-  }
+  for (int a = 0; a < 3; ++a) out[a] = trac ? mk<T>(T(v[a].re), T(v[a].im)) : mk<T>(T(-v[a].re), T(-v[a].im));
 }
 
 // ---------------------------------------------------------------------------

@@ -156,6 +156,54 @@ __device__ __forceinline__ void accumulate_point(UTAcc<R>& acc, R rx, R ry, R rz
   }
 }
 
+// One line of the 3x3 pair block at one quadrature point: row idx (col = false:
+// entries (idx, c), c < 3) or column idx (col = true: entries (a, idx)) of T
+// (useT) or of U. ACA steps need one scalar row or column of the system
+// matrix, i.e. one line of each pair's block; the radial functions are shared,
+// the rest of the tensor is not formed.
+template <typename R>
+__device__ __forceinline__ void accumulate_point_line(cplx<R> out[3], R rx, R ry, R rz, R nx, R ny, R nz, R w,
+                                                      const KParams<R>& P, bool useT, bool col, int idx) {
+  R r2 = rx * rx + ry * ry + rz * rz;
+  R r = sqrt(r2);
+  R ir = R(1) / r;
+  R h[3] = {rx * ir, ry * ir, rz * ir};
+  R n[3] = {nx, ny, nz};
+  cplx<R> Phi, Psi, A, B, C;
+  radial5<R, true>(r, P, Phi, Psi, A, B, C);
+  const R hi = idx == 0 ? h[0] : (idx == 1 ? h[1] : h[2]);
+  if (useT) {
+    R rn = h[0] * nx + h[1] * ny + h[2] * nz;
+    R tw = P.t_scale * w * ir * ir;
+    cplx<R> a = A * tw;
+    cplx<R> brn = B * (tw * rn);
+    cplx<R> c = C * tw;
+    cplx<R> arn = a * rn;
+    const R ni = idx == 0 ? n[0] : (idx == 1 ? n[1] : n[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      // (i, j) = (idx, k) for a row, (k, idx) for a column
+      const R hI = col ? h[k] : hi, hJ = col ? hi : h[k];
+      const R nI = col ? n[k] : ni, nJ = col ? ni : n[k];
+      cplx<R>& t = out[k];
+      if (k == idx) t = t + arn;
+      cfmr(t, a, nI * hJ);
+      cfmr(t, brn, hI * hJ);
+      cfmr(t, c, hI * nJ);
+    }
+  } else {
+    R uw = P.u_scale * w * ir;
+    cplx<R> cd = Phi * uw;
+    cplx<R> cr = Psi * (-uw);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cplx<R>& u = out[k];
+      if (k == idx) u = u + cd;
+      cfmr(u, cr, hi * h[k]);  // U is symmetric: row and column lines agree
+    }
+  }
+}
+
 // U only (6 entries), full kernel: for right-hand sides of traction-loaded
 // elements, where T is not needed.
 template <typename R>
