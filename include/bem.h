@@ -71,6 +71,14 @@ extern "C" {
                            plus one learned proposal column (bem_mlp_*); the
                            paper has no learned guess */
 
+/* storage of the far-field factors (bem_set_far_storage) */
+#define BEM_FAR_AUTO 0    /* full when both operator sets' capped factors take at
+                             most a quarter of the device memory, else compact */
+#define BEM_FAR_FULL 1    /* every block's U, V at its rank cap, ACA writes in place */
+#define BEM_FAR_COMPACT 2 /* ACA in a workspace batch by batch, factors packed at
+                             their actual ranks; one operator set (no overlap of
+                             the next frequency's assembly with the solve) */
+
 typedef struct bem_ctx bem_ctx;
 
 typedef struct bem_opts {
@@ -242,6 +250,32 @@ int bem_set_aca_reuse(bem_ctx* ctx, int on);
  * when the last assembly did not reuse pivots). nmax = 0 queries the count.
  * Errors: STATE (not assembled). */
 int bem_far_block_info(bem_ctx* ctx, int64_t nmax, int32_t* info, int64_t* count);
+
+/* Far-field factor storage of the meshes set after this call (mode
+ * BEM_FAR_AUTO, _FULL or _COMPACT). The admissible blocks' factors at their
+ * rank caps (3 min(rows, cols) elements, at most 128 columns) need
+ * 3 (rows + cols) x cap complex entries per block: at 231k elements that is
+ * 374 GB in complex64, though ACA stops at a fraction of the cap. Compact
+ * storage runs ACA over consecutive runs of blocks (batches) whose capped
+ * factors fit a workspace of `workspace_bytes` (0: 8 GiB for complex64,
+ * 16 GiB for complex128, raised to the largest block when smaller) and
+ * packs each block's first `rank` columns of U and V into pools that grow
+ * by a quarter over the need when an assembly overflows them (the assembly
+ * is then redone from the same pivot state, so the result does not depend
+ * on the pools' history). Both storages give bit-identical operators.
+ * Errors: INVALID_ARG. */
+int bem_set_far_storage(bem_ctx* ctx, int32_t mode, int64_t workspace_bytes);
+
+typedef struct bem_far_storage {
+  int32_t compact;          /* storage of the current mesh: 1 compact, 0 full */
+  int32_t batches;          /* ACA batches per assembly */
+  int64_t workspace_bytes;  /* compact: workspace allocated for the last assembly */
+  int64_t factor_bytes;     /* U and V storage allocated for the set in use */
+  int64_t used_bytes;       /* U and V bytes of the last assembly's ranks */
+  int32_t regrows;          /* compact: assemblies redone after a pool overflow */
+  int32_t reserved;
+} bem_far_storage;
+int bem_get_far_storage(bem_ctx* ctx, bem_far_storage* out);
 
 /* ---- learned initial guess (BEM_GUESS_MLP) ---------------------------------
  * The paper's extrapolation (Sec. 4.2) fits a_k^(0) in the span of the last

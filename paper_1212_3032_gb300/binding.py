@@ -22,6 +22,7 @@ BC_TRACTION, BC_DISPLACEMENT = 0, 1
 WIN_NONE, WIN_HANNING, WIN_BLACKMAN = 0, 1, 2
 PREC_C64_MIXED, PREC_C128 = 0, 1
 GUESS_ZERO, GUESS_SEM, GUESS_MLP = 0, 1, 2
+FAR_AUTO, FAR_FULL, FAR_COMPACT = 0, 1, 2
 
 EXPORTED = [
     "bem_default_opts", "bem_create", "bem_destroy", "bem_last_error", "bem_mesh", "bem_mesh_dev",
@@ -31,7 +32,7 @@ EXPORTED = [
     "bem_set_profiling", "bem_get_profile", "bem_apply_noalloc",
     "bem_mlp_num_params", "bem_mlp_init", "bem_mlp_set_training", "bem_mlp_set_weights", "bem_mlp_get_weights",
     "bem_mlp_forward", "bem_mlp_gradient", "bem_mlp_train_step", "bem_set_aca_reuse",
-    "bem_far_block_info",
+    "bem_far_block_info", "bem_set_far_storage", "bem_get_far_storage",
 ]
 
 
@@ -68,6 +69,15 @@ class Profile(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class FarStorage(ctypes.Structure):
+    _fields_ = [("compact", ctypes.c_int32), ("batches", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
+                ("factor_bytes", ctypes.c_int64), ("used_bytes", ctypes.c_int64), ("regrows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
 _lib = None
@@ -109,6 +119,8 @@ def load_library(path: str = LIB_PATH):
         "bem_get_profile": (ctypes.c_int, [P, ctypes.POINTER(Profile)]),
         "bem_set_aca_reuse": (ctypes.c_int, [P, ctypes.c_int]),
         "bem_far_block_info": (ctypes.c_int, [P, I64, P, P]),
+        "bem_set_far_storage": (ctypes.c_int, [P, ctypes.c_int32, I64]),
+        "bem_get_far_storage": (ctypes.c_int, [P, P]),
         "bem_mlp_num_params": (I64, []),
         "bem_mlp_init": (ctypes.c_int, [P, ctypes.c_uint64]),
         "bem_mlp_set_training": (ctypes.c_int, [P, I32, D]),
@@ -385,6 +397,15 @@ class Context:
         if n.value:
             self._check(self.lib.bem_far_block_info(self.h, n.value, _ptr(info), ctypes.byref(n)))
         return info
+
+    def set_far_storage(self, mode: int, workspace_bytes: int = 0):
+        """Factor storage (FAR_AUTO / FAR_FULL / FAR_COMPACT) of the meshes set after this call."""
+        self._check(self.lib.bem_set_far_storage(self.h, int(mode), int(workspace_bytes)))
+
+    def far_storage(self):
+        f = FarStorage()
+        self._check(self.lib.bem_get_far_storage(self.h, ctypes.byref(f)))
+        return f.as_dict()
 
     def get_profile(self):
         p = Profile()

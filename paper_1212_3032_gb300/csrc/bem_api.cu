@@ -279,6 +279,8 @@ void swap_ops(bem_ctx* ctx) {
   swap_buf(ctx->rank, o.rank);
   swap_buf(ctx->aca_fail, o.aca_fail);
   swap_buf(ctx->status, o.status);
+  swap_buf(ctx->fbase, o.fbase);
+  std::swap(ctx->fbase_ready, o.fbase_ready);
   std::swap(ctx->near_zero_pending, o.near_zero_pending);
   std::swap(ctx->prof_slot, o.prof_slot);
 }
@@ -452,6 +454,9 @@ extern "C" int bem_set_window(bem_ctx* ctx, double eta, int window) {
 // ---------------------------------------------------------------------------
 // mesh
 // ---------------------------------------------------------------------------
+// Admissible blocks assembled one warp each (the others one CTA each).
+static bool far_small_class(const FarBlk& fb) { return fb.nr + fb.nc <= 256; }
+
 static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int* tri_d, int ne,
                      const signed char* bc_d, const bem_opts* opts) {
   cudaStream_t st = ctx->stream;
@@ -520,7 +525,7 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   ctx->near_entries = noff;
   ctx->near_zero_pending = true;
   ctx->back.near_zero_pending = true;  // the other operator set's padding rows too
-  long long uoff = 0, voff = 0;
+  long long ucap = 0, vcap = 0, bigcap = 0;
   int toff = 0;
   for (const BlockPair& bp : tr.far) {
     const Cluster& t = tr.nodes[bp.tau];
@@ -532,17 +537,75 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
     fb.nc = s.size();
     int mn = 3 * std::min(fb.nr, fb.nc);
     fb.rmax = std::min(mn, 128);
-    fb.uoff = uoff;
-    fb.voff = voff;
     fb.toff = toff;
-    uoff += 3LL * fb.nr * fb.rmax;
-    voff += 3LL * fb.nc * fb.rmax;
+    ucap += 3LL * fb.nr * fb.rmax;
+    vcap += 3LL * fb.nc * fb.rmax;
+    bigcap = std::max(bigcap, 3LL * std::max(fb.nr, fb.nc) * fb.rmax);
     toff += fb.rmax;
     ctx->far_h.push_back(fb);
   }
-  ctx->u_entries = uoff;
-  ctx->v_entries = voff;
+  ctx->u_entries = ucap;
+  ctx->v_entries = vcap;
   ctx->t_entries = toff;
+  // factor storage: full (capped factors in place, two operator sets) unless
+  // that would take over a quarter of the device memory, or compact is asked for
+  {
+    size_t freeb = 0, totalb = 0;
+    BEM_CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
+    const double esz = o.precision == BEM_PREC_C128 ? 16.0 : 8.0;
+    const double full_bytes = 2.0 * (double)(ucap + vcap) * esz;
+    ctx->far_compact = ctx->far_mode_req == BEM_FAR_COMPACT ||
+                       (ctx->far_mode_req == BEM_FAR_AUTO && full_bytes > 0.25 * (double)totalb);
+    const long long ws_total = ctx->far_ws_req > 0 ? ctx->far_ws_req / 16 : (1LL << 30);
+    const long long half = ctx->far_compact ? std::max(ws_total / 2, bigcap) : 0;
+    ctx->ws_entries = half;
+    ctx->far_batches.clear();
+    FarBatch cur{0, 0, 0, 0, 0, 0};
+    long long cu = 0, cv = 0;
+    int ns = 0, nl = 0;
+    const int nfb = (int)ctx->far_h.size();
+    for (int b = 0; b < nfb; ++b) {
+      FarBlk& fb = ctx->far_h[b];
+      const long long nu = 3LL * fb.nr * fb.rmax, nvv = 3LL * fb.nc * fb.rmax;
+      if (ctx->far_compact && b > cur.b0 && (cu + nu > half || cv + nvv > half)) {
+        cur.b1 = b;
+        cur.s1 = ns;
+        cur.l1 = nl;
+        ctx->far_batches.push_back(cur);
+        cur = FarBatch{b, 0, ns, 0, nl, 0};
+        cu = cv = 0;
+      }
+      fb.uoff = cu;
+      fb.voff = cv;
+      cu += nu;
+      cv += nvv;
+      (far_small_class(fb) ? ns : nl) += 1;
+    }
+    if (nfb) {
+      cur.b1 = nfb;
+      cur.s1 = ns;
+      cur.l1 = nl;
+      ctx->far_batches.push_back(cur);
+    }
+    // a new mesh invalidates both sets' factor offsets; the set not in use
+    // gives back its operator storage (it is reallocated when next used)
+    ctx->fbase_ready = false;
+    ctx->back.fbase_ready = false;
+    ctx->back.near32.release();
+    ctx->back.u32.release();
+    ctx->back.v32.release();
+    ctx->back.near64.release();
+    ctx->back.u64.release();
+    ctx->back.v64.release();
+    if (ctx->far_compact) {
+      // pools are sized by the first assembly's need
+      ctx->u32.release();
+      ctx->v32.release();
+      ctx->u64.release();
+      ctx->v64.release();
+    }
+    ctx->far_regrows = 0;
+  }
   BEM_CUDA_TRY(ctx->near_d.alloc(std::max<size_t>(1, ctx->near_h.size())));
   BEM_CUDA_TRY(ctx->far_d.alloc(std::max<size_t>(1, ctx->far_h.size())));
   if (!ctx->near_h.empty())
@@ -581,17 +644,17 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   }
   for (size_t b = 0; b < ctx->far_h.size(); ++b) {
     const FarBlk& fb = ctx->far_h[b];
-    // every leaf inside the row cluster gets the matching slice of U_b
-    for (int l = 0; l < L; ++l) {
-      if (r0[l] >= fb.r0 && r0[l] + nr[l] <= fb.r0 + fb.nr) {
-        Panel p;
-        p.data = fb.uoff + 3LL * (r0[l] - fb.r0);
-        p.ld = 3 * fb.nr;
-        p.ncols = 0;
-        p.xoff = (int)b;
-        p.kind = 1;
-        per[l].push_back(p);
-      }
+    // every leaf inside the row cluster (a run of consecutive leaves) gets
+    // the matching slice of U_b
+    int l = (int)(std::lower_bound(r0.begin(), r0.end(), fb.r0) - r0.begin());
+    for (; l < L && r0[l] + nr[l] <= fb.r0 + fb.nr; ++l) {
+      Panel p;
+      p.data = 3LL * (r0[l] - fb.r0);
+      p.ld = 3 * fb.nr;
+      p.ncols = 0;
+      p.xoff = (int)b;
+      p.kind = 1;
+      per[l].push_back(p);
     }
   }
   std::vector<int> pptr(L + 1, 0);
@@ -676,7 +739,7 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
     std::vector<int> sm_l, lg_l;
     for (size_t b = 0; b < ctx->far_h.size(); ++b) {
       const FarBlk& fb = ctx->far_h[b];
-      (fb.nr + fb.nc <= 256 ? sm_l : lg_l).push_back((int)b);
+      (far_small_class(fb) ? sm_l : lg_l).push_back((int)b);
     }
     ctx->nfar_small = (int)sm_l.size();
     ctx->nfar_large = (int)lg_l.size();
@@ -828,9 +891,13 @@ int check_ready(bem_ctx* ctx) {
 }
 
 // Far-field blocks at the current s: reuse of the previous assembly's pivots
-// where available, then ACA steps for every block not yet converged.
+// where available, then ACA steps for every block not yet converged, batch by
+// batch. Full storage: ACA writes the factors in place (U, V). Compact
+// storage: ACA writes each batch into the workspace halves ws, ws + ws_entries
+// and the batch is packed into the pools U, V (capU, capV entries).
 template <typename R, typename Op>
-int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, const bem_opts& o, cudaStream_t st) {
+int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, long long capU, long long capV, Op* ws,
+            const bem_opts& o, bool count, cudaStream_t st) {
   const size_t nf = ctx->far_h.size();
   BEM_CUDA_TRY(ctx->piv_i.ensure(std::max(1, ctx->t_entries)));
   BEM_CUDA_TRY(ctx->piv_j.ensure(std::max(1, ctx->t_entries)));
@@ -842,18 +909,32 @@ int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, const bem_opts& o, 
   const bool warm = ctx->aca_reuse && ctx->aca_warm_ok && nf > 0;
   ctx->aca_last_warm = warm;
   if (warm) {
-    BEM_CUDA_TRY((launch_aca_warm<R, Op>(ctx->far_d.p, (int)nf, ctx->ef.p, ctx->ed.p, ctx->bc.p, P, U, V,
-                                         ctx->rank.p, ctx->aca_npiv.p, ctx->piv_i.p, ctx->piv_j.p,
-                                         ctx->aca_kstart.p, ctx->aca_norm0.p, ctx->aca_done.p, o.aca_tol,
-                                         ctx->aca_tau, st)));
     S.kstart = ctx->aca_kstart.p;
     S.norm0 = ctx->aca_norm0.p;
     S.done = ctx->aca_done.p;
   }
-  launch_aca<R, Op>(ctx->far_d.p, ctx->far_small.p, ctx->nfar_small, ctx->far_large.p, ctx->nfar_large, ctx->ef.p,
-                    ctx->ed.p, ctx->bc.p, P, U, V, ctx->rank.p, ctx->aca_fail.p, o.aca_tol, S, st);
-  CK("aca");
-  if (ctx->profiling && nf) {
+  const bool compact = ctx->far_compact;
+  unsigned long long* cursor = reinterpret_cast<unsigned long long*>(ctx->fbase.p + 2 * nf);
+  if (compact && nf) BEM_CUDA_TRY(cudaMemsetAsync(cursor, 0, 2 * sizeof(unsigned long long), st));
+  Op* Uw = compact ? ws : U;
+  Op* Vw = compact ? ws + ctx->ws_entries : V;
+  for (const FarBatch& fb : ctx->far_batches) {
+    const int nb = fb.b1 - fb.b0;
+    if (warm)
+      BEM_CUDA_TRY((launch_aca_warm<R, Op>(ctx->far_d.p, fb.b0, nb, ctx->ef.p, ctx->ed.p, ctx->bc.p, P, Uw, Vw,
+                                           ctx->rank.p, ctx->aca_npiv.p, ctx->piv_i.p, ctx->piv_j.p,
+                                           ctx->aca_kstart.p, ctx->aca_norm0.p, ctx->aca_done.p, o.aca_tol,
+                                           ctx->aca_tau, st)));
+    launch_aca<R, Op>(ctx->far_d.p, ctx->far_small.p + fb.s0, fb.s1 - fb.s0, ctx->far_large.p + fb.l0,
+                      fb.l1 - fb.l0, ctx->ef.p, ctx->ed.p, ctx->bc.p, P, Uw, Vw, ctx->rank.p, ctx->aca_fail.p,
+                      o.aca_tol, S, st);
+    CK("aca");
+    if (compact) {
+      launch_far_pack<Op>(ctx->far_d.p, fb.b0, nb, ctx->rank.p, Uw, Vw, U, V, capU, capV, ctx->fbase.p, cursor, st);
+      CK("far pack");
+    }
+  }
+  if (count && ctx->profiling && nf) {
     ctx->prof_aca_blocks += (long long)nf;
     if (warm) {
       count_if(true);
@@ -865,6 +946,79 @@ int run_aca(bem_ctx* ctx, const KParams<R>& P, Op* U, Op* V, const bem_opts& o, 
     }
   }
   ctx->aca_warm_ok = true;
+  return BEM_OK;
+}
+
+constexpr int FAR_CUR_SLOT = 4088;  // pinned host slots (two int64) of the pool cursors
+
+// Compact storage: initial pool capacity (entries) of a factor whose capped
+// size is cap; the pools grow by a quarter over the need on overflow.
+static long long pool_initial(long long cap) { return std::max(1LL, cap / 6); }
+
+// Far field of one assembly in the precision Op, on the auxiliary stream:
+// storage, pivot-state snapshot (compact storage), ACA.
+template <typename R, typename Op>
+int far_field_begin(bem_ctx* ctx, const KParams<R>& P, DevBuf<Op>& U, DevBuf<Op>& V, DevBuf<Op>& ws,
+                    const bem_opts& o, cudaStream_t aux, cudaStream_t st) {
+  const size_t nf = ctx->far_h.size();
+  if (!ctx->far_compact) {
+    BEM_CUDA_TRY(U.ensure(std::max<long long>(1, ctx->u_entries)));
+    BEM_CUDA_TRY(V.ensure(std::max<long long>(1, ctx->v_entries)));
+  } else {
+    if (U.n == 0) BEM_CUDA_TRY(U.alloc(pool_initial(ctx->u_entries)));
+    if (V.n == 0) BEM_CUDA_TRY(V.alloc(pool_initial(ctx->v_entries)));
+    BEM_CUDA_TRY(ws.ensure(std::max<long long>(2, 2 * ctx->ws_entries)));
+    // the pivot state this assembly starts from, kept for a redo
+    ctx->far_was_ok = ctx->aca_warm_ok;
+    const long long nt = std::max(1, ctx->t_entries);
+    if (ctx->far_was_ok && nf) {
+      BEM_CUDA_TRY(ctx->piv_snap.ensure(2 * nt + (long long)nf));
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->piv_snap.p, ctx->piv_i.p, nt * sizeof(int), cudaMemcpyDeviceToDevice, st));
+      BEM_CUDA_TRY(
+          cudaMemcpyAsync(ctx->piv_snap.p + nt, ctx->piv_j.p, nt * sizeof(int), cudaMemcpyDeviceToDevice, st));
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->piv_snap.p + 2 * nt, ctx->aca_npiv.p, nf * sizeof(int),
+                                   cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  BEM_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
+  BEM_CUDA_TRY(cudaStreamWaitEvent(aux, ctx->ev_fork, 0));
+  TRY((run_aca<R, Op>(ctx, P, U.p, V.p, (long long)U.n, (long long)V.n, ws.p, o, true, aux)));
+  BEM_CUDA_TRY(cudaEventRecord(ctx->ev_join, aux));
+  return BEM_OK;
+}
+
+// Joins the far field into st. Compact storage: reads the pools' need; on an
+// overflow the pools grow to the need plus a quarter and the far field is
+// redone on st from the pivot state it started from (the same factors).
+template <typename R, typename Op>
+int far_field_finish(bem_ctx* ctx, const KParams<R>& P, DevBuf<Op>& U, DevBuf<Op>& V, DevBuf<Op>& ws,
+                     const bem_opts& o, cudaStream_t st) {
+  const size_t nf = ctx->far_h.size();
+  BEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+  if (!ctx->far_compact || !nf) return BEM_OK;
+  long long* hc = reinterpret_cast<long long*>(ctx->host_red + FAR_CUR_SLOT);
+  BEM_CUDA_TRY(cudaMemcpyAsync(hc, ctx->fbase.p + 2 * nf, 2 * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hc[0] <= (long long)U.n && hc[1] <= (long long)V.n) return BEM_OK;
+  ctx->far_regrows += 1;
+  const long long nu = std::min(ctx->u_entries, hc[0] + hc[0] / 4 + 1);
+  const long long nv = std::min(ctx->v_entries, hc[1] + hc[1] / 4 + 1);
+  if (hc[0] > (long long)U.n) BEM_CUDA_TRY(U.alloc(std::max<long long>(nu, U.n)));
+  if (hc[1] > (long long)V.n) BEM_CUDA_TRY(V.alloc(std::max<long long>(nv, V.n)));
+  const long long nt = std::max(1, ctx->t_entries);
+  if (ctx->far_was_ok) {
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->piv_i.p, ctx->piv_snap.p, nt * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->piv_j.p, ctx->piv_snap.p + nt, nt * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->aca_npiv.p, ctx->piv_snap.p + 2 * nt, nf * sizeof(int),
+                                 cudaMemcpyDeviceToDevice, st));
+  }
+  ctx->aca_warm_ok = ctx->far_was_ok;
+  BEM_CUDA_TRY(cudaMemsetAsync(ctx->aca_fail.p, 0, sizeof(int), st));
+  TRY((run_aca<R, Op>(ctx, P, U.p, V.p, (long long)U.n, (long long)V.n, ws.p, o, false, st)));
+  BEM_CUDA_TRY(cudaMemcpyAsync(hc, ctx->fbase.p + 2 * nf, 2 * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hc[0] > (long long)U.n || hc[1] > (long long)V.n)
+    return fail(ctx, BEM_ERR_STATE, "far-field pools overflowed after regrowth");
   return BEM_OK;
 }
 
@@ -891,23 +1045,25 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
   if (mixed) {
     if (ctx->near32.n < (size_t)std::max<long long>(1, ctx->near_entries)) ctx->near_zero_pending = true;
     BEM_CUDA_TRY(ctx->near32.ensure(std::max<long long>(1, ctx->near_entries)));
-    BEM_CUDA_TRY(ctx->u32.ensure(std::max<long long>(1, ctx->u_entries)));
-    BEM_CUDA_TRY(ctx->v32.ensure(std::max<long long>(1, ctx->v_entries)));
     BEM_CUDA_TRY(ctx->t32.ensure(4LL * std::max(1, ctx->t_entries)));
     BEM_CUDA_TRY(ctx->prec_inv32.ensure(9LL * ctx->ne));
   } else {
     if (ctx->near64.n < (size_t)std::max<long long>(1, ctx->near_entries)) ctx->near_zero_pending = true;
     BEM_CUDA_TRY(ctx->near64.ensure(std::max<long long>(1, ctx->near_entries)));
-    BEM_CUDA_TRY(ctx->u64.ensure(std::max<long long>(1, ctx->u_entries)));
-    BEM_CUDA_TRY(ctx->v64.ensure(std::max<long long>(1, ctx->v_entries)));
   }
   BEM_CUDA_TRY(ctx->t64.ensure(4LL * std::max(1, ctx->t_entries)));
+  if (ctx->fbase.n < 2 * nf + 2) {
+    BEM_CUDA_TRY(ctx->fbase.alloc(2 * nf + 2));
+    ctx->fbase_ready = false;
+  }
+  if (!ctx->far_compact && !ctx->fbase_ready) {
+    launch_fbase_full(ctx->far_d.p, (int)nf, ctx->fbase.p, st);
+    CK("factor offsets");
+    ctx->fbase_ready = true;
+  }
   cudaStream_t aux = ctx->aux_stream;
-  BEM_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
-  BEM_CUDA_TRY(cudaStreamWaitEvent(aux, ctx->ev_fork, 0));
-  if (mixed) TRY((run_aca<float, c64>(ctx, Pf, ctx->u32.p, ctx->v32.p, o, aux)));
-  else TRY((run_aca<double, c128>(ctx, Pd, ctx->u64.p, ctx->v64.p, o, aux)));
-  BEM_CUDA_TRY(cudaEventRecord(ctx->ev_join, aux));
+  if (mixed) TRY((far_field_begin<float, c64>(ctx, Pf, ctx->u32, ctx->v32, ctx->ws32, o, aux, st)));
+  else TRY((far_field_begin<double, c128>(ctx, Pd, ctx->u64, ctx->v64, ctx->ws64, o, aux, st)));
   if (b) {
     BEM_CUDA_TRY(cudaMemsetAsync(b, 0, ctx->N * sizeof(c128), st));
     if (mixed)
@@ -947,7 +1103,8 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
                                       b ? ctx->patf.p : nullptr, b ? ctx->pattern.p : nullptr, pk, b, st);
     CK("near_regular");
   }
-  BEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+  if (mixed) TRY((far_field_finish<float, c64>(ctx, Pf, ctx->u32, ctx->v32, ctx->ws32, o, st)));
+  else TRY((far_field_finish<double, c128>(ctx, Pd, ctx->u64, ctx->v64, ctx->ws64, o, st)));
   prof_end(ctx, ev, 1, 0.0, 0.0, st);
   ctx->assembled = true;
   ctx->s_re = sre;
@@ -1324,6 +1481,33 @@ extern "C" int bem_assemble(bem_ctx* ctx, double s_re, double s_im, const bem_op
   return BEM_OK;
 }
 
+// Entries count at base + off + i stride (i < count) of an operator array of
+// complex64 (mixed) or complex128 entries, as complex128 on the host.
+static int fetch_entries(bem_ctx* ctx, const void* base, bool c64s, long long off, long long count, long long stride,
+                         std::vector<c128>& out) {
+  out.assign(count, c128{0, 0});
+  if (count == 0) return BEM_OK;
+  const size_t esz = c64s ? sizeof(c64) : sizeof(c128);
+  std::vector<unsigned char> tmp(count * esz);
+  const unsigned char* src = static_cast<const unsigned char*>(base) + off * esz;
+  cudaStream_t st = ctx->stream;
+  if (stride == 1)
+    BEM_CUDA_TRY(cudaMemcpyAsync(tmp.data(), src, count * esz, cudaMemcpyDeviceToHost, st));
+  else
+    BEM_CUDA_TRY(cudaMemcpy2DAsync(tmp.data(), esz, src, stride * esz, esz, count, cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  for (long long i = 0; i < count; ++i) {
+    if (c64s) {
+      c64 v;
+      std::memcpy(&v, tmp.data() + i * esz, esz);
+      out[i] = c128{v.re, v.im};
+    } else {
+      std::memcpy(&out[i], tmp.data() + i * esz, esz);
+    }
+  }
+  return BEM_OK;
+}
+
 extern "C" int bem_operator_rows(bem_ctx* ctx, const int64_t* rows, int64_t nrows, double* out) {
   if (!ctx || (!rows && nrows) || (!out && nrows) || nrows < 0) return BEM_ERR_INVALID_ARG;
   if (!ctx->assembled) return fail(ctx, BEM_ERR_STATE, "operator not assembled");
@@ -1331,50 +1515,48 @@ extern "C" int bem_operator_rows(bem_ctx* ctx, const int64_t* rows, int64_t nrow
   const long long N = ctx->N;
   for (int64_t r = 0; r < nrows; ++r)
     if (rows[r] < 0 || rows[r] >= N) return fail(ctx, BEM_ERR_INVALID_ARG, "row index out of range");
-  // download operator storage and reconstruct rows on the host
-  std::vector<c128> nearv(ctx->near_entries), Uv(ctx->u_entries), Vv(ctx->v_entries);
-  std::vector<int> rk(ctx->far_h.size());
+  // the stored entries of each row's blocks are read from the device; the
+  // low-rank entries are formed on the host in FP64
+  const bool mixed = is_mixed(ctx);
+  const void* nearp = mixed ? (const void*)ctx->near32.p : (const void*)ctx->near64.p;
+  const void* Up = mixed ? (const void*)ctx->u32.p : (const void*)ctx->u64.p;
+  const void* Vp = mixed ? (const void*)ctx->v32.p : (const void*)ctx->v64.p;
+  const size_t nf = ctx->far_h.size();
+  std::vector<int> rk(nf);
+  std::vector<long long> fbase(2 * nf);
   cudaStream_t st = ctx->stream;
-  if (is_mixed(ctx)) {
-    std::vector<c64> a(ctx->near_entries), u(ctx->u_entries), v(ctx->v_entries);
-    if (!a.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(a.data(), ctx->near32.p, a.size() * sizeof(c64), cudaMemcpyDeviceToHost, st));
-    if (!u.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(u.data(), ctx->u32.p, u.size() * sizeof(c64), cudaMemcpyDeviceToHost, st));
-    if (!v.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(v.data(), ctx->v32.p, v.size() * sizeof(c64), cudaMemcpyDeviceToHost, st));
-    BEM_CUDA_TRY(cudaStreamSynchronize(st));
-    for (size_t i = 0; i < a.size(); ++i) nearv[i] = c128{a[i].re, a[i].im};
-    for (size_t i = 0; i < u.size(); ++i) Uv[i] = c128{u[i].re, u[i].im};
-    for (size_t i = 0; i < v.size(); ++i) Vv[i] = c128{v[i].re, v[i].im};
-  } else {
-    if (!nearv.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(nearv.data(), ctx->near64.p, nearv.size() * sizeof(c128), cudaMemcpyDeviceToHost, st));
-    if (!Uv.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(Uv.data(), ctx->u64.p, Uv.size() * sizeof(c128), cudaMemcpyDeviceToHost, st));
-    if (!Vv.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(Vv.data(), ctx->v64.p, Vv.size() * sizeof(c128), cudaMemcpyDeviceToHost, st));
+  if (nf) {
+    BEM_CUDA_TRY(cudaMemcpyAsync(rk.data(), ctx->rank.p, nf * sizeof(int), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA_TRY(cudaMemcpyAsync(fbase.data(), ctx->fbase.p, 2 * nf * sizeof(long long), cudaMemcpyDeviceToHost, st));
   }
-  if (!rk.empty()) BEM_CUDA_TRY(cudaMemcpyAsync(rk.data(), ctx->rank.p, rk.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
   BEM_CUDA_TRY(cudaStreamSynchronize(st));
   const auto& perm = ctx->tree.perm;
   const auto& ip = ctx->tree.iperm;
+  std::vector<c128> a, u, v;
   for (int64_t q = 0; q < nrows; ++q) {
     long long rc = rows[q];            // caller dof
-    int ec = (int)(rc / 3), a = (int)(rc % 3);
+    int ec = (int)(rc / 3), ca = (int)(rc % 3);
     int et = ip[ec];                   // tree element
-    long long rt = 3LL * et + a;       // tree row
+    long long rt = 3LL * et + ca;      // tree row
     std::vector<c128> rowt(N, c128{0, 0});
     for (const NearBlk& nb : ctx->near_h) {
       if (et < nb.r0 || et >= nb.r0 + nb.nr) continue;
-      long long ld = nb.ld, lr = rt - 3LL * nb.r0;
-      for (int c = 0; c < 3 * nb.nc; ++c) rowt[3LL * nb.c0 + c] = nearv[nb.off + c * ld + lr];
+      long long lr = rt - 3LL * nb.r0;
+      TRY(fetch_entries(ctx, nearp, mixed, nb.off + lr, 3LL * nb.nc, nb.ld, a));
+      for (int c = 0; c < 3 * nb.nc; ++c) rowt[3LL * nb.c0 + c] = a[c];
     }
-    for (size_t b = 0; b < ctx->far_h.size(); ++b) {
+    for (size_t b = 0; b < nf; ++b) {
       const FarBlk& fb = ctx->far_h[b];
       if (et < fb.r0 || et >= fb.r0 + fb.nr) continue;
       long long m = 3LL * fb.nr, n = 3LL * fb.nc, lr = rt - 3LL * fb.r0;
+      const int r = rk[b];
+      TRY(fetch_entries(ctx, Up, mixed, fbase[2 * b] + lr, r, m, u));
+      TRY(fetch_entries(ctx, Vp, mixed, fbase[2 * b + 1], n * r, 1, v));
       for (long long c = 0; c < n; ++c) {
-        std::complex<double> s = 0;
-        for (int l = 0; l < rk[b]; ++l) {
-          c128 u = Uv[fb.uoff + l * m + lr], v = Vv[fb.voff + l * n + c];
-          s += std::complex<double>(u.re, u.im) * std::complex<double>(v.re, v.im);
-        }
-        rowt[3LL * fb.c0 + c] = c128{s.real(), s.imag()};
+        std::complex<double> sum = 0;
+        for (int l = 0; l < r; ++l)
+          sum += std::complex<double>(u[l].re, u[l].im) * std::complex<double>(v[l * n + c].re, v[l * n + c].im);
+        rowt[3LL * fb.c0 + c] = c128{sum.real(), sum.imag()};
       }
     }
     double* o = out + 2 * q * N;
@@ -1568,7 +1750,9 @@ static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_de
   Timer ta[2], t1, t2;  // ta: assembly of frequency k in ta[k & 1]
   // frequency 0 on the caller's stream; afterwards frequency k + 1 is
   // assembled on asm_stream into the other operator set while the guess and
-  // GMRES of frequency k run on the caller's stream
+  // GMRES of frequency k run on the caller's stream (compact storage keeps one
+  // operator set: frequency k + 1 is assembled after frequency k is solved)
+  const bool pipe = !ctx->far_compact;
   cudaEventRecord(ta[0].a, st);
   TRY(assemble_impl(ctx, ctx->eta, 0.0, o, ctx->pattern.p, ctx->Pk_host[0], ctx->b64.p, st));
   cudaEventRecord(ta[0].b, st);
@@ -1580,7 +1764,7 @@ static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_de
     s.s_im = k * dw;
     c128* xk = ctx->sol.p + (long long)k * N;
     const bool next = k + 1 < nf;
-    if (next) {
+    if (next && pipe) {
       // the other set was last used by frequency k - 1, which the host has
       // seen complete (stream synchronised at the end of its iteration)
       swap_ops(ctx);
@@ -1628,10 +1812,14 @@ static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_de
     s.near_bytes = ctx->near_entries * (is_mixed(ctx) ? 8 : 16);
     if (stats) stats[k] = s;
     ctx->nf = k + 1;
-    if (next) {
+    if (next && pipe) {
       // frequency k + 1's operator and right-hand side become the set in use
       BEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_asm_done, 0));
       swap_ops(ctx);
+    } else if (next) {
+      cudaEventRecord(ta[(k + 1) & 1].a, st);
+      TRY(assemble_impl(ctx, ctx->eta, (k + 1) * dw, o, ctx->pattern.p, ctx->Pk_host[k + 1], ctx->b64.p, st));
+      cudaEventRecord(ta[(k + 1) & 1].b, st);
     }
   }
   if (stats && !ctx->far_h.empty()) {
@@ -1825,6 +2013,39 @@ extern "C" int bem_far_block_info(bem_ctx* ctx, int64_t nmax, int32_t* info, int
 extern "C" int bem_set_aca_reuse(bem_ctx* ctx, int on) {
   if (!ctx) return BEM_ERR_INVALID_ARG;
   ctx->aca_reuse = on != 0;
+  return BEM_OK;
+}
+
+extern "C" int bem_set_far_storage(bem_ctx* ctx, int32_t mode, int64_t workspace_bytes) {
+  if (!ctx) return BEM_ERR_INVALID_ARG;
+  if (mode < BEM_FAR_AUTO || mode > BEM_FAR_COMPACT) return fail(ctx, BEM_ERR_INVALID_ARG, "unknown storage mode");
+  if (workspace_bytes < 0) return fail(ctx, BEM_ERR_INVALID_ARG, "workspace_bytes must be >= 0");
+  ctx->far_mode_req = mode;
+  ctx->far_ws_req = workspace_bytes;
+  return BEM_OK;
+}
+
+extern "C" int bem_get_far_storage(bem_ctx* ctx, bem_far_storage* out) {
+  if (!ctx || !out) return BEM_ERR_INVALID_ARG;
+  *out = bem_far_storage{};
+  if (!ctx->have_mesh) return fail(ctx, BEM_ERR_NO_MESH, "no mesh");
+  TRY(set_device(ctx));
+  const bool mixed = is_mixed(ctx);
+  const long long esz = mixed ? 8 : 16;
+  out->compact = ctx->far_compact ? 1 : 0;
+  out->batches = (int32_t)ctx->far_batches.size();
+  out->workspace_bytes = ctx->far_compact ? (long long)(mixed ? ctx->ws32.n : ctx->ws64.n) * esz : 0;
+  out->factor_bytes = (long long)(mixed ? ctx->u32.n + ctx->v32.n : ctx->u64.n + ctx->v64.n) * esz;
+  out->regrows = ctx->far_regrows;
+  const size_t nf = ctx->far_h.size();
+  if (ctx->assembled && nf) {
+    std::vector<int> rk(nf);
+    BEM_CUDA_TRY(cudaMemcpyAsync(rk.data(), ctx->rank.p, nf * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    long long used = 0;
+    for (size_t b = 0; b < nf; ++b) used += 3LL * rk[b] * (ctx->far_h[b].nr + ctx->far_h[b].nc);
+    out->used_bytes = used * esz;
+  }
   return BEM_OK;
 }
 

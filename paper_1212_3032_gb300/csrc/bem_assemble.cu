@@ -1452,7 +1452,7 @@ constexpr int WARM_THREADS = 256;
 // Pivot rows into V[:, l] and pivot columns into U[:, l], l < the pivot count
 // of the previous frequency (its rank plus spares).
 template <typename R, typename Op>
-__global__ void __launch_bounds__(WARM_THREADS) k_aca_warm_eval(const FarBlk* __restrict__ blks,
+__global__ void __launch_bounds__(WARM_THREADS) k_aca_warm_eval(const FarBlk* __restrict__ blks, int b0,
                                                                 const ElemF* __restrict__ ef,
                                                                 const ElemD* __restrict__ ed,
                                                                 const signed char* __restrict__ bc, KParams<R> P,
@@ -1461,7 +1461,7 @@ __global__ void __launch_bounds__(WARM_THREADS) k_aca_warm_eval(const FarBlk* __
                                                                 const int* __restrict__ piv_i,
                                                                 const int* __restrict__ piv_j) {
   using T = decltype(Op{}.re);
-  const int bi = blockIdx.x;
+  const int bi = b0 + blockIdx.x;
   const int r = npiv[bi];
   if (r <= 0 || r > WARM_RMAX) return;
   const FarBlk B = blks[bi];
@@ -1637,7 +1637,7 @@ __device__ __forceinline__ void warm_trsm(Op* X, long long ldx, int ncol, int nr
 // RCAP. Blocks with nothing to reuse (r <= 0) are written as cold starts by
 // the launch with RLO = 0, blocks above the last class's RCAP by the LAST one.
 template <typename Op, int RLO, int RCAP, bool LAST, int NT, int CH>
-__global__ void __launch_bounds__(NT) k_aca_warm_solve(const FarBlk* __restrict__ blks, Op* __restrict__ Ustore,
+__global__ void __launch_bounds__(NT) k_aca_warm_solve(const FarBlk* __restrict__ blks, int b0, Op* __restrict__ Ustore,
                                                        Op* __restrict__ Vstore, int* __restrict__ rank,
                                                        int* __restrict__ npiv, const int* __restrict__ piv_i,
                                                        const int* __restrict__ piv_j, int* __restrict__ kstart,
@@ -1652,7 +1652,7 @@ __global__ void __launch_bounds__(NT) k_aca_warm_solve(const FarBlk* __restrict_
   T* nv2w = rowmax + RCAP;                                 // [l][warp]
   T* nu2w = nv2w + RCAP * NW;
   __shared__ int sh_rp, sh_ls;
-  const int bi = blockIdx.x;
+  const int bi = b0 + blockIdx.x;
   const int tid = threadIdx.x;
   const int r = npiv[bi];
   if (r <= RLO || r > RCAP) {
@@ -1831,7 +1831,7 @@ template <typename Op> size_t warm_solve_smem(int rcap, int nt) {
 }
 
 template <typename Op, int RLO, int RCAP, bool LAST, int NT, int CH>
-cudaError_t launch_warm_solve(const FarBlk* blks, int nfar, Op* U, Op* V, int* rank, int* npiv, const int* piv_i,
+cudaError_t launch_warm_solve(const FarBlk* blks, int b0, int nfar, Op* U, Op* V, int* rank, int* npiv, const int* piv_i,
                               const int* piv_j, int* kstart, double* norm0, int* done, double eps, double tau,
                               cudaStream_t st) {
   const size_t sm = warm_solve_smem<Op>(RCAP, NT);
@@ -1840,27 +1840,88 @@ cudaError_t launch_warm_solve(const FarBlk* blks, int nfar, Op* U, Op* V, int* r
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   count_if(true);
-  k_aca_warm_solve<Op, RLO, RCAP, LAST, NT, CH><<<nfar, NT, sm, st>>>(blks, U, V, rank, npiv, piv_i, piv_j,
+  k_aca_warm_solve<Op, RLO, RCAP, LAST, NT, CH><<<nfar, NT, sm, st>>>(blks, b0, U, V, rank, npiv, piv_i, piv_j,
                                                                       kstart, norm0, done, eps, tau);
   return cudaGetLastError();
 }
 
 template <typename R, typename Op>
-cudaError_t launch_aca_warm(const FarBlk* blks, int nfar, const ElemF* ef, const ElemD* ed, const signed char* bc,
-                            const KParams<R>& P, Op* U, Op* V, int* rank, int* npiv, int* piv_i, int* piv_j,
-                            int* kstart, double* norm0, int* done, double eps, double tau, cudaStream_t st) {
+cudaError_t launch_aca_warm(const FarBlk* blks, int b0, int nfar, const ElemF* ef, const ElemD* ed,
+                            const signed char* bc, const KParams<R>& P, Op* U, Op* V, int* rank, int* npiv,
+                            int* piv_i, int* piv_j, int* kstart, double* norm0, int* done, double eps, double tau,
+                            cudaStream_t st) {
   if (!nfar) return cudaSuccess;
   count_if(true);
-  k_aca_warm_eval<R, Op><<<nfar, WARM_THREADS, 0, st>>>(blks, ef, ed, bc, P, U, V, npiv, piv_i, piv_j);
+  k_aca_warm_eval<R, Op><<<nfar, WARM_THREADS, 0, st>>>(blks, b0, ef, ed, bc, P, U, V, npiv, piv_i, piv_j);
   // rank classes (0, 64] and (64, 128]; complex128 pivot blocks above rank
   // 112 do not fit in shared memory and restart ACA
   constexpr int RTOP = sizeof(Op) == 8 ? WARM_RMAX : 112;
-  cudaError_t e = launch_warm_solve<Op, 0, WARM_SPLIT, false, 128, 8>(blks, nfar, U, V, rank, npiv, piv_i, piv_j,
+  cudaError_t e = launch_warm_solve<Op, 0, WARM_SPLIT, false, 128, 8>(blks, b0, nfar, U, V, rank, npiv, piv_i, piv_j,
                                                                       kstart, norm0, done, eps, tau, st);
   if (e != cudaSuccess) return e;
-  return launch_warm_solve<Op, WARM_SPLIT, RTOP, true, 256, 16>(blks, nfar, U, V, rank, npiv, piv_i, piv_j, kstart,
+  return launch_warm_solve<Op, WARM_SPLIT, RTOP, true, 256, 16>(blks, b0, nfar, U, V, rank, npiv, piv_i, piv_j, kstart,
                                                                 norm0, done, eps, tau, st);
 }
+
+// ---------------------------------------------------------------------------
+// far-field factor storage
+// ---------------------------------------------------------------------------
+// Full storage: the factors stay where ACA wrote them.
+__global__ void k_fbase_full(const FarBlk* __restrict__ blks, int nfar, long long* __restrict__ fbase) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nfar) return;
+  fbase[2 * b] = blks[b].uoff;
+  fbase[2 * b + 1] = blks[b].voff;
+}
+
+// Compact storage: block b0 + blockIdx.x takes 3 nr rank and 3 nc rank
+// entries from the pool cursors and copies the first rank columns of its U
+// and V (contiguous, column-major) out of the workspace. The cursors count
+// the full need even past the pools' capacity; a block that does not fit is
+// not copied (the host sees the overflow and redoes the assembly).
+template <typename Op>
+__global__ void __launch_bounds__(256) k_far_pack(const FarBlk* __restrict__ blks, int b0, const int* __restrict__ rank,
+                                                  const Op* __restrict__ wsU, const Op* __restrict__ wsV,
+                                                  Op* __restrict__ U, Op* __restrict__ V, long long capU,
+                                                  long long capV, long long* __restrict__ fbase,
+                                                  unsigned long long* __restrict__ cursor) {
+  const int b = b0 + blockIdx.x;
+  const FarBlk B = blks[b];
+  const int r = rank[b];
+  const long long nu = 3LL * B.nr * r, nv = 3LL * B.nc * r;
+  __shared__ long long ou, ov;
+  if (threadIdx.x == 0) {
+    ou = (long long)atomicAdd(&cursor[0], (unsigned long long)nu);
+    ov = (long long)atomicAdd(&cursor[1], (unsigned long long)nv);
+    fbase[2 * b] = ou;
+    fbase[2 * b + 1] = ov;
+  }
+  __syncthreads();
+  if (ou + nu > capU || ov + nv > capV) return;
+  const Op* su = wsU + B.uoff;
+  const Op* sv = wsV + B.voff;
+  Op* du = U + ou;
+  Op* dv = V + ov;
+  for (long long i = threadIdx.x; i < nu; i += blockDim.x) du[i] = su[i];
+  for (long long i = threadIdx.x; i < nv; i += blockDim.x) dv[i] = sv[i];
+}
+
+void launch_fbase_full(const FarBlk* blks, int nfar, long long* fbase, cudaStream_t st) {
+  if (count_if(nfar)) k_fbase_full<<<(nfar + 255) / 256, 256, 0, st>>>(blks, nfar, fbase);
+}
+
+template <typename Op>
+void launch_far_pack(const FarBlk* blks, int b0, int nblk, const int* rank, const Op* wsU, const Op* wsV, Op* U,
+                     Op* V, long long capU, long long capV, long long* fbase, unsigned long long* cursor,
+                     cudaStream_t st) {
+  if (count_if(nblk))
+    k_far_pack<Op><<<nblk, 256, 0, st>>>(blks, b0, rank, wsU, wsV, U, V, capU, capV, fbase, cursor);
+}
+
+template void launch_far_pack<c64>(const FarBlk*, int, int, const int*, const c64*, const c64*, c64*, c64*,
+                                   long long, long long, long long*, unsigned long long*, cudaStream_t);
+template void launch_far_pack<c128>(const FarBlk*, int, int, const int*, const c128*, const c128*, c128*, c128*,
+                                    long long, long long, long long*, unsigned long long*, cudaStream_t);
 
 template void launch_near_regular<float, c64>(const NearBlk*, int, int, const unsigned*, const long long*,
                                               const int*, const ElemF*, const ElemD*, const signed char*,
@@ -1888,10 +1949,10 @@ template void launch_aca<float, c64>(const FarBlk*, const int*, int, const int*,
 template void launch_aca<double, c128>(const FarBlk*, const int*, int, const int*, int, const ElemF*,
                                        const ElemD*, const signed char*, const KParams<double>&, c128*, c128*, int*,
                                        int*, double, const AcaState&, cudaStream_t);
-template cudaError_t launch_aca_warm<float, c64>(const FarBlk*, int, const ElemF*, const ElemD*, const signed char*,
+template cudaError_t launch_aca_warm<float, c64>(const FarBlk*, int, int, const ElemF*, const ElemD*, const signed char*,
                                                  const KParams<float>&, c64*, c64*, int*, int*, int*, int*, int*,
                                                  double*, int*, double, double, cudaStream_t);
-template cudaError_t launch_aca_warm<double, c128>(const FarBlk*, int, const ElemF*, const ElemD*,
+template cudaError_t launch_aca_warm<double, c128>(const FarBlk*, int, int, const ElemF*, const ElemD*,
                                                    const signed char*, const KParams<double>&, c128*, c128*, int*,
                                                    int*, int*, int*, int*, double*, int*, double, double,
                                                    cudaStream_t);

@@ -45,7 +45,9 @@ struct NearBlk {
 // Low-rank far-field block A ~ U V^T; U: (3 nr) x rmax column-major,
 // V: (3 nc) x rmax column-major; rank[b] <= rmax set by ACA.
 struct FarBlk {
-  long long uoff, voff;
+  long long uoff, voff;  // this block's U, V while ACA runs: offsets in the U, V arrays it
+                         // writes (the stored factors in full storage; the workspace of
+                         // the block's batch in compact storage)
   int r0, nr, c0, nc;
   int rmax;
   int toff;  // offset of this block's t = V^T x in the t buffer
@@ -54,7 +56,8 @@ struct FarBlk {
 // One column panel of a leaf row of the matrix-vector product:
 // y[rows of leaf] += P x_panel, P column-major with leading dimension ld.
 struct Panel {
-  long long data;  // offset into the near array (kind 0) or U array (kind 1)
+  long long data;  // offset into the near array (kind 0); kind 1: row offset within the
+                   // block's U (its start comes from the operator set's factor offsets)
   int ld;          // leading dimension of the stored block
   int ncols;       // kind 0: columns; kind 1: ignored (rank read at run time)
   int xoff;        // kind 0: first x index; kind 1: far block index
@@ -130,8 +133,19 @@ struct OpSet {
   DevBuf<c64> near32, u32, v32, prec_inv32;
   DevBuf<c128> near64, u64, v64, prec_inv, b64;
   DevBuf<int> rank, aca_fail, status;
+  DevBuf<long long> fbase;
   bool near_zero_pending = true;
+  bool fbase_ready = false;
   int prof_slot = 0;
+};
+
+// A run of consecutive admissible blocks whose ACA factors, at their rank
+// caps, fit the workspace together (compact storage); full storage has one
+// batch over all blocks. The size-class lists hold each batch's blocks in
+// the index ranges [s0, s1) and [l0, l1).
+struct FarBatch {
+  int b0, b1;
+  int s0, s1, l0, l1;
 };
 
 // Host-side rule tables (Gauss-Legendre on [0,1], series coefficients).
@@ -172,8 +186,21 @@ struct bem_ctx {
   std::vector<bem::FarBlk> far_h;
   bem::DevBuf<bem::NearBlk> near_d;
   bem::DevBuf<bem::FarBlk> far_d;
-  long long near_entries = 0, u_entries = 0, v_entries = 0;
+  long long near_entries = 0, u_entries = 0, v_entries = 0;  // u/v: factors at their rank caps
   int t_entries = 0;
+  // far-field factor storage (bem_set_far_storage): full = every block at its
+  // rank cap, written in place by ACA; compact = ACA runs batch by batch in a
+  // workspace and each batch is packed at its actual ranks into pools that
+  // grow on demand
+  int far_mode_req = BEM_FAR_AUTO;
+  long long far_ws_req = 0;            // requested workspace bytes (0: default)
+  bool far_compact = false;            // storage chosen for the current mesh
+  std::vector<bem::FarBatch> far_batches;
+  long long ws_entries = 0;            // workspace entries per factor (U half, V half)
+  int far_regrows = 0;                 // pool regrowths (assemblies re-run after an overflow)
+  bool far_was_ok = false;             // the current assembly started from stored pivots
+  bem::DevBuf<bem::c64> ws32;          // 2 x ws_entries
+  bem::DevBuf<bem::c128> ws64;
   int nleaves = 0;
   std::vector<int> leaf_nodes;        // node index per leaf (row order)
   bem::DevBuf<int> leaf_r0, leaf_nr;  // per leaf
@@ -219,12 +246,17 @@ struct bem_ctx {
   bem::DevBuf<bem::c128> near64, u64, v64, t64;
   bem::DevBuf<int> rank;
   bem::DevBuf<int> aca_fail;
+  // per admissible block: offsets of its stored U and V ([2b], [2b + 1]);
+  // then the pool cursors (entries the last assembly needed)
+  bem::DevBuf<long long> fbase;
+  bool fbase_ready = false;            // full storage: offsets filled for this set
   // cross-frequency reuse of ACA pivots
   bool aca_reuse = true;               // bem_set_aca_reuse
   bool aca_warm_ok = false;            // pivots of a previous assembly of this mesh are stored
   bool aca_last_warm = false;          // the last assembly started from reused pivots
   double aca_tau = 0.1;                // pivot test of the reused steps
   bem::DevBuf<int> piv_i, piv_j;       // t_entries each
+  bem::DevBuf<int> piv_snap;           // compact storage: piv_i, piv_j, npiv an assembly started from
   bem::DevBuf<int> aca_kstart, aca_done, aca_npiv;
   bem::DevBuf<double> aca_norm0;
   long long prof_aca_blocks = 0;       // far blocks assembled (profiling)

@@ -49,10 +49,21 @@ void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int
 // writes the start state (kstart, norm0, done) for launch_aca. npiv holds the
 // previous pivot counts (rank plus spares); rank and npiv of every block
 // settled by the reuse are updated, the others by launch_aca.
+// Blocks b0 .. b0 + nfar - 1.
 template <typename R, typename Op>
-cudaError_t launch_aca_warm(const FarBlk* blks, int nfar, const ElemF* ef, const ElemD* ed, const signed char* bc,
-                            const KParams<R>& P, Op* U, Op* V, int* rank, int* npiv, int* piv_i, int* piv_j,
-                            int* kstart, double* norm0, int* done, double eps, double tau, cudaStream_t st);
+cudaError_t launch_aca_warm(const FarBlk* blks, int b0, int nfar, const ElemF* ef, const ElemD* ed,
+                            const signed char* bc, const KParams<R>& P, Op* U, Op* V, int* rank, int* npiv,
+                            int* piv_i, int* piv_j, int* kstart, double* norm0, int* done, double eps, double tau,
+                            cudaStream_t st);
+// Factor offsets of full storage: fbase[2b], fbase[2b + 1] = uoff, voff.
+void launch_fbase_full(const FarBlk* blks, int nfar, long long* fbase, cudaStream_t st);
+// Compact storage: packs blocks b0 .. b0 + nblk - 1 from the workspace (wsU,
+// wsV at the blocks' uoff, voff) at their ranks into the pools U, V of
+// capU, capV entries, taking space from cursor[0], cursor[1]; writes fbase.
+template <typename Op>
+void launch_far_pack(const FarBlk* blks, int b0, int nblk, const int* rank, const Op* wsU, const Op* wsV, Op* U,
+                     Op* V, long long capU, long long capV, long long* fbase, unsigned long long* cursor,
+                     cudaStream_t st);
 
 // ---- solver (bem_solve.cu) ----
 // H-matrix product y = A x for nrhs right-hand sides (x, y: nrhs vectors of

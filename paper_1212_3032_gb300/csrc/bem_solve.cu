@@ -68,7 +68,8 @@ template <typename Acc> __device__ __forceinline__ Acc wsum(Acc v) {
 // ---------------------------------------------------------------------------
 template <typename Op, typename X, typename Acc, int NRHS>
 __device__ __forceinline__ void hmv_t_block(int bi, const FarBlk* __restrict__ blks, const int* __restrict__ rank,
-                                            const Op* __restrict__ V, const X* __restrict__ x, long long N,
+                                            const long long* __restrict__ fbase, const Op* __restrict__ V,
+                                            const X* __restrict__ x, long long N,
                                             cplx<Acc>* __restrict__ t, int tstride) {
   // one warp per 4 factor columns: 4 independent coalesced column streams in flight
   constexpr int C = 4;
@@ -79,7 +80,7 @@ __device__ __forceinline__ void hmv_t_block(int bi, const FarBlk* __restrict__ b
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int l0 = warp * C; l0 < r; l0 += nw * C) {
     const int nc = min(C, r - l0);
-    const Op* col = V + B.voff + (long long)l0 * n;
+    const Op* col = V + fbase[2 * bi + 1] + (long long)l0 * n;
     cplx<Acc> acc[C][NRHS];
 #pragma unroll
     for (int c = 0; c < C; ++c)
@@ -111,9 +112,10 @@ __device__ __forceinline__ void hmv_t_block(int bi, const FarBlk* __restrict__ b
 
 template <typename Op, typename X, typename Acc, int NRHS>
 __global__ void __launch_bounds__(256) k_hmv_t(const FarBlk* __restrict__ blks, const int* __restrict__ rank,
-                                               const Op* __restrict__ V, const X* __restrict__ x, long long N,
-                                               cplx<Acc>* __restrict__ t, int tstride) {
-  hmv_t_block<Op, X, Acc, NRHS>(blockIdx.x, blks, rank, V, x, N, t, tstride);
+                                               const long long* __restrict__ fbase, const Op* __restrict__ V,
+                                               const X* __restrict__ x, long long N, cplx<Acc>* __restrict__ t,
+                                               int tstride) {
+  hmv_t_block<Op, X, Acc, NRHS>(blockIdx.x, blks, rank, fbase, V, x, N, t, tstride);
 }
 
 // ---------------------------------------------------------------------------
@@ -128,7 +130,8 @@ constexpr int HMV_THREADS = 384;
 template <typename Op, typename X, typename Acc, int NRHS>
 __device__ __forceinline__ void hmv_task(
     const Task tk, const int* __restrict__ leaf_nr, const Panel* __restrict__ panels,
-    const FarBlk* __restrict__ far, const int* __restrict__ rank, const Op* __restrict__ near,
+    const FarBlk* __restrict__ far, const int* __restrict__ rank, const long long* __restrict__ fbase,
+    const Op* __restrict__ near,
     const Op* __restrict__ U, const cplx<Acc>* __restrict__ t, int tstride, const X* __restrict__ x, long long N,
     cplx<Acc>* __restrict__ part, long long pstride, cplx<Acc>* red) {
   const int rows = 3 * leaf_nr[tk.leaf];
@@ -175,7 +178,7 @@ __device__ __forceinline__ void hmv_task(
         } else {
           const int b = P.xoff;
           const int nc = rank[b];
-          const Op* d = U + P.data + r;
+          const Op* d = U + fbase[2 * b] + P.data + r;
           const cplx<Acc>* ts = t + far[b].toff;
           int j = g;
           for (; j + 3 * G < nc; j += 4 * G) {
@@ -222,13 +225,13 @@ __device__ __forceinline__ void hmv_task(
 template <typename Op, typename X, typename Acc, int NRHS>
 __global__ void __launch_bounds__(HMV_THREADS, 2) k_hmv_tasks(
     const Task* __restrict__ tasks, const int* __restrict__ leaf_nr, const Panel* __restrict__ panels,
-    const FarBlk* __restrict__ far, const int* __restrict__ rank, const Op* __restrict__ near,
-    const Op* __restrict__ U, const cplx<Acc>* __restrict__ t, int tstride, const X* __restrict__ x, long long N,
-    cplx<Acc>* __restrict__ part, long long pstride) {
+    const FarBlk* __restrict__ far, const int* __restrict__ rank, const long long* __restrict__ fbase,
+    const Op* __restrict__ near, const Op* __restrict__ U, const cplx<Acc>* __restrict__ t, int tstride,
+    const X* __restrict__ x, long long N, cplx<Acc>* __restrict__ part, long long pstride) {
   extern __shared__ unsigned char smem_raw[];
   cplx<Acc>* red = reinterpret_cast<cplx<Acc>*>(smem_raw);
-  hmv_task<Op, X, Acc, NRHS>(tasks[blockIdx.x], leaf_nr, panels, far, rank, near, U, t, tstride, x, N, part, pstride,
-                             red);
+  hmv_task<Op, X, Acc, NRHS>(tasks[blockIdx.x], leaf_nr, panels, far, rank, fbase, near, U, t, tstride, x, N, part,
+                             pstride, red);
 }
 
 // The same task kernel over a list of task indices (the launch order), with
@@ -241,15 +244,15 @@ template <typename Op, typename X, typename Y, typename Acc, int NRHS>
 __global__ void __launch_bounds__(HMV_THREADS, (NRHS == 1 && sizeof(Acc) == 4) ? 3 : 2) k_hmv_tasks_list(
     const int* __restrict__ list, const Task* __restrict__ tasks, const int* __restrict__ leaf_nr,
     const Panel* __restrict__ panels, const FarBlk* __restrict__ far, const int* __restrict__ rank,
-    const Op* __restrict__ near, const Op* __restrict__ U, const cplx<Acc>* __restrict__ t, int tstride,
-    const X* __restrict__ x, long long N, cplx<Acc>* __restrict__ part, long long pstride,
-    const int* __restrict__ leaf_r0, const int* __restrict__ task_ptr, int* __restrict__ leaf_cnt,
+    const long long* __restrict__ fbase, const Op* __restrict__ near, const Op* __restrict__ U,
+    const cplx<Acc>* __restrict__ t, int tstride, const X* __restrict__ x, long long N,
+    cplx<Acc>* __restrict__ part, long long pstride, const int* __restrict__ leaf_r0, const int* __restrict__ task_ptr, int* __restrict__ leaf_cnt,
     Y* __restrict__ y) {
   extern __shared__ unsigned char smem_raw[];
   cplx<Acc>* red = reinterpret_cast<cplx<Acc>*>(smem_raw);
   __shared__ int last;
   const Task tk = tasks[list[blockIdx.x]];
-  hmv_task<Op, X, Acc, NRHS>(tk, leaf_nr, panels, far, rank, near, U, t, tstride, x, N, part, pstride, red);
+  hmv_task<Op, X, Acc, NRHS>(tk, leaf_nr, panels, far, rank, fbase, near, U, t, tstride, x, N, part, pstride, red);
   __threadfence();  // this task's partials are visible before its arrival is counted
   __syncthreads();
   const int t0 = task_ptr[tk.leaf], t1 = task_ptr[tk.leaf + 1];
@@ -308,16 +311,18 @@ template <typename Op, typename X, typename Y, typename Acc, int NRHS>
 static void hmv_impl(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V, cplx<Acc>* t,
                      const X* x, Y* y, cudaStream_t st) {
   int nfar = (int)ctx->far_h.size();
-  if (count_if(nfar)) k_hmv_t<Op, X, Acc, NRHS><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, V, x, ctx->N, t,
-                                                                       ctx->t_entries);
+  if (count_if(nfar))
+    k_hmv_t<Op, X, Acc, NRHS><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, ctx->fbase.p, V, x, ctx->N, t,
+                                                    ctx->t_entries);
   cplx<Acc>* part = reinterpret_cast<cplx<Acc>*>(ctx->part.p);
   size_t sm = (size_t)HMV_THREADS * NRHS * sizeof(cplx<Acc>);  // red: NRHS x G x rows <= NRHS x threads
   // every task, largest first (CTAs are dispatched in index order: the long
   // tasks start early and the short ones fill the tail)
   if (count_if(ctx->ntasks))
     k_hmv_tasks_list<Op, X, Y, Acc, NRHS><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
-        ctx->task_order.p, ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t,
-        ctx->t_entries, x, ctx->N, part, ctx->part_rows, ctx->leaf_r0.p, ctx->task_ptr.p, ctx->leaf_cnt.p, y);
+        ctx->task_order.p, ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, ctx->fbase.p,
+        near, U, t, ctx->t_entries, x, ctx->N, part, ctx->part_rows, ctx->leaf_r0.p, ctx->task_ptr.p,
+        ctx->leaf_cnt.p, y);
 }
 
 template <typename Op, typename X, typename Y, typename Acc>
@@ -338,12 +343,13 @@ void launch_hmatvec_scratch_c64(const bem_ctx* ctx, const c64* near, const c64* 
                                 cplx<float>* part, const c64* x, c64* y, cudaStream_t st) {
   int nfar = (int)ctx->far_h.size();
   if (count_if(nfar))
-    k_hmv_t<c64, c64, float, 1><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, V, x, ctx->N, t, ctx->t_entries);
+    k_hmv_t<c64, c64, float, 1><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, ctx->fbase.p, V, x, ctx->N, t,
+                                                      ctx->t_entries);
   size_t sm = (size_t)2 * HMV_THREADS * sizeof(cplx<float>);
   count_if(true);
   k_hmv_tasks<c64, c64, float, 1><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
-      ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, near, U, t, ctx->t_entries, x, ctx->N,
-      part, ctx->part_rows);
+      ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, ctx->fbase.p, near, U, t,
+      ctx->t_entries, x, ctx->N, part, ctx->part_rows);
   count_if(true);
   k_hmv_reduce<float, c64, 1><<<ctx->nleaves, 256, 0, st>>>(ctx->leaf_r0.p, ctx->leaf_nr.p, ctx->task_ptr.p,
                                                            ctx->tasks.p, part, ctx->part_rows, ctx->N, y);
