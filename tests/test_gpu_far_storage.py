@@ -2,9 +2,10 @@
 
 * Compact storage (ACA batch by batch in a workspace, factors packed at their
   ranks into pools that grow on overflow) gives the same operator, bit for
-  bit, as full storage (capped factors written in place): products, stored
-  rows and sweep solutions, in complex64 and complex128, through fresh ACA,
-  pivot reuse and a pool overflow in either.
+  bit, as full storage (capped factors written in place): products and
+  stored rows, in complex64 and complex128, through fresh ACA, pivot reuse
+  and a pool overflow in either. Sweeps agree to the solver tolerance (the
+  right-hand side sums with atomics, so its last bits vary run to run).
 * The unit cube with 8 cavities (231,088 triangles, 693,264 unknowns,
   bottom fixed, top loaded: mixed boundary conditions) at ACA tolerance 1e-4
   in complex64 selects compact storage by itself, stays under 180 GB of
@@ -104,7 +105,8 @@ def test_compact_sweep_equals_pipelined_sweep(B):
                 assert c.far_storage()["batches"] > 1
         finally:
             c.close()
-    assert np.array_equal(sols[0], sols[1])
+    for k in range(N // 2 + 1):
+        assert _rel(sols[1][k], sols[0][k]) <= 2e-5, k
 
 
 def test_storage_arguments(B):
