@@ -1051,6 +1051,42 @@ template <typename T> __device__ __forceinline__ void aca_argmax(T& v, int& idx,
     }
 }
 
+// Residual row irow of a block into V[:, k]: A(irow, :) - sum_{l<k} U(irow, l) V(:, l)^T,
+// the block's column elements split over the threads t0, t0 + tstride, ...
+template <typename R, typename T, typename Op>
+__device__ __forceinline__ void aca_residual_row(const ElemF* ef, const ElemD* ed, const signed char* bc,
+                                                 const KParams<R>& P, const FarBlk& B, const Op* Ub, Op* Vb, int m,
+                                                 int n, int k, int irow, int t0, int tstride) {
+  const int ie = B.r0 + irow / 3, ia = irow % 3;
+  for (int el = t0; el < B.nc; el += tstride) {
+    int e = B.c0 + el;
+    cplx<T> vv[3];
+    aca_row3<R, T>(ef, ed, bc, P, ie, ia, e, vv);
+    const Op* vrow = Vb + 3 * el;
+#pragma unroll 4
+    for (int l = 0; l < k; ++l) {
+      Op ul = Ub[(long long)l * m + irow];
+      const Op* vl = vrow + (long long)l * n;
+      Op v0 = vl[0], v1 = vl[1], v2 = vl[2];
+      cplx<T> cu = mk<T>(ul.re, ul.im);
+      vv[0] = vv[0] - cu * mk<T>(v0.re, v0.im);
+      vv[1] = vv[1] - cu * mk<T>(v1.re, v1.im);
+      vv[2] = vv[2] - cu * mk<T>(v2.re, v2.im);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Vb[(long long)k * n + 3 * el + c] = to_op<Op>(vv[c]);
+  }
+}
+
+// Check rows of the convergence test, one per displacement component a,
+// from elements spread over the row cluster. Partial pivoting only follows
+// the nonzero pattern of the rows and columns it has visited: on a flat face
+// the normal-component rows of a coplanar block couple only to the
+// tangential columns and the tangential rows only to the normal columns, so
+// a block that converged on one of the two parts has not seen the other.
+// A check row whose residual is not small restarts the ACA steps from it.
+__device__ __forceinline__ int aca_check_row(int nr, int a) { return 3 * ((a * nr) / 3 + nr / 6) + a; }
+
 template <typename R, typename Op>
 __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ list, const FarBlk* __restrict__ blks,
                                                      const ElemF* __restrict__ ef,
@@ -1102,28 +1138,13 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
     istar = inext;
     __syncthreads();
   }
-  int kconv = -1;  // rank at which the stopping test first held
+  int kconv = -1;         // rank at which the stopping test first held
+  int vnext = 0;          // components whose check row has been examined
+  bool have_row = false;  // V[:, k] already holds the residual row of istar
   while (k < rmax) {
     // --- residual row istar -> V[:, k]
-    int ie = B.r0 + istar / 3, ia = istar % 3;
-    for (int el = threadIdx.x; el < B.nc; el += blockDim.x) {
-      int e = B.c0 + el;
-      cplx<T> vv[3];
-      aca_row3<R, T>(ef, ed, bc, P, ie, ia, e, vv);
-      const Op* vrow = Vb + 3 * el;
-#pragma unroll 4
-      for (int l = 0; l < k; ++l) {
-        Op ul = Ub[(long long)l * m + istar];
-        const Op* vl = vrow + (long long)l * n;
-        Op v0 = vl[0], v1 = vl[1], v2 = vl[2];
-        cplx<T> cu = mk<T>(ul.re, ul.im);
-        vv[0] = vv[0] - cu * mk<T>(v0.re, v0.im);
-        vv[1] = vv[1] - cu * mk<T>(v1.re, v1.im);
-        vv[2] = vv[2] - cu * mk<T>(v2.re, v2.im);
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Vb[(long long)k * n + 3 * el + c] = to_op<Op>(vv[c]);
-    }
+    if (!have_row) aca_residual_row<R, T, Op>(ef, ed, bc, P, B, Ub, Vb, m, n, k, istar, threadIdx.x, blockDim.x);
+    have_row = false;
     __syncthreads();
     T best = T(-1);
     int jstar = 0;
@@ -1136,103 +1157,139 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
       }
     }
     aca_argmax(best, jstar, sh);
+    bool stop = false;
     if (!(best > T(0))) {
-      if (kconv < 0) kconv = k;  // zero residual row: the block is represented exactly
-      break;
-    }
-    Op pv = Vb[(long long)k * n + jstar];
-    cplx<T> ipiv = inv(mk<T>(pv.re, pv.im));
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      Op v = Vb[(long long)k * n + j];
-      Vb[(long long)k * n + j] = to_op<Op>(mk<T>(v.re, v.im) * ipiv);
-    }
-    if (threadIdx.x == 0) {
-      piv_i[k] = istar;
-      piv_j[k] = jstar;
-    }
-    __syncthreads();
-    // --- residual column jstar -> U[:, k]
-    int je = B.c0 + jstar / 3, jc = jstar % 3;
-    for (int il = threadIdx.x; il < B.nr; il += blockDim.x) {
-      int i = B.r0 + il;
-      cplx<T> uu[3];
-      aca_col3<R, T>(ef, ed, bc, P, i, je, jc, uu);
-      const Op* ucol = Ub + 3 * il;
-#pragma unroll 4
-      for (int l = 0; l < k; ++l) {
-        Op vl = Vb[(long long)l * n + jstar];
-        const Op* ul = ucol + (long long)l * m;
-        Op u0 = ul[0], u1 = ul[1], u2 = ul[2];
-        cplx<T> cv = mk<T>(vl.re, vl.im);
-        uu[0] = uu[0] - mk<T>(u0.re, u0.im) * cv;
-        uu[1] = uu[1] - mk<T>(u1.re, u1.im) * cv;
-        uu[2] = uu[2] - mk<T>(u2.re, u2.im) * cv;
-      }
-#pragma unroll
-      for (int a = 0; a < 3; ++a) Ub[(long long)k * m + 3 * il + a] = to_op<Op>(uu[a]);
-    }
-    if (threadIdx.x == 0) sh.rows_used[k] = istar;
-    __syncthreads();
-    // earlier pivot rows are exactly represented already: their residual is zero
-    for (int l = threadIdx.x; l < k; l += blockDim.x) Ub[(long long)k * m + sh.rows_used[l]] = Op{};
-    __syncthreads();
-    // Frobenius norm of the approximant estimated by its diagonal terms:
-    // ||S_k||^2 ~ sum_l |u_l|^2 |v_l|^2
-    {
-      T nu2 = 0, nv2 = 0;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        Op a = Ub[(long long)k * m + i];
-        nu2 += a.re * a.re + a.im * a.im;
-      }
+      if (kconv < 0) kconv = k;  // zero residual row
+      stop = true;
+    } else {
+      Op pv = Vb[(long long)k * n + jstar];
+      cplx<T> ipiv = inv(mk<T>(pv.re, pv.im));
+      __syncthreads();
       for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        Op a = Vb[(long long)k * n + j];
-        nv2 += a.re * a.re + a.im * a.im;
+        Op v = Vb[(long long)k * n + j];
+        Vb[(long long)k * n + j] = to_op<Op>(mk<T>(v.re, v.im) * ipiv);
       }
-      nu2 = wsumT(nu2);
-      nv2 = wsumT(nv2);
-      if (lane == 0) {
-        sh.dot[0][0][wid] = nu2;
-        sh.dot[1][0][wid] = nv2;
-      }
-      __syncthreads();
       if (threadIdx.x == 0) {
-        T a = 0, b2 = 0;
-        for (int w = 0; w < ACA_WARPS; ++w) {
-          a += sh.dot[0][0][w];
-          b2 += sh.dot[1][0][w];
-        }
-        normS2 += a * b2;
-        sh.scal[0] = normS2;
-        sh.scal[1] = a * b2;
+        piv_i[k] = istar;
+        piv_j[k] = jstar;
       }
       __syncthreads();
-    }
-    normS2 = sh.scal[0];
-    T term = sh.scal[1];
-    ++k;
-    if (kconv < 0 && term <= eps * eps * normS2) kconv = k;
-    // ACA_EXTRA steps past the stopping point record spare pivots for reuse
-    if (kconv >= 0 && k >= kconv + ACA_EXTRA) break;
-    // --- next pivot row: largest entry of u_k outside the rows used so far
-    T bu = T(-1);
-    int inext = 0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      if (i == istar) continue;
-      Op u = Ub[(long long)(k - 1) * m + i];
-      T a = u.re * u.re + u.im * u.im;
-      if (a > bu) {
-        bu = a;
-        inext = i;
+      // --- residual column jstar -> U[:, k]
+      int je = B.c0 + jstar / 3, jc = jstar % 3;
+      for (int il = threadIdx.x; il < B.nr; il += blockDim.x) {
+        int i = B.r0 + il;
+        cplx<T> uu[3];
+        aca_col3<R, T>(ef, ed, bc, P, i, je, jc, uu);
+        const Op* ucol = Ub + 3 * il;
+#pragma unroll 4
+        for (int l = 0; l < k; ++l) {
+          Op vl = Vb[(long long)l * n + jstar];
+          const Op* ul = ucol + (long long)l * m;
+          Op u0 = ul[0], u1 = ul[1], u2 = ul[2];
+          cplx<T> cv = mk<T>(vl.re, vl.im);
+          uu[0] = uu[0] - mk<T>(u0.re, u0.im) * cv;
+          uu[1] = uu[1] - mk<T>(u1.re, u1.im) * cv;
+          uu[2] = uu[2] - mk<T>(u2.re, u2.im) * cv;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Ub[(long long)k * m + 3 * il + a] = to_op<Op>(uu[a]);
+      }
+      if (threadIdx.x == 0) sh.rows_used[k] = istar;
+      __syncthreads();
+      // earlier pivot rows are exactly represented already: their residual is zero
+      for (int l = threadIdx.x; l < k; l += blockDim.x) Ub[(long long)k * m + sh.rows_used[l]] = Op{};
+      __syncthreads();
+      // Frobenius norm of the approximant estimated by its diagonal terms:
+      // ||S_k||^2 ~ sum_l |u_l|^2 |v_l|^2
+      {
+        T nu2 = 0, nv2 = 0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          Op a = Ub[(long long)k * m + i];
+          nu2 += a.re * a.re + a.im * a.im;
+        }
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+          Op a = Vb[(long long)k * n + j];
+          nv2 += a.re * a.re + a.im * a.im;
+        }
+        nu2 = wsumT(nu2);
+        nv2 = wsumT(nv2);
+        if (lane == 0) {
+          sh.dot[0][0][wid] = nu2;
+          sh.dot[1][0][wid] = nv2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          T a = 0, b2 = 0;
+          for (int w = 0; w < ACA_WARPS; ++w) {
+            a += sh.dot[0][0][w];
+            b2 += sh.dot[1][0][w];
+          }
+          normS2 += a * b2;
+          sh.scal[0] = normS2;
+          sh.scal[1] = a * b2;
+        }
+        __syncthreads();
+      }
+      normS2 = sh.scal[0];
+      T term = sh.scal[1];
+      ++k;
+      if (kconv < 0 && term <= eps * eps * normS2) kconv = k;
+      // ACA_EXTRA steps past the stopping point record spare pivots for reuse
+      if (kconv >= 0 && k >= kconv + ACA_EXTRA) {
+        stop = true;
+      } else {
+        // --- next pivot row: largest entry of u_k outside the rows used so far
+        T bu = T(-1);
+        int inext = 0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          if (i == istar) continue;
+          Op u = Ub[(long long)(k - 1) * m + i];
+          T a = u.re * u.re + u.im * u.im;
+          if (a > bu) {
+            bu = a;
+            inext = i;
+          }
+        }
+        aca_argmax(bu, inext, sh);
+        if (!(bu > T(0))) {
+          if (kconv < 0) kconv = k;
+          stop = true;
+        } else {
+          istar = inext;
+        }
       }
     }
-    aca_argmax(bu, inext, sh);
-    if (!(bu > T(0))) {
-      if (kconv < 0) kconv = k;
-      break;
-    }
-    istar = inext;
     __syncthreads();
+    if (!stop) continue;
+    // --- the test held: check rows (residual into V[:, k]) before stopping
+    bool again = false;
+    while (vnext < 3 && k < rmax) {
+      const int irow = aca_check_row(B.nr, vnext++);
+      bool used = false;
+      for (int l = 0; l < k; ++l) used |= sh.rows_used[l] == irow;
+      if (used) continue;
+      aca_residual_row<R, T, Op>(ef, ed, bc, P, B, Ub, Vb, m, n, k, irow, threadIdx.x, blockDim.x);
+      __syncthreads();
+      T r2 = 0;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        Op v = Vb[(long long)k * n + j];
+        r2 += v.re * v.re + v.im * v.im;
+      }
+      r2 = wsumT(r2);
+      if (lane == 0) sh.dot[0][0][wid] = r2;
+      __syncthreads();
+      T tot = 0;
+      for (int w = 0; w < ACA_WARPS; ++w) tot += sh.dot[0][0][w];
+      __syncthreads();
+      if (tot > eps * eps * normS2) {
+        istar = irow;
+        again = true;
+        break;
+      }
+    }
+    if (!again) break;
+    kconv = -1;
+    have_row = true;
   }
   if (threadIdx.x == 0) {
     rank[bi] = kconv >= 0 ? kconv : k;
@@ -1315,26 +1372,11 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
     __syncwarp();
   }
   int kconv = -1;
+  int vnext = 0;          // components whose check row has been examined (see k_aca)
+  bool have_row = false;  // V[:, k] already holds the residual row of istar
   while (k < rmax) {
-    int ie = B.r0 + istar / 3, ia = istar % 3;
-    for (int el = lane; el < B.nc; el += 32) {
-      int e = B.c0 + el;
-      cplx<T> vv[3];
-      aca_row3<R, T>(ef, ed, bc, P, ie, ia, e, vv);
-      const Op* vrow = Vb + 3 * el;
-#pragma unroll 4
-      for (int l = 0; l < k; ++l) {
-        Op ul = Ub[(long long)l * m + istar];
-        const Op* vl = vrow + (long long)l * n;
-        Op v0 = vl[0], v1 = vl[1], v2 = vl[2];
-        cplx<T> cu = mk<T>(ul.re, ul.im);
-        vv[0] = vv[0] - cu * mk<T>(v0.re, v0.im);
-        vv[1] = vv[1] - cu * mk<T>(v1.re, v1.im);
-        vv[2] = vv[2] - cu * mk<T>(v2.re, v2.im);
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Vb[(long long)k * n + 3 * el + c] = to_op<Op>(vv[c]);
-    }
+    if (!have_row) aca_residual_row<R, T, Op>(ef, ed, bc, P, B, Ub, Vb, m, n, k, istar, lane, 32);
+    have_row = false;
     __syncwarp();
     T best = T(-1);
     int jstar = 0;
@@ -1347,80 +1389,111 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
       }
     }
     warp_argmax(best, jstar);
+    bool stop = false;
     if (!(best > T(0))) {
       if (kconv < 0) kconv = k;
-      break;
-    }
-    Op pv = Vb[(long long)k * n + jstar];
-    cplx<T> ipiv = inv(mk<T>(pv.re, pv.im));
-    __syncwarp();
-    for (int j = lane; j < n; j += 32) {
-      Op v = Vb[(long long)k * n + j];
-      Vb[(long long)k * n + j] = to_op<Op>(mk<T>(v.re, v.im) * ipiv);
-    }
-    if (lane == 0) {
-      piv_i[k] = istar;
-      piv_j[k] = jstar;
-    }
-    __syncwarp();
-    int je = B.c0 + jstar / 3, jc = jstar % 3;
-    for (int il = lane; il < B.nr; il += 32) {
-      int i = B.r0 + il;
-      cplx<T> uu[3];
-      aca_col3<R, T>(ef, ed, bc, P, i, je, jc, uu);
-      const Op* ucol = Ub + 3 * il;
+      stop = true;
+    } else {
+      Op pv = Vb[(long long)k * n + jstar];
+      cplx<T> ipiv = inv(mk<T>(pv.re, pv.im));
+      __syncwarp();
+      for (int j = lane; j < n; j += 32) {
+        Op v = Vb[(long long)k * n + j];
+        Vb[(long long)k * n + j] = to_op<Op>(mk<T>(v.re, v.im) * ipiv);
+      }
+      if (lane == 0) {
+        piv_i[k] = istar;
+        piv_j[k] = jstar;
+      }
+      __syncwarp();
+      int je = B.c0 + jstar / 3, jc = jstar % 3;
+      for (int il = lane; il < B.nr; il += 32) {
+        int i = B.r0 + il;
+        cplx<T> uu[3];
+        aca_col3<R, T>(ef, ed, bc, P, i, je, jc, uu);
+        const Op* ucol = Ub + 3 * il;
 #pragma unroll 4
-      for (int l = 0; l < k; ++l) {
-        Op vl = Vb[(long long)l * n + jstar];
-        const Op* ul = ucol + (long long)l * m;
-        Op u0 = ul[0], u1 = ul[1], u2 = ul[2];
-        cplx<T> cv = mk<T>(vl.re, vl.im);
-        uu[0] = uu[0] - mk<T>(u0.re, u0.im) * cv;
-        uu[1] = uu[1] - mk<T>(u1.re, u1.im) * cv;
-        uu[2] = uu[2] - mk<T>(u2.re, u2.im) * cv;
-      }
+        for (int l = 0; l < k; ++l) {
+          Op vl = Vb[(long long)l * n + jstar];
+          const Op* ul = ucol + (long long)l * m;
+          Op u0 = ul[0], u1 = ul[1], u2 = ul[2];
+          cplx<T> cv = mk<T>(vl.re, vl.im);
+          uu[0] = uu[0] - mk<T>(u0.re, u0.im) * cv;
+          uu[1] = uu[1] - mk<T>(u1.re, u1.im) * cv;
+          uu[2] = uu[2] - mk<T>(u2.re, u2.im) * cv;
+        }
 #pragma unroll
-      for (int a = 0; a < 3; ++a) Ub[(long long)k * m + 3 * il + a] = to_op<Op>(uu[a]);
-    }
-    if (lane == 0) rows_used[k] = istar;
-    __syncwarp();
-    for (int l = lane; l < k; l += 32) Ub[(long long)k * m + rows_used[l]] = Op{};
-    __syncwarp();
-    // Frobenius norm of the approximant estimated by its diagonal terms:
-    // ||S_k||^2 ~ sum_l |u_l|^2 |v_l|^2
-    T nu2 = 0, nv2 = 0;
-    for (int i = lane; i < m; i += 32) {
-      Op a = Ub[(long long)k * m + i];
-      nu2 += a.re * a.re + a.im * a.im;
-    }
-    for (int j = lane; j < n; j += 32) {
-      Op a = Vb[(long long)k * n + j];
-      nv2 += a.re * a.re + a.im * a.im;
-    }
-    nu2 = wsumT(nu2);
-    nv2 = wsumT(nv2);
-    normS2 += nu2 * nv2;
-    ++k;
-    if (kconv < 0 && nu2 * nv2 <= eps * eps * normS2) kconv = k;
-    if (kconv >= 0 && k >= kconv + ACA_EXTRA) break;
-    T bu = T(-1);
-    int inext = 0;
-    for (int i = lane; i < m; i += 32) {
-      if (i == istar) continue;
-      Op u = Ub[(long long)(k - 1) * m + i];
-      T a = u.re * u.re + u.im * u.im;
-      if (a > bu) {
-        bu = a;
-        inext = i;
+        for (int a = 0; a < 3; ++a) Ub[(long long)k * m + 3 * il + a] = to_op<Op>(uu[a]);
+      }
+      if (lane == 0) rows_used[k] = istar;
+      __syncwarp();
+      for (int l = lane; l < k; l += 32) Ub[(long long)k * m + rows_used[l]] = Op{};
+      __syncwarp();
+      // Frobenius norm of the approximant estimated by its diagonal terms:
+      // ||S_k||^2 ~ sum_l |u_l|^2 |v_l|^2
+      T nu2 = 0, nv2 = 0;
+      for (int i = lane; i < m; i += 32) {
+        Op a = Ub[(long long)k * m + i];
+        nu2 += a.re * a.re + a.im * a.im;
+      }
+      for (int j = lane; j < n; j += 32) {
+        Op a = Vb[(long long)k * n + j];
+        nv2 += a.re * a.re + a.im * a.im;
+      }
+      nu2 = wsumT(nu2);
+      nv2 = wsumT(nv2);
+      normS2 += nu2 * nv2;
+      ++k;
+      if (kconv < 0 && nu2 * nv2 <= eps * eps * normS2) kconv = k;
+      if (kconv >= 0 && k >= kconv + ACA_EXTRA) {
+        stop = true;
+      } else {
+        T bu = T(-1);
+        int inext = 0;
+        for (int i = lane; i < m; i += 32) {
+          if (i == istar) continue;
+          Op u = Ub[(long long)(k - 1) * m + i];
+          T a = u.re * u.re + u.im * u.im;
+          if (a > bu) {
+            bu = a;
+            inext = i;
+          }
+        }
+        warp_argmax(bu, inext);
+        if (!(bu > T(0))) {
+          if (kconv < 0) kconv = k;
+          stop = true;
+        } else {
+          istar = inext;
+        }
       }
     }
-    warp_argmax(bu, inext);
-    if (!(bu > T(0))) {
-      if (kconv < 0) kconv = k;
-      break;
-    }
-    istar = inext;
     __syncwarp();
+    if (!stop) continue;
+    // the test held: check rows before stopping (see k_aca)
+    bool again = false;
+    while (vnext < 3 && k < rmax) {
+      const int irow = aca_check_row(B.nr, vnext++);
+      bool used = false;
+      for (int l = 0; l < k; ++l) used |= rows_used[l] == irow;
+      if (used) continue;
+      aca_residual_row<R, T, Op>(ef, ed, bc, P, B, Ub, Vb, m, n, k, irow, lane, 32);
+      __syncwarp();
+      T r2 = 0;
+      for (int j = lane; j < n; j += 32) {
+        Op v = Vb[(long long)k * n + j];
+        r2 += v.re * v.re + v.im * v.im;
+      }
+      r2 = wsumT(r2);
+      if (r2 > eps * eps * normS2) {
+        istar = irow;
+        again = true;
+        break;
+      }
+    }
+    if (!again) break;
+    kconv = -1;
+    have_row = true;
   }
   if (lane == 0) {
     rank[bi] = kconv >= 0 ? kconv : k;
@@ -1723,10 +1796,12 @@ __global__ void __launch_bounds__(NT) k_aca_warm_solve(const FarBlk* __restrict_
     if (p < q) Ub[(long long)q * m + pi[p]] = Op{};
   }
   if (tid == 0) {
+    // the rank is the first step at which the stopping test holds after the
+    // last step at which it fails: the reused pivots may cover parts of the
+    // block that ACA reached only through its check rows (see k_aca)
     const T eps2 = T(eps_d * eps_d);
     T S = 0;
-    int kc = ls;
-    int conv = 0;
+    int lastfail = -1;
     for (int l = 0; l < ls; ++l) {
       T nu = 0, nv = 0;
       for (int w = 0; w < NW; ++w) {
@@ -1735,12 +1810,10 @@ __global__ void __launch_bounds__(NT) k_aca_warm_solve(const FarBlk* __restrict_
       }
       T term = nu * nv;
       S += term;
-      if (term <= eps2 * S) {
-        kc = l + 1;
-        conv = 1;
-        break;
-      }
+      if (!(term <= eps2 * S)) lastfail = l;
     }
+    const int conv = lastfail + 1 < ls ? 1 : 0;
+    const int kc = conv ? lastfail + 2 : ls;
     kstart[bi] = kc;
     norm0[bi] = double(S);
     done[bi] = conv;

@@ -109,6 +109,30 @@ def test_compact_sweep_equals_pipelined_sweep(B):
         assert _rel(sols[1][k], sols[0][k]) <= 2e-5, k
 
 
+@pytest.mark.parametrize("prec,aca_tol", [(1, 1e-8), (0, 1e-5)])
+def test_flat_face_blocks(B, prec, aca_tol):
+    # cube faces: coplanar admissible blocks couple normal rows only to
+    # tangential columns and tangential rows only to normal columns; ACA must
+    # approximate both parts (its per-component check rows)
+    mesh = inputs.cube_with_cavities(n_face=24, n_cav=2, cav_radius=0.15, cav_n=8, seed=3032)
+    c = _ctx(B, B.FAR_AUTO)
+    try:
+        o = _mesh(c, B, mesh, prec, aca_tol=aca_tol)
+        T = 8.0
+        g = bem.geometry(mesh.xyz, mesh.tri)
+        rows_e = np.array([10, 500, 1500, 3000, 4000, 6000, mesh.ne - 5])
+        sel = (3 * rows_e[:, None] + np.arange(3)).ravel()
+        for k in (16, 17):  # fresh ACA, then pivot reuse
+            s = 4.0 / T + 1j * k * 2 * math.pi / T
+            c.assemble(s, o)
+            A_ref, _ = bem.system_rows(g, mesh.bc_type, mesh.pattern.astype(complex), s, MAT, rows=rows_e)
+            got = c.operator_rows(sel)
+            for q in range(len(sel)):
+                assert _rel(got[q], A_ref[q]) <= 30 * aca_tol, (k, q)
+    finally:
+        c.close()
+
+
 def test_storage_arguments(B):
     c = B.Context(0)
     try:
