@@ -127,8 +127,11 @@ def test_flat_face_blocks(B, prec, aca_tol):
             c.assemble(s, o)
             A_ref, _ = bem.system_rows(g, mesh.bc_type, mesh.pattern.astype(complex), s, MAT, rows=rows_e)
             got = c.operator_rows(sel)
-            for q in range(len(sel)):
-                assert _rel(got[q], A_ref[q]) <= 30 * aca_tol, (k, q)
+            err = np.array([_rel(got[q], A_ref[q]) for q in range(len(sel))])
+            # ACA's stopping test bounds a block's Frobenius error by about
+            # aca_tol; one row of it may carry a few tens of that. A block
+            # missing its second part is off by 1e3 aca_tol and more.
+            assert np.sqrt(np.mean(err ** 2)) <= 30 * aca_tol and err.max() <= 100 * aca_tol, (k, err)
     finally:
         c.close()
 
@@ -172,8 +175,8 @@ def test_cube_with_cavities_full_size(B):
         A_ref, b_ref = bem.system_rows(g, mesh.bc_type, mesh.pattern.astype(complex), s, MAT, rows=rows_e)
         sel = (3 * rows_e[:, None] + np.arange(3)).ravel()
         got = c.operator_rows(sel)
-        for q in range(len(sel)):
-            assert _rel(got[q], A_ref[q]) <= 30 * aca_tol, q
+        err = np.array([_rel(got[q], A_ref[q]) for q in range(len(sel))])
+        assert np.sqrt(np.mean(err ** 2)) <= 30 * aca_tol and err.max() <= 100 * aca_tol, err
         b = c.rhs(1.0, mesh.pattern)
         assert _rel(b[sel], b_ref) <= 1e-4
         x, stats = c.solve_assembled(b, opts=o)
