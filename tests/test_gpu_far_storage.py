@@ -109,7 +109,7 @@ def test_compact_sweep_equals_pipelined_sweep(B):
         assert _rel(sols[1][k], sols[0][k]) <= 2e-5, k
 
 
-@pytest.mark.parametrize("prec,aca_tol", [(1, 1e-8), (0, 1e-5)])
+@pytest.mark.parametrize("prec,aca_tol", [(1, 1e-6), (0, 1e-5)])
 def test_flat_face_blocks(B, prec, aca_tol):
     # cube faces: coplanar admissible blocks couple normal rows only to
     # tangential columns and tangential rows only to normal columns; ACA must
@@ -127,6 +127,9 @@ def test_flat_face_blocks(B, prec, aca_tol):
             c.assemble(s, o)
             A_ref, _ = bem.system_rows(g, mesh.bc_type, mesh.pattern.astype(complex), s, MAT, rows=rows_e)
             got = c.operator_rows(sel)
+            info = c.far_block_info()
+            cap = np.minimum(3 * np.minimum(info[:, 0], info[:, 1]), 128)
+            assert np.all(info[:, 2] < cap), k  # every block met the test below its rank cap
             err = np.array([_rel(got[q], A_ref[q]) for q in range(len(sel))])
             # ACA's stopping test bounds a block's Frobenius error by about
             # aca_tol; one row of it may carry a few tens of that. A block
