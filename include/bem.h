@@ -277,6 +277,31 @@ typedef struct bem_far_storage {
 } bem_far_storage;
 int bem_get_far_storage(bem_ctx* ctx, bem_far_storage* out);
 
+/* ---- several meshes in one context ------------------------------------------
+ * Independent problems (the batched sweep of meshes of uneven size) share one
+ * GPU: each added mesh gets its own context state and non-blocking stream,
+ * and bem_solve_sweep_batched drives every mesh's sweep from its own host
+ * thread, so small meshes fill the GPU around large ones. The material and
+ * window of the context apply to every mesh (set them before the sweep); far
+ * storage and pivot reuse settings are taken when the mesh is added. The
+ * single-mesh calls (bem_mesh, bem_solve_sweep, ...) keep their own mesh. */
+/* Adds a mesh (arguments as bem_mesh) and returns its id 0, 1, ... in
+ * *mesh_id. Errors: as bem_mesh. */
+int bem_add_mesh(bem_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t ne,
+                 const int8_t* bc_type, const bem_opts* opts, int32_t* mesh_id);
+/* Number of added meshes (or INVALID_ARG). */
+int bem_mesh_count(const bem_ctx* ctx);
+/* Sweeps every added mesh with one load history and its own prescribed
+ * pattern bc_patterns[id] (ne x 3 each). stats (may be NULL): per mesh id,
+ * n_omega / 2 + 1 entries, mesh-major. Returns the first hard error of any
+ * mesh, else NOT_CONVERGED if any frequency of any mesh missed the tolerance,
+ * else OK; every mesh's results are kept. */
+int bem_solve_sweep_batched(bem_ctx* ctx, double T, int32_t n_omega, const double* load_hist,
+                            const double* const* bc_patterns, const bem_opts* opts, bem_freq_stats* stats);
+/* As bem_get_frequency_solution and bem_time_response, for mesh mesh_id. */
+int bem_mesh_frequency_solution(bem_ctx* ctx, int32_t mesh_id, int32_t k, double* out);
+int bem_mesh_time_response(bem_ctx* ctx, int32_t mesh_id, const int64_t* dofs, int64_t ndof, double* out);
+
 /* ---- learned initial guess (BEM_GUESS_MLP) ---------------------------------
  * The paper's extrapolation (Sec. 4.2) fits a_k^(0) in the span of the last
  * K solutions. The learned guess adds one candidate column p_k to that span,

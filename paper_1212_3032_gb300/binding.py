@@ -33,6 +33,8 @@ EXPORTED = [
     "bem_mlp_num_params", "bem_mlp_init", "bem_mlp_set_training", "bem_mlp_set_weights", "bem_mlp_get_weights",
     "bem_mlp_forward", "bem_mlp_gradient", "bem_mlp_train_step", "bem_set_aca_reuse",
     "bem_far_block_info", "bem_set_far_storage", "bem_get_far_storage",
+    "bem_add_mesh", "bem_mesh_count", "bem_solve_sweep_batched", "bem_mesh_frequency_solution",
+    "bem_mesh_time_response",
 ]
 
 
@@ -120,6 +122,11 @@ def load_library(path: str = LIB_PATH):
         "bem_set_aca_reuse": (ctypes.c_int, [P, ctypes.c_int]),
         "bem_far_block_info": (ctypes.c_int, [P, I64, P, P]),
         "bem_set_far_storage": (ctypes.c_int, [P, ctypes.c_int32, I64]),
+        "bem_add_mesh": (ctypes.c_int, [P, P, I64, P, I64, P, P, P]),
+        "bem_mesh_count": (ctypes.c_int, [P]),
+        "bem_solve_sweep_batched": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int32, P, P, P, P]),
+        "bem_mesh_frequency_solution": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
+        "bem_mesh_time_response": (ctypes.c_int, [P, ctypes.c_int32, P, I64, P]),
         "bem_get_far_storage": (ctypes.c_int, [P, P]),
         "bem_mlp_num_params": (I64, []),
         "bem_mlp_init": (ctypes.c_int, [P, ctypes.c_uint64]),
@@ -272,6 +279,53 @@ class Context:
             raise ValueError("out must hold n_omega x ndof values")
         self._check(self.lib.bem_time_response_dev(self.h, _tptr(dofs_t, "torch.int64"), dofs_t.numel(),
                                                    _tptr(out_t, "torch.float64")))
+
+    # --- several meshes (batched sweeps) -----------------------------------
+    def add_mesh(self, xyz, tri, bc_type, opts: Opts | None = None) -> int:
+        xyz = _f64(xyz)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        bc = np.ascontiguousarray(bc_type, dtype=np.int8)
+        mid = ctypes.c_int32(-1)
+        self._check(self.lib.bem_add_mesh(self.h, _ptr(xyz), xyz.shape[0], _ptr(tri), tri.shape[0], _ptr(bc),
+                                          ctypes.byref(opts) if opts else None, ctypes.byref(mid)))
+        if not hasattr(self, "batch_ne"):
+            self.batch_ne = []
+        self.batch_ne.append(int(tri.shape[0]))
+        return mid.value
+
+    def mesh_count(self) -> int:
+        n = self.lib.bem_mesh_count(self.h)
+        self._check(min(n, 0))
+        return n
+
+    def solve_sweep_batched(self, T, n_omega, load_hist, patterns, opts: Opts | None = None,
+                            allow_unconverged=False):
+        """Sweeps every added mesh; returns one list of per-frequency stats per mesh."""
+        load = _f64(load_hist)
+        pats = [_f64(p) for p in patterns]
+        arr = (ctypes.c_void_p * len(pats))(*[p.ctypes.data for p in pats])
+        nf = n_omega // 2 + 1
+        stats = (FreqStats * (nf * len(pats)))()
+        rc = self.lib.bem_solve_sweep_batched(self.h, float(T), int(n_omega), _ptr(load), arr,
+                                              ctypes.byref(opts) if opts else None, stats)
+        self._check(rc, allow=(-5,) if allow_unconverged else ())
+        self.batch_n_omega = n_omega
+        return [[stats[m * nf + k].as_dict() for k in range(nf)] for m in range(len(pats))]
+
+    def _batch_ne(self, mesh_id):
+        ne = getattr(self, "batch_ne", [])
+        return ne[mesh_id] if 0 <= mesh_id < len(ne) else 0  # unknown ids: the library reports the error
+
+    def mesh_frequency_solution(self, mesh_id, k):
+        out = np.zeros(3 * self._batch_ne(mesh_id), dtype=np.complex128)
+        self._check(self.lib.bem_mesh_frequency_solution(self.h, int(mesh_id), int(k), _ptr(out)))
+        return out
+
+    def mesh_time_response(self, mesh_id, dofs):
+        dofs = np.ascontiguousarray(dofs, dtype=np.int64)
+        out = np.zeros((getattr(self, "batch_n_omega", 0), dofs.size), dtype=np.float64)
+        self._check(self.lib.bem_mesh_time_response(self.h, int(mesh_id), _ptr(dofs), dofs.size, _ptr(out)))
+        return out
 
     # --- step-level entry points -------------------------------------------
     def load_dft(self, T, n_omega, eta, load_hist):

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "bem_internal.h"
@@ -259,6 +260,33 @@ void prof_end(bem_ctx* ctx, cudaEvent_t a, int kind, double base = 0.0, double m
   ctx->pending.push_back({a, b, base, mult, kind == 0 ? ctx->prof_slot : 0, kind});
 }
 
+// Cooperative (grid-synchronising) launches of a context that shares the GPU
+// with other contexts' streams (the meshes of a batched sweep) go through one
+// stream common to those contexts, ordered against the context's own stream
+// by events: two such grids then never wait for residency at the same time.
+// A lone context launches on its own stream.
+class CoopLane {
+ public:
+  CoopLane(bem_ctx* ctx, cudaStream_t st) : ctx_(ctx), st_(st) {
+    if (!ctx->coop_stream) return;
+    e_ = cudaEventRecord(ctx->coop_in, st);
+    if (e_ == cudaSuccess) e_ = cudaStreamWaitEvent(ctx->coop_stream, ctx->coop_in, 0);
+  }
+  cudaError_t status() const { return e_; }
+  cudaStream_t stream() const { return ctx_->coop_stream ? ctx_->coop_stream : st_; }
+  cudaError_t join() {
+    if (!ctx_->coop_stream) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(ctx_->coop_out, ctx_->coop_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st_, ctx_->coop_out, 0);
+    return e;
+  }
+
+ private:
+  bem_ctx* ctx_;
+  cudaStream_t st_;
+  cudaError_t e_ = cudaSuccess;
+};
+
 // Exchanges the operator set in use with the other one (host pointers only:
 // work already enqueued keeps the buffers it was given).
 template <typename T> void swap_buf(DevBuf<T>& a, DevBuf<T>& b) {
@@ -418,6 +446,17 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
     cudaEventDestroy(p.b);
   }
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  for (size_t i = 0; i < ctx->batch.size(); ++i) {
+    cudaStream_t bs = ctx->batch[i]->stream;
+    bem_destroy(ctx->batch[i]);
+    cudaStreamDestroy(bs);
+  }
+  if (ctx->coop_in) cudaEventDestroy(ctx->coop_in);
+  if (ctx->coop_out) cudaEventDestroy(ctx->coop_out);
+  if (ctx->coop_owner && ctx->coop_stream) {
+    cudaStreamSynchronize(ctx->coop_stream);
+    cudaStreamDestroy(ctx->coop_stream);
+  }
   mlp_free(ctx);
   delete ctx;
 }
@@ -1293,7 +1332,12 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
                                                reinterpret_cast<c128*>(wbuf.p), 1, st);
     CK("arnoldi matvec");
     prof_end_hmv(ctx, ev, sizeof(Vb), sizeof(Vb), sizeof(Vb), 1);
-    BEM_CUDA_TRY(launch_arnoldi_orth<Vb>(V, N, j, wbuf.p, N, orth_part, hd, m, st));
+    {
+      CoopLane lane(ctx, st);
+      BEM_CUDA_TRY(lane.status());
+      BEM_CUDA_TRY(launch_arnoldi_orth<Vb>(V, N, j, wbuf.p, N, orth_part, hd, m, lane.stream()));
+      BEM_CUDA_TRY(lane.join());
+    }
     CK("arnoldi");
     BEM_CUDA_TRY(cudaMemcpyAsync(hcol + 2 * j * slot_len, hd, slot_len * sizeof(c128), cudaMemcpyDeviceToHost, st));
     BEM_CUDA_TRY(cudaEventRecord(ctx->col_events[j], st));
@@ -1456,7 +1500,12 @@ int sem_impl(bem_ctx* ctx, const c128* const* X, int K, const c128* b, c128* a0,
   for (int q = 0; q < C; q += 4) TRY(apply_fast(ctx, Xc + q * N, Y + q * N, std::min(4, C - q)));
   BEM_CUDA_TRY(ctx->sem_part.ensure((size_t)3 * (SEM_MAXC + 1) * arnoldi_orth_max_blocks()));
   BEM_CUDA_TRY(ctx->sem_res.ensure(2));
-  BEM_CUDA_TRY(launch_sem_fit(cols.data(), C, K, Y, b, Q, ctx->sem_part.p, a0, ctx->sem_res.p, N, st));
+  {
+    CoopLane lane(ctx, st);
+    BEM_CUDA_TRY(lane.status());
+    BEM_CUDA_TRY(launch_sem_fit(cols.data(), C, K, Y, b, Q, ctx->sem_part.p, a0, ctx->sem_res.p, N, lane.stream()));
+    BEM_CUDA_TRY(lane.join());
+  }
   CK("sem fit");
   if (want_res)
     BEM_CUDA_TRY(cudaMemcpyAsync(ctx->host_red + SEM_RES_SLOT, ctx->sem_res.p, 2 * sizeof(double),
@@ -2068,4 +2117,110 @@ extern "C" int bem_get_profile(bem_ctx* ctx, bem_profile* out) {
   out->aca_blocks = ctx->prof_aca_blocks;
   out->aca_stepped = ctx->prof_aca_continued + (ctx->prof_dev.p ? lr[0] : 0);
   return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// several meshes in one context: batched sweeps
+// ---------------------------------------------------------------------------
+extern "C" int bem_add_mesh(bem_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t ne,
+                            const int8_t* bc_type, const bem_opts* opts, int32_t* mesh_id) {
+  if (!ctx || !mesh_id) return BEM_ERR_INVALID_ARG;
+  *mesh_id = -1;
+  TRY(set_device(ctx));
+  if (!ctx->coop_stream) {
+    BEM_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->coop_stream, cudaStreamNonBlocking));
+    ctx->coop_owner = true;
+  }
+  cudaStream_t s = nullptr;
+  BEM_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  bem_ctx* child = nullptr;
+  int rc = bem_create(&child, ctx->device, s);
+  if (rc != BEM_OK) {
+    cudaStreamDestroy(s);
+    return fail(ctx, rc, "could not create the mesh's context");
+  }
+  child->coop_stream = ctx->coop_stream;
+  rc = cudaEventCreateWithFlags(&child->coop_in, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&child->coop_out, cudaEventDisableTiming) == cudaSuccess
+           ? BEM_OK
+           : BEM_ERR_CUDA;
+  if (rc == BEM_OK && ctx->have_mat) rc = bem_set_material(child, ctx->E, ctx->nu, ctx->rho);
+  if (rc == BEM_OK) rc = bem_set_far_storage(child, ctx->far_mode_req, ctx->far_ws_req);
+  if (rc == BEM_OK) rc = bem_set_aca_reuse(child, ctx->aca_reuse ? 1 : 0);
+  if (rc == BEM_OK) rc = bem_mesh(child, xyz, nv, tri, ne, bc_type, opts);
+  if (rc != BEM_OK) {
+    std::string msg = child->err;
+    bem_destroy(child);
+    cudaStreamDestroy(s);
+    return fail(ctx, rc, "bem_add_mesh: " + msg);
+  }
+  ctx->batch.push_back(child);
+  *mesh_id = (int32_t)(ctx->batch.size() - 1);
+  return BEM_OK;
+}
+
+extern "C" int bem_mesh_count(const bem_ctx* ctx) { return ctx ? (int)ctx->batch.size() : BEM_ERR_INVALID_ARG; }
+
+static int batch_child(bem_ctx* ctx, int32_t mesh_id, bem_ctx** out) {
+  if (mesh_id < 0 || mesh_id >= (int32_t)ctx->batch.size()) return fail(ctx, BEM_ERR_INVALID_ARG, "unknown mesh id");
+  *out = ctx->batch[mesh_id];
+  return BEM_OK;
+}
+
+extern "C" int bem_solve_sweep_batched(bem_ctx* ctx, double T, int32_t n_omega, const double* load_hist,
+                                       const double* const* bc_patterns, const bem_opts* opts,
+                                       bem_freq_stats* stats) {
+  if (!ctx || !load_hist || !bc_patterns) return BEM_ERR_INVALID_ARG;
+  const int nm = (int)ctx->batch.size();
+  if (!nm) return fail(ctx, BEM_ERR_NO_MESH, "no mesh added (bem_add_mesh)");
+  if (!ctx->have_mat) return fail(ctx, BEM_ERR_STATE, "material not set");
+  for (int i = 0; i < nm; ++i)
+    if (!bc_patterns[i]) return fail(ctx, BEM_ERR_INVALID_ARG, "missing boundary pattern");
+  TRY(set_device(ctx));
+  for (bem_ctx* c : ctx->batch) {
+    TRY(bem_set_material(c, ctx->E, ctx->nu, ctx->rho));
+    TRY(bem_set_window(c, ctx->eta, ctx->window));
+  }
+  const int nf = n_omega / 2 + 1;
+  std::vector<int> rc(nm, BEM_OK);
+  std::vector<std::thread> th;
+  th.reserve(nm);
+  for (int i = 0; i < nm; ++i)
+    th.emplace_back([&, i]() {
+      if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        rc[i] = BEM_ERR_CUDA;
+        return;
+      }
+      rc[i] = bem_solve_sweep(ctx->batch[i], T, n_omega, load_hist, bc_patterns[i], opts,
+                              stats ? stats + (long long)i * nf : nullptr);
+    });
+  for (auto& t : th) t.join();
+  int worst = BEM_OK;
+  for (int i = 0; i < nm; ++i) {
+    if (rc[i] == BEM_OK) continue;
+    if (worst == BEM_OK || worst == BEM_ERR_NOT_CONVERGED) {
+      worst = rc[i];
+      fail(ctx, rc[i], "mesh " + std::to_string(i) + ": " + ctx->batch[i]->err);
+    }
+  }
+  return worst;
+}
+
+extern "C" int bem_mesh_frequency_solution(bem_ctx* ctx, int32_t mesh_id, int32_t k, double* out) {
+  if (!ctx) return BEM_ERR_INVALID_ARG;
+  bem_ctx* c = nullptr;
+  TRY(batch_child(ctx, mesh_id, &c));
+  int rc = bem_get_frequency_solution(c, k, out);
+  if (rc != BEM_OK) fail(ctx, rc, c->err);
+  return rc;
+}
+
+extern "C" int bem_mesh_time_response(bem_ctx* ctx, int32_t mesh_id, const int64_t* dofs, int64_t ndof,
+                                      double* out) {
+  if (!ctx) return BEM_ERR_INVALID_ARG;
+  bem_ctx* c = nullptr;
+  TRY(batch_child(ctx, mesh_id, &c));
+  int rc = bem_time_response(c, dofs, ndof, out);
+  if (rc != BEM_OK) fail(ctx, rc, c->err);
+  return rc;
 }

@@ -310,6 +310,14 @@ struct bem_ctx {
   bem::DevBuf<bem::c128> sem_part;     // its partial sums
   bem::DevBuf<double> sem_res;         // its residual estimates
 
+  // several meshes in one context (bem_add_mesh): each in a child context
+  // with its own non-blocking stream; the children's cooperative launches
+  // share one stream (CoopLane)
+  std::vector<bem_ctx*> batch;
+  cudaStream_t coop_stream = nullptr;  // set in children (and their parent) only
+  bool coop_owner = false;
+  cudaEvent_t coop_in = nullptr, coop_out = nullptr;
+
   // sweep results
   int n_omega = 0;
   double T = 0;

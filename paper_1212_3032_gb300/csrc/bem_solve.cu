@@ -627,15 +627,15 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_arnoldi_orth(Vb* __restrict__ 
 
 template <typename Vb>
 int orth_grid(long long n) {
-  static int cap[2] = {0, 0};  // resident blocks (per process; one device)
-  int& c = cap[sizeof(Vb) == 8 ? 0 : 1];
-  if (!c) {
+  // resident blocks (per process and instantiation; one device), computed
+  // once under the thread-safe initialisation of a local static
+  static const int c = [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi_orth<Vb>, ORTH_THREADS, 0);
-    c = std::max(1, sms * std::max(1, per));
-  }
+    return std::max(1, sms * std::max(1, per));
+  }();
   // about 256 rows per block, at most one wave of resident blocks
   return (int)std::max<long long>(1, std::min<long long>(c, (n + 255) / 256));
 }

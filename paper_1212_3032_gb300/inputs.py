@@ -20,6 +20,9 @@ synthetic stand-in with the sizes and structure the text describes):
 * ``ellipsoid_mesh``: geodesic sphere mapped to an ellipsoid.
 * ``cube_with_cavities``: the large example of Sec. 5.3 (cube with spherical
   cavities, bottom fixed, top loaded), built at a chosen resolution.
+* ``ball_with_void``: a solid ball with an off-centre spherical void, outer
+  surface under pressure (geodesic n=28 outside and n=15 inside give
+  15,680 + 4,500 = 20,180 triangles).
 * ``heaviside_history``: P(n dt) for a step load, with P(0) = 1/2.
 """
 from __future__ import annotations
@@ -313,3 +316,24 @@ def cube_with_cavities(n_face: int = 118, n_cav: int = 8, cav_radius: float = 0.
     pattern[top, 2] = traction
     return Mesh(xyz=xyz, tri=tri, bc_type=bc, pattern=pattern,
                 name=f"cube_{n_cav}cav_{ne}")
+
+
+def ball_with_void(n_outer: int = 28, n_inner: int = 15, radius: float = 1.0,
+                   void_radius: float = 0.3, void_center=(0.35, 0.2, -0.1),
+                   pressure: float = 1.0) -> Mesh:
+    """Solid ball of ``radius`` with a spherical void, both geodesic spheres.
+
+    The solid is the ball minus the void: the outer sphere's normals point
+    away from the centre, the void's into the void. Every element is on
+    Gamma_sigma; the outer surface carries t = -p n (a uniform pressure), the
+    void wall is traction free.
+    """
+    xo, to = geodesic_sphere(n_outer, radius=radius)
+    xi, ti = geodesic_sphere(n_inner, radius=void_radius, center=void_center, inward=True)
+    xyz = np.concatenate([xo, xi])
+    tri = np.concatenate([to, ti + xo.shape[0]]).astype(np.int32)
+    ne = tri.shape[0]
+    pattern = np.zeros((ne, 3))
+    pattern[:to.shape[0]] = -pressure * _normals(xo, to)
+    return Mesh(xyz=xyz, tri=tri, bc_type=np.zeros(ne, dtype=np.int8), pattern=pattern,
+                name=f"ball_void_{ne}")

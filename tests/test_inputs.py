@@ -61,3 +61,24 @@ def test_batched_meshes_uneven():
     sizes = [m.ne for m in ms]
     assert len(set(sizes)) == 4
     assert all(150 <= n <= 2600 for n in sizes)
+
+
+def test_ball_with_void():
+    m = inputs.ball_with_void(n_outer=6, n_inner=3)
+    n_out = 20 * 36
+    assert m.ne == n_out + 20 * 9
+    assert _edges_closed(m.tri)
+    p = m.xyz[m.tri]
+    c = p.mean(axis=1)
+    nrm = np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0])
+    # outer normals away from the centre, void normals into the void
+    assert np.all(np.einsum("ij,ij->i", nrm[:n_out], c[:n_out]) > 0)
+    vc = np.array([0.35, 0.2, -0.1])
+    assert np.all(np.einsum("ij,ij->i", nrm[n_out:], c[n_out:] - vc) < 0)
+    # pressure on the outer surface only: t = -p n points inward there
+    assert np.all(np.einsum("ij,ij->i", m.pattern[:n_out], c[:n_out]) < 0)
+    assert np.all(m.pattern[n_out:] == 0) and np.all(m.bc_type == inputs.BC_TRACTION)
+    # enclosed volume (divergence theorem) = ball minus void
+    vol = np.sum(np.einsum("ij,ij->i", p[:, 0], np.cross(p[:, 1], p[:, 2]))) / 6
+    assert abs(vol - 4 / 3 * np.pi * (1 - 0.3 ** 3)) < 0.1
+    assert inputs.ball_with_void().ne == 20180
