@@ -9,7 +9,7 @@ sphere-with-void mesh, at their full sizes.
   a box and an ellipsoid match the oracle on sampled operator rows.
 * Learned guess: the network is trained online on the 320-triangle cavity
   sweep, then proposes for the 20,180-triangle ball with an off-centre void
-  (128 samples). Its guess residual is never above the extrapolation's from
+  (128 samples, the same sample interval). Its guess residual is never above the extrapolation's from
   the same fit, its solutions match the extrapolation-only sweep's to the
   solver tolerance, and sampled rows of the ball's operator match the oracle.
 """
@@ -49,7 +49,9 @@ def test_batched_sweep_uneven_meshes(B):
     meshes = inputs.batched_meshes()
     sizes = [m.ne for m in meshes]
     assert len(meshes) == 16 and min(sizes) >= 1500 and max(sizes) <= 45000
-    T, N = 16.0, 128
+    # T = 64: at the highest of the 65 frequencies the coarsest mesh still has
+    # about 4.4 elements per shear wavelength (8 for the median mesh)
+    T, N = 64.0, 128
     eta = 5.0 / T
     hist = inputs.heaviside_history(N)
     o = B.default_opts(dense=0, precision=0, aca_tol=1e-5, leaf_size=64, tol=1e-5)
@@ -118,7 +120,10 @@ def test_learned_guess_on_ball_with_void(B):
         ctx.close()
     ball = inputs.ball_with_void()
     assert ball.ne == 20180
-    N = 128
+    # T = 32 (the same sample interval as the training sweep): about 8
+    # elements per shear wavelength at the highest frequency
+    T, N = 32.0, 128
+    eta = 5.0 / T
     hist = inputs.heaviside_history(N)
     res = {}
     for guess in (B.GUESS_MLP, B.GUESS_SEM):
