@@ -122,7 +122,7 @@ def test_flat_face_blocks(B, prec, aca_tol):
         g = bem.geometry(mesh.xyz, mesh.tri)
         rows_e = np.array([10, 500, 1500, 3000, 4000, 6000, mesh.ne - 5])
         sel = (3 * rows_e[:, None] + np.arange(3)).ravel()
-        for k in (16, 17):  # fresh ACA, then pivot reuse
+        for k in (8, 9):  # fresh ACA, then pivot reuse (ranks well below the cap of 128)
             s = 4.0 / T + 1j * k * 2 * math.pi / T
             c.assemble(s, o)
             A_ref, _ = bem.system_rows(g, mesh.bc_type, mesh.pattern.astype(complex), s, MAT, rows=rows_e)
