@@ -20,6 +20,8 @@ synthetic stand-in with the sizes and structure the text describes):
 * ``ellipsoid_mesh``: geodesic sphere mapped to an ellipsoid.
 * ``cube_with_cavities``: the large example of Sec. 5.3 (cube with spherical
   cavities, bottom fixed, top loaded), built at a chosen resolution.
+* ``rod_problem``: the prismatic rod of Sec. 5.1 (3 x 1 x 1, one end fixed,
+  a step traction on the other, sides free); h = 1/21 gives 12,348 triangles.
 * ``ball_with_void``: a solid ball with an off-centre spherical void, outer
   surface under pressure (geodesic n=28 outside and n=15 inside give
   15,680 + 4,500 = 20,180 triangles).
@@ -337,3 +339,23 @@ def ball_with_void(n_outer: int = 28, n_inner: int = 15, radius: float = 1.0,
     pattern[:to.shape[0]] = -pressure * _normals(xo, to)
     return Mesh(xyz=xyz, tri=tri, bc_type=np.zeros(ne, dtype=np.int8), pattern=pattern,
                 name=f"ball_void_{ne}")
+
+
+def rod_problem(length: float = 3.0, h: float = 1.0 / 21, pressure: float = 1.0) -> Mesh:
+    """Prismatic rod [0, length] x [-1/2, 1/2]^2 (the rod example, Sec. 5.1).
+
+    The end x = 0 is fixed (Gamma_u, u = 0); the end x = length carries the
+    traction t = -pressure n (a compressive step when multiplied by H(t));
+    the four sides are traction free.
+    """
+    xyz, tri = box_mesh(length, 1.0, 1.0, h, center=(length / 2, 0.0, 0.0))
+    cen = _centroids(xyz, tri)
+    nrm = _normals(xyz, tri)
+    ne = tri.shape[0]
+    bc = np.zeros(ne, dtype=np.int8)
+    pattern = np.zeros((ne, 3))
+    fixed = np.abs(cen[:, 0]) < 1e-9 * length
+    loaded = np.abs(cen[:, 0] - length) < 1e-9 * length
+    bc[fixed] = BC_DISPLACEMENT
+    pattern[loaded] = -pressure * nrm[loaded]
+    return Mesh(xyz=xyz, tri=tri, bc_type=bc, pattern=pattern, name=f"rod_{ne}")

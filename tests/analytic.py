@@ -9,6 +9,16 @@ q = s / c_p, and the wall condition sigma_rr(a) = -p fixes C. At r = a
 
 At s = 0 this is the Lame result p a / (4 mu). ``cavity_field`` returns the
 whole radial field so a test can check the ODE and the wall condition.
+
+Prismatic rod (Sec. 5.1) with Poisson's ratio 0: the 3-D problem is exactly
+1-D (uniaxial stress is uniaxial strain when nu = 0), u_x(x, s) solves
+E u'' = rho s^2 u with u(0) = 0 (fixed end) and E u'(L) = -p (the
+compressive traction -p n on the end x = L), c = sqrt(E / rho):
+
+    u_x(x, s) = -(p c / (E s)) sinh(s x / c) / cosh(s L / c),
+
+so u_x(L, s) = -(p c / (E s)) tanh(s L / c), and the traction on the fixed
+end (normal -x) is t_x(0, s) = -E u'(0) = p / cosh(s L / c).
 """
 import math
 
@@ -43,3 +53,22 @@ def cavity_step_response(t, a, mu, lam, rho, p=1.0):
         Nk = p * a * (1 + a * pk / cp)
         out = out + Nk / (pk * dD) * np.exp(pk * t)
     return out.real
+
+
+def rod_field(x, s, L, E, rho, p=1.0):
+    """u_x(x, s) of the rod, 0 <= x <= L."""
+    c = math.sqrt(E / rho)
+    s = np.asarray(s, dtype=np.complex128)
+    return -(p * c / (E * s)) * np.sinh(s * x / c) / np.cosh(s * L / c)
+
+
+def rod_end_displacement(s, L, E, rho, p=1.0):
+    c = math.sqrt(E / rho)
+    s = np.asarray(s, dtype=np.complex128)
+    return -(p * c / (E * s)) * np.tanh(s * L / c)
+
+
+def rod_fixed_traction(s, L, E, rho, p=1.0):
+    c = math.sqrt(E / rho)
+    s = np.asarray(s, dtype=np.complex128)
+    return p / np.cosh(s * L / c)

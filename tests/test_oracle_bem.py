@@ -208,6 +208,47 @@ def test_cavity_converges_to_closed_form():
         assert e6 < 0.03
 
 
+def test_rod_closed_form_pins_itself():
+    """The rod's 1-D field solves E u'' = rho s^2 u, u(0) = 0, E u'(L) = -p."""
+    L, E, rho = 3.0, 1.0, 1.0
+    for s in (0.3 + 0.4j, 0.2 + 1.0j):
+        h = 1e-4
+        f = lambda x: analytic.rod_field(x, s, L, E, rho)
+        x = 1.7
+        upp = (f(x + h) - 2 * f(x) + f(x - h)) / h**2
+        assert abs(E * upp - rho * s * s * f(x)) <= 1e-5 * abs(rho * s * s * f(x))
+        assert abs(f(0.0)) == 0.0
+        assert abs(E * (f(L) - f(L - h)) / h + 1.0) <= 1e-3
+        assert analytic.rod_end_displacement(s, L, E, rho) == pytest.approx(f(L))
+        # traction on the fixed end (outward normal -x): -E u'(0)
+        assert analytic.rod_fixed_traction(s, L, E, rho) == pytest.approx(-E * (f(h) - f(-h)) / (2 * h), rel=1e-6)
+
+
+def _rod_errors(h, s):
+    mat = kernels.Material(1.0, 0.0, 1.0)
+    m = inputs.rod_problem(h=h)
+    g = bem.geometry(m.xyz, m.tri)
+    A, b = bem.system_rows(g, m.bc_type, m.pattern.astype(complex), s, mat)
+    a = solvers.direct_solve(A, b).reshape(-1, 3)
+    right = np.abs(g.c[:, 0] - 3.0) < 1e-9
+    left = np.abs(g.c[:, 0]) < 1e-9
+    uL = analytic.rod_end_displacement(s, 3.0, 1.0, 1.0)
+    t0 = analytic.rod_fixed_traction(s, 3.0, 1.0, 1.0)
+    return abs(a[right, 0].mean() - uL) / abs(uL), abs(a[left, 0].mean() - t0) / abs(t0)
+
+
+def test_rod_mixed_bc_converges_to_1d_solution():
+    """Mixed boundary conditions (fixed end: traction unknowns, -U columns)
+    against the exact 1-D rod solution: the free-end displacement and the
+    fixed-end traction converge as the mesh is refined."""
+    s = 0.3 + 0.4j
+    e_coarse = _rod_errors(0.5, s)
+    e_fine = _rod_errors(1.0 / 3, s)
+    for ec, ef in zip(e_coarse, e_fine):
+        assert ef < 0.8 * ec
+        assert ef < 0.03
+
+
 def test_far_bands_against_brute_force():
     """Q2 and Q1 bands on a finer sphere (well-resolved frequency)."""
     mesh = inputs.cavity_problem(8)
