@@ -53,9 +53,9 @@ MAT = dict(E=1.0, nu=0.25, rho=1.0)
 
 # DRAM read + write of one H-matrix product (k_hmv_t + k_hmv_tasks_list) at
 # k = n_omega / 4 of cavity5120, from the ncu capture of `bench.py
-# --profile-case`; the same product's algorithmic bytes are 874.5 MB (bytes
+# --profile-case`; the same product's algorithmic bytes are 887.3 MB (bytes
 # counted by the library), so the kernels stream every operator entry once.
-HMV_TRAFFIC_K64 = 893_764_864
+HMV_TRAFFIC_K64 = 910_439_680
 
 
 def _peaks():
@@ -364,7 +364,7 @@ def run_ours(args, cfg):
         "roofline": {"kernel": "H-matrix product (k_hmv_t + k_hmv_tasks_list)", "bound": "hbm", "achieved": hmv_gbs,
                      "peak": peak, "unit": "GB/s", "frac": (hmv_gbs / peak) if hmv_gbs else None,
                      "peak_source": peak_kind, "traffic": HMV_TRAFFIC_K64,
-                     "traffic_note": "DRAM bytes of one product at k = n_omega/4 (ncu); algorithmic 874.5 MB there",
+                     "traffic_note": "DRAM bytes of one product at k = n_omega/4 (ncu); algorithmic 887.3 MB there",
                      "launches": prof["hmv_launches"], "ms_total": prof["hmv_ms"],
                      "note": "timed inside the sweep, where the next frequency's assembly shares the GPU",
                      "isolated": {"achieved": iso_gbs, "frac": (iso_gbs / peak) if iso_gbs else None,
@@ -386,6 +386,76 @@ def run_ours(args, cfg):
     print(json.dumps(out))
 
 
+def run_batched(args):
+    """Sixteen uneven meshes (closed boxes and ellipsoids of 2k-37k triangles,
+    cavity problems, T = 64, 128 samples): converged solves/s of one batched
+    sweep (bem_add_mesh + bem_solve_sweep_batched, compact far-field storage)
+    against the same meshes swept one after another through single-mesh
+    contexts (default storage, assembly overlapped with the solve). Wall time
+    around each complete call (both calls return after the GPU work)."""
+    import torch
+
+    from paper_1212_3032_gb300 import binding, build, inputs
+
+    build.build()
+    torch.cuda.set_device(0)
+    meshes = inputs.batched_meshes()
+    T, n_omega = 64.0, 128
+    eta = 5.0 / T
+    nf = n_omega // 2 + 1
+    load = inputs.heaviside_history(n_omega)
+    opts = binding.default_opts(leaf_size=64, aca_tol=1e-5, tol=1e-5, precision=binding.PREC_C64_MIXED,
+                                guess=binding.GUESS_SEM, sem_k=4)
+    out = {"metric": "converged frequency solves/s, 16 uneven meshes swept on one GPU", "unit": "solves/s",
+           "config": {"workload": "batched16", "triangles": [m.ne for m in meshes], "n_omega": n_omega, "T": T,
+                      "aca_tol": 1e-5, "gmres_tol": 1e-5, "guess": "SEM K=4"}}
+    c = binding.Context(0)
+    try:
+        c.set_material(**MAT)
+        c.set_window(eta, binding.WIN_HANNING)
+        c.set_far_storage(binding.FAR_COMPACT)
+        for m in meshes:
+            c.add_mesh(m.xyz, m.tri, m.bc_type, opts)
+        pats = [m.pattern for m in meshes]
+        times = []
+        for _ in range(2):  # the first sweep is the warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = c.solve_sweep_batched(T, n_omega, load, pats, opts, allow_unconverged=True)
+            times.append(time.perf_counter() - t0)
+        t_b = statistics.median(times[1:])
+        out["batched"] = {"value": len(meshes) * nf / t_b, "seconds": t_b,
+                          "unconverged": sum(1 for per in st for s in per if not s["converged"]),
+                          "iters": sum(s["iters"] for per in st for s in per)}
+    finally:
+        c.close()
+    ctxs = []
+    try:
+        for m in meshes:
+            one = binding.Context(0)
+            ctxs.append(one)
+            one.set_material(**MAT)
+            one.set_window(eta, binding.WIN_HANNING)
+            one.mesh(m.xyz, m.tri, m.bc_type, opts)
+        times = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            iters = 0
+            for one, m in zip(ctxs, meshes):
+                st = one.solve_sweep(T, n_omega, load, m.pattern, opts, allow_unconverged=True)
+                iters += sum(s["iters"] for s in st)
+            times.append(time.perf_counter() - t0)
+        t_s = statistics.median(times[1:])
+        out["sequential"] = {"value": len(meshes) * nf / t_s, "seconds": t_s, "iters": iters}
+    finally:
+        for one in ctxs:
+            one.close()
+    out["value"] = out["batched"]["value"]
+    out["speedup_vs_sequential"] = out["batched"]["value"] / out["sequential"]["value"]
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,9 +470,13 @@ def main():
                     help="assemble every frequency with a fresh ACA (no reuse of the previous pivots)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one frequency (assembly + one solve) and exit; for profiler captures")
+    ap.add_argument("--batched", action="store_true",
+                    help="the 16-mesh batched sweep against the same meshes one after another (separate line)")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
-    if args.impl == "reference":
+    if args.batched:
+        run_batched(args)
+    elif args.impl == "reference":
         run_reference(args, cfg)
     else:
         run_ours(args, cfg)
