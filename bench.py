@@ -126,6 +126,26 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over the ranks of the default process group (x without one).
+
+    The replicas share no data: the timing maximum is the only collective."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, t_max_ms: float) -> float:
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / (t_max_ms / 1e3)
+
+
 def cpu_oracle_sample(cfg, rows_per_step=1024, lu_n=6144):
     """Times the CPU oracle on a bounded sample of one frequency of the workload.
 
@@ -289,13 +309,8 @@ def run_ours(args, cfg):
     prof = ctx.get_profile()
     ctx.set_profiling(False)
     clocks = clk.summary()
-    t_max = total_ms
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        dist.barrier()
-    value = nf * args.steps * ws / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, dev)
+    value = replica_throughput(nf * args.steps, ws, t_max)
 
     # end to end through the host-pointer API
     h2d = mesh.xyz.nbytes + mesh.tri.astype(np.int32).nbytes + mesh.bc_type.nbytes + load.nbytes + \
