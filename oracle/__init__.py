@@ -18,6 +18,8 @@ frequency-domain BEM for rapid transient elastodynamic analysis"):
                   A a = b (Sec. 2.1, Eqs. Tu_Ut, Aa_b)
 * ``transforms``  DFT-MFT / IDFT-MFT, windows, damping rule (Sec. 3)
 * ``solvers``     direct solve, block-Jacobi GMRES, solution extrapolation
+* ``aca``         adaptive cross approximation of one admissible block, with
+                  the per-component check rows the library uses
                   (Sec. 4.2, Eqs. a0, lsem, a0-solution)
 * ``sweep``       the whole sequence A_k a_k = b_k, k = 0..N/2 (Eq.
                   Aa_b-sequence) and the time response
