@@ -34,13 +34,56 @@ def _apply_block(Minv, v):
     return np.einsum("eij,ej->ei", Minv, v.reshape(-1, 3)).reshape(-1)
 
 
-def gmres(A, b, x0=None, tol=1e-10, restart=50, maxiter=5000, precondition=True):
-    """Right-preconditioned restarted GMRES; returns (x, iterations, rel_residual)."""
+def bisection_clusters(centroids, leaf: int):
+    """Element groups of at most ``leaf`` elements: recursive halving at the
+    median along the longest extent of the group's centroids."""
+    c = np.asarray(centroids, dtype=np.float64)
+    todo, out = [np.arange(c.shape[0])], []
+    while todo:
+        I = todo.pop()
+        if I.size <= leaf:
+            out.append(I)
+            continue
+        ax = int(np.argmax(c[I].max(axis=0) - c[I].min(axis=0)))
+        o = np.argsort(c[I, ax], kind="stable")
+        h = I.size // 2
+        todo += [I[o[:h]], I[o[h:]]]
+    return out
+
+
+def cluster_block_inverse(A, groups):
+    """Inverses of the diagonal blocks of A over element groups (3 rows and
+    columns per element): a block-Jacobi preconditioner with larger blocks."""
+    out = []
+    for I in groups:
+        d = (3 * np.asarray(I)[:, None] + np.arange(3)).ravel()
+        out.append((d, np.linalg.inv(A[np.ix_(d, d)])))
+    return out
+
+
+def _apply_groups(inv, v):
+    o = np.empty_like(v)
+    for d, Bi in inv:
+        o[d] = Bi @ v[d]
+    return o
+
+
+def gmres(A, b, x0=None, tol=1e-10, restart=50, maxiter=5000, precondition=True, groups=None):
+    """Right-preconditioned restarted GMRES; returns (x, iterations, rel_residual).
+
+    The preconditioner is the inverse of the 3x3 diagonal blocks, or of the
+    diagonal blocks over element ``groups`` when given."""
     A = np.asarray(A, dtype=np.complex128)
     b = np.asarray(b, dtype=np.complex128)
     N = b.size
-    Minv = block_jacobi_inverse(A) if precondition else None
-    M = (lambda v: _apply_block(Minv, v)) if precondition else (lambda v: v)
+    if precondition and groups is not None:
+        ginv = cluster_block_inverse(A, groups)
+        M = lambda v: _apply_groups(ginv, v)
+    elif precondition:
+        Minv = block_jacobi_inverse(A)
+        M = lambda v: _apply_block(Minv, v)
+    else:
+        M = lambda v: v
     x = np.zeros(N, dtype=np.complex128) if x0 is None else np.asarray(x0, dtype=np.complex128).copy()
     bnorm = np.linalg.norm(b)
     if bnorm == 0.0:
