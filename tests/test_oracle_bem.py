@@ -249,6 +249,53 @@ def test_rod_mixed_bc_converges_to_1d_solution():
         assert ef < 0.03
 
 
+def _manufactured_errors(xyz, tri, fixed, s):
+    """Point force e at x0 outside the solid: u = e U(x0, .), t = e T(x0, .; n)
+    solve the Navier equation inside, so prescribing them (u on the fixed
+    elements, t elsewhere, sampled at the centroids) must return the other
+    half as the mesh is refined."""
+    x0, e = np.array([2.2, 0.9, -0.6]), np.array([0.3, -0.5, 0.8])
+    g = bem.geometry(xyz, tri)
+    bc = fixed(g.c).astype(np.int8)
+    U, T = kernels.kernel_pair(x0, g.c, g.n, s, MAT)
+    u, t = np.einsum("i,eij->ej", e, U), np.einsum("i,eij->ej", e, T)
+    known = np.where(bc[:, None] == 1, u, t)
+    want = np.where(bc[:, None] == 1, t, u)
+    A, b = bem.system_rows(g, bc, known, s, MAT)
+    a = solvers.direct_solve(A, b).reshape(-1, 3)
+    free = bc == 0
+    return (np.linalg.norm((a - want)[free]) / np.linalg.norm(want[free]),
+            np.linalg.norm((a - want)[~free]) / np.linalg.norm(want[~free]))
+
+
+def test_traction_kernel_is_the_traction_of_the_displacement_kernel():
+    """e_i T_ij(x0, y; n) equals sigma(u) n for the field u_j = e_i U_ij(x0, y)
+    (Hooke's law on central differences of U), the convention the
+    manufactured solution below relies on."""
+    x0, e, s = np.array([1.3, 0.2, -0.1]), np.array([0.3, -0.5, 0.8]), 0.5 + 1.0j
+    y, n = np.array([0.5, -0.1, 0.2]), np.array([0.6, 0.0, 0.8])
+    f = lambda yy: e @ kernels.displacement_kernel(x0, yy, s, MAT)
+    h = 1e-5
+    G = np.stack([(f(y + h * d) - f(y - h * d)) / (2 * h) for d in np.eye(3)], axis=1)
+    eps = 0.5 * (G + G.T)
+    sig = MAT.lam * np.trace(eps) * np.eye(3) + 2 * MAT.mu * eps
+    assert np.allclose(e @ kernels.traction_kernel(x0, y, n, s, MAT), sig @ n, rtol=1e-6, atol=1e-9)
+
+
+def test_manufactured_point_force_converges():
+    """Mixed boundary conditions on a ball (lower cap fixed) and a box (bottom
+    face fixed): the errors against the exact field fall at least at first
+    order under refinement."""
+    s = 0.5 + 1.0j
+    eb = [_manufactured_errors(*inputs.geodesic_sphere(n), lambda c: c[:, 2] < -0.3, s) for n in (3, 5)]
+    ex = [_manufactured_errors(*inputs.box_mesh(1.0, 1.0, 1.0, h), lambda c: np.abs(c[:, 2] + 0.5) < 1e-9, s)
+          for h in (1 / 3, 1 / 5)]
+    for coarse, fine, ratio in ((eb[0], eb[1], 0.6), (ex[0], ex[1], 0.6)):
+        for ec, ef in zip(coarse, fine):
+            assert ef < (ratio + 0.1) * ec
+    assert eb[1][0] < 0.05 and eb[1][1] < 0.1
+
+
 def test_far_bands_against_brute_force():
     """Q2 and Q1 bands on a finer sphere (well-resolved frequency)."""
     mesh = inputs.cavity_problem(8)
