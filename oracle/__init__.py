@@ -15,7 +15,8 @@ frequency-domain BEM for rapid transient elastodynamic analysis"):
                   the rule is fixed here and implemented independently on the
                   GPU side)
 * ``bem``         dense collocation T u = U t and boundary conditions
-                  A a = b (Sec. 2.1, Eqs. Tu_Ut, Aa_b)
+                  A a = b (Sec. 2.1, Eqs. Tu_Ut, Aa_b); the interior field
+                  by the representation formula
 * ``transforms``  DFT-MFT / IDFT-MFT, windows, damping rule (Sec. 3)
 * ``solvers``     direct solve, block-Jacobi GMRES, solution extrapolation
 * ``aca``         adaptive cross approximation of one admissible block, with

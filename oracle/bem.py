@@ -210,3 +210,44 @@ def full_matrices(g: Geometry, s, mat):
     for e in range(g.ne):
         T[e, e] += 0.5 * np.eye(3)
     return _to_matrix(T), _to_matrix(U)
+
+
+def interior_field(g: Geometry, bc_type, known, a, points, s, mat):
+    """Displacement at points inside the solid from the boundary solution.
+
+    The representation formula (Somigliana's identity, the interior form of
+    Eq. bie with c = I): u_i(x) = sum_e [int_e U_ij(x, y) dy t_j(e)
+    - int_e T_ij(x, y) dy u_j(e)], with u, t constant per element: on
+    Gamma_sigma elements t is the prescribed ``known`` and u the solved ``a``,
+    on Gamma_u elements the reverse. Each (point, element) pair takes the rule
+    of its distance band (as the matrix entries); the NEAR band takes the
+    1024-point subdivided rule on the full kernel (the point is off the
+    boundary, so the integrand is only nearly singular). Points must not lie
+    on the boundary. Returns (P, 3) complex.
+    """
+    x = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    a = np.asarray(a, dtype=np.complex128).reshape(-1, 3)
+    known = np.asarray(known, dtype=np.complex128).reshape(-1, 3)
+    fixed = np.asarray(bc_type).astype(bool)
+    u = np.where(fixed[:, None], known, a)
+    t = np.where(fixed[:, None], a, known)
+    out = np.zeros((x.shape[0], 3), dtype=np.complex128)
+    ne = g.c.shape[0]
+    for p in range(x.shape[0]):
+        xp = np.broadcast_to(x[p], (ne, 3))
+        band = qd.classify(xp, g.c, g.h, np.zeros(ne, dtype=bool))
+        for b in (qd.BAND_NEAR, qd.BAND_Q4, qd.BAND_Q2, qd.BAND_Q1):
+            e = np.nonzero(band == b)[0]
+            if e.size == 0:
+                continue
+            if b == qd.BAND_NEAR:
+                pts, wts = qd.near_rule(g.p0[e], g.p1[e], g.p2[e])
+            elif b == qd.BAND_Q4:
+                pts, wts = qd.collapsed_rule(g.p0[e], g.p1[e], g.p2[e], 4)
+            elif b == qd.BAND_Q2:
+                pts, wts = qd.collapsed_rule(g.p0[e], g.p1[e], g.p2[e], 2)
+            else:
+                pts, wts = qd.centroid_rule(g.p0[e], g.p1[e], g.p2[e])
+            Ui, Ti = _integrate(xp[e], pts, wts, g.n[e], s, mat)
+            out[p] += np.einsum("eij,ej->i", Ui, t[e]) - np.einsum("eij,ej->i", Ti, u[e])
+    return out

@@ -296,6 +296,43 @@ def test_manufactured_point_force_converges():
     assert eb[1][0] < 0.05 and eb[1][1] < 0.1
 
 
+def test_interior_field_manufactured():
+    """Representation formula at interior points of a box with the exact
+    boundary data of a point force outside: the field converges to the point
+    force's field; with the boundary solution of the mixed problem the error
+    follows the boundary solution's."""
+    x0, e, s = np.array([2.2, 0.9, -0.6]), np.array([0.3, -0.5, 0.8]), 0.5 + 1.0j
+    P = np.array([[0.1, -0.2, 0.05], [0.3, 0.3, -0.3], [-0.35, 0.1, 0.4]])
+    exact = np.einsum("i,pij->pj", e, kernels.displacement_kernel(x0, P, s, MAT))
+    errs = []
+    for h in (1 / 3, 1 / 5):
+        xyz, tri = inputs.box_mesh(1.0, 1.0, 1.0, h)
+        g = bem.geometry(xyz, tri)
+        bc = (np.abs(g.c[:, 2] + 0.5) < 1e-9).astype(np.int8)
+        U, T = kernels.kernel_pair(x0, g.c, g.n, s, MAT)
+        u, t = np.einsum("i,eij->ej", e, U), np.einsum("i,eij->ej", e, T)
+        known = np.where(bc[:, None] == 1, u, t)
+        other = np.where(bc[:, None] == 1, t, u)
+        f = bem.interior_field(g, bc, known, other, P, s, MAT)
+        errs.append(np.linalg.norm(f - exact) / np.linalg.norm(exact))
+    assert errs[0] < 0.015 and errs[1] < 0.7 * errs[0]
+
+
+def test_interior_field_rod():
+    """Interior displacement of the rod against its exact 1-D field."""
+    mat = kernels.Material(1.0, 0.0, 1.0)
+    rod = inputs.rod_problem(h=1 / 3)
+    g = bem.geometry(rod.xyz, rod.tri)
+    s = 0.3 + 0.4j
+    A, b = bem.system_rows(g, rod.bc_type, rod.pattern.astype(complex), s, mat)
+    a = solvers.direct_solve(A, b)
+    xs = np.array([[0.5, 0.05, -0.1], [1.5, 0.0, 0.0], [2.5, -0.2, 0.1]])
+    f = bem.interior_field(g, rod.bc_type, rod.pattern.astype(complex), a, xs, s, mat)
+    ref = analytic.rod_field(xs[:, 0], s, 3.0, 1.0, 1.0)
+    assert np.linalg.norm(f[:, 0] - ref) <= 0.03 * np.linalg.norm(ref)
+    assert np.max(np.abs(f[:, 1:])) <= 0.01 * np.max(np.abs(ref))
+
+
 def test_far_bands_against_brute_force():
     """Q2 and Q1 bands on a finer sphere (well-resolved frequency)."""
     mesh = inputs.cavity_problem(8)
