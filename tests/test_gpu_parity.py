@@ -8,7 +8,7 @@ Tolerances (written from the arithmetic):
   |z| ~ 1e-3 (innermost polar nodes of the self element at low frequency) it
   keeps only ~8 digits; the GPU path sums the Taylor series there;
 * low-rank blocks add the ACA tolerance (rows compared at 30 x aca_tol);
-* solutions: the benchmark spec's target 1e-4 relative L2 in the frequency domain
+* solutions: the target 1e-4 relative L2 in the frequency domain
   and 1e-3 for time traces (mixed); plain form 1e-8 / 1e-7.
 """
 import math
