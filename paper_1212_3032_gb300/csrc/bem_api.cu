@@ -264,11 +264,11 @@ void prof_end(bem_ctx* ctx, cudaEvent_t a, int kind, double base = 0.0, double m
 // with other contexts' streams (the meshes of a batched sweep) go through one
 // stream common to those contexts, ordered against the context's own stream
 // by events: two such grids then never wait for residency at the same time.
-// A lone context launches on its own stream.
+// A lone context (and the parent of a batch) launches on its own stream.
 class CoopLane {
  public:
   CoopLane(bem_ctx* ctx, cudaStream_t st) : ctx_(ctx), st_(st) {
-    if (!ctx->coop_stream) return;
+    if (!ctx->coop_stream) return;  // set only together with coop_in, coop_out (bem_add_mesh)
     e_ = cudaEventRecord(ctx->coop_in, st);
     if (e_ == cudaSuccess) e_ = cudaStreamWaitEvent(ctx->coop_stream, ctx->coop_in, 0);
   }
@@ -453,9 +453,9 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
   }
   if (ctx->coop_in) cudaEventDestroy(ctx->coop_in);
   if (ctx->coop_out) cudaEventDestroy(ctx->coop_out);
-  if (ctx->coop_owner && ctx->coop_stream) {
-    cudaStreamSynchronize(ctx->coop_stream);
-    cudaStreamDestroy(ctx->coop_stream);
+  if (ctx->batch_coop) {
+    cudaStreamSynchronize(ctx->batch_coop);
+    cudaStreamDestroy(ctx->batch_coop);
   }
   mlp_free(ctx);
   delete ctx;
@@ -2127,10 +2127,7 @@ extern "C" int bem_add_mesh(bem_ctx* ctx, const double* xyz, int64_t nv, const i
   if (!ctx || !mesh_id) return BEM_ERR_INVALID_ARG;
   *mesh_id = -1;
   TRY(set_device(ctx));
-  if (!ctx->coop_stream) {
-    BEM_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->coop_stream, cudaStreamNonBlocking));
-    ctx->coop_owner = true;
-  }
+  if (!ctx->batch_coop) BEM_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->batch_coop, cudaStreamNonBlocking));
   cudaStream_t s = nullptr;
   BEM_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   bem_ctx* child = nullptr;
@@ -2139,11 +2136,11 @@ extern "C" int bem_add_mesh(bem_ctx* ctx, const double* xyz, int64_t nv, const i
     cudaStreamDestroy(s);
     return fail(ctx, rc, "could not create the mesh's context");
   }
-  child->coop_stream = ctx->coop_stream;
   rc = cudaEventCreateWithFlags(&child->coop_in, cudaEventDisableTiming) == cudaSuccess &&
                cudaEventCreateWithFlags(&child->coop_out, cudaEventDisableTiming) == cudaSuccess
            ? BEM_OK
            : BEM_ERR_CUDA;
+  if (rc == BEM_OK) child->coop_stream = ctx->batch_coop;
   if (rc == BEM_OK && ctx->have_mat) rc = bem_set_material(child, ctx->E, ctx->nu, ctx->rho);
   if (rc == BEM_OK) rc = bem_set_far_storage(child, ctx->far_mode_req, ctx->far_ws_req);
   if (rc == BEM_OK) rc = bem_set_aca_reuse(child, ctx->aca_reuse ? 1 : 0);

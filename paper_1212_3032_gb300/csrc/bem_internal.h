@@ -314,8 +314,8 @@ struct bem_ctx {
   // with its own non-blocking stream; the children's cooperative launches
   // share one stream (CoopLane)
   std::vector<bem_ctx*> batch;
-  cudaStream_t coop_stream = nullptr;  // set in children (and their parent) only
-  bool coop_owner = false;
+  cudaStream_t batch_coop = nullptr;   // the children's shared stream (owned by the parent)
+  cudaStream_t coop_stream = nullptr;  // in a child: the parent's batch_coop (borrowed)
   cudaEvent_t coop_in = nullptr, coop_out = nullptr;
 
   // sweep results
