@@ -280,8 +280,8 @@ int bem_get_far_storage(bem_ctx* ctx, bem_far_storage* out);
 /* ---- several meshes in one context ------------------------------------------
  * Independent problems (the batched sweep of meshes of uneven size) share one
  * GPU: each added mesh gets its own context state and non-blocking stream,
- * and bem_solve_sweep_batched drives every mesh's sweep from its own host
- * thread, so small meshes fill the GPU around large ones. The material and
+ * and bem_solve_sweep_batched runs the meshes' sweeps on a pool of up to 16
+ * host threads, so the kernels of several meshes share the GPU. The material and
  * window of the context apply to every mesh (set them before the sweep); far
  * storage and pivot reuse settings are taken when the mesh is added. The
  * single-mesh calls (bem_mesh, bem_solve_sweep, ...) keep their own mesh. */

@@ -9,6 +9,7 @@
 //        residual accumulated in FP64 (iterative refinement of the c64 solve)
 //   3. bem_time_response: Eq. IDFT-MFT with the window of Sec. 3.2.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -2180,16 +2181,19 @@ extern "C" int bem_solve_sweep_batched(bem_ctx* ctx, double T, int32_t n_omega, 
   }
   const int nf = n_omega / 2 + 1;
   std::vector<int> rc(nm, BEM_OK);
+  // a bounded pool of host threads takes the meshes in turn
+  const int hw = (int)std::thread::hardware_concurrency();
+  const int nw = std::min(nm, std::max(1, std::min(16, hw > 0 ? hw : 16)));
+  std::atomic<int> next{0};
   std::vector<std::thread> th;
-  th.reserve(nm);
-  for (int i = 0; i < nm; ++i)
-    th.emplace_back([&, i]() {
-      if (cudaSetDevice(ctx->device) != cudaSuccess) {
-        rc[i] = BEM_ERR_CUDA;
-        return;
-      }
-      rc[i] = bem_solve_sweep(ctx->batch[i], T, n_omega, load_hist, bc_patterns[i], opts,
-                              stats ? stats + (long long)i * nf : nullptr);
+  th.reserve(nw);
+  for (int w = 0; w < nw; ++w)
+    th.emplace_back([&]() {
+      const bool dev_ok = cudaSetDevice(ctx->device) == cudaSuccess;
+      for (int i = next.fetch_add(1); i < nm; i = next.fetch_add(1))
+        rc[i] = dev_ok ? bem_solve_sweep(ctx->batch[i], T, n_omega, load_hist, bc_patterns[i], opts,
+                                         stats ? stats + (long long)i * nf : nullptr)
+                       : BEM_ERR_CUDA;
     });
   for (auto& t : th) t.join();
   int worst = BEM_OK;
