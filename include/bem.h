@@ -266,6 +266,22 @@ int bem_far_block_info(bem_ctx* ctx, int64_t nmax, int32_t* info, int64_t* count
  * Errors: INVALID_ARG. */
 int bem_set_far_storage(bem_ctx* ctx, int32_t mode, int64_t workspace_bytes);
 
+/* The block partition bem_mesh builds, on the host alone (no device, no
+ * context): centroid (ne x 3) and element size h (ne, the longest edge) in
+ * caller order; leaf_size, eta_adm and dense as in bem_opts. The cluster tree
+ * halves each cluster at the median along the longest extent of its
+ * centroids until at most leaf_size remain; a cluster pair is admissible
+ * (far, low rank) when min(diam) <= eta_adm dist (bounding boxes of the
+ * centroids) and dist^2 > 2.2 h_max^2 (no element pair of it in the
+ * near-singular band); the other leaf pairs are near. perm (may be NULL):
+ * ne values, tree position -> caller element. near_blocks / far_blocks: the
+ * first nmax blocks as (row begin, rows, column begin, columns) in tree
+ * positions, 4 int32 each; *n_near, *n_far the counts (nmax = 0 queries
+ * them). Errors: INVALID_ARG. */
+int bem_block_tree(const double* centroid, const double* h, int64_t ne, int32_t leaf_size, double eta_adm,
+                   int32_t dense, int32_t* perm, int64_t nmax, int32_t* near_blocks, int32_t* far_blocks,
+                   int64_t* n_near, int64_t* n_far);
+
 typedef struct bem_far_storage {
   int32_t compact;          /* storage of the current mesh: 1 compact, 0 full */
   int32_t batches;          /* ACA batches per assembly */

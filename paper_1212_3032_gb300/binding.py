@@ -34,7 +34,7 @@ EXPORTED = [
     "bem_mlp_forward", "bem_mlp_gradient", "bem_mlp_train_step", "bem_set_aca_reuse",
     "bem_far_block_info", "bem_set_far_storage", "bem_get_far_storage",
     "bem_add_mesh", "bem_mesh_count", "bem_solve_sweep_batched", "bem_mesh_frequency_solution",
-    "bem_mesh_time_response",
+    "bem_mesh_time_response", "bem_block_tree",
 ]
 
 
@@ -85,6 +85,33 @@ class FarStorage(ctypes.Structure):
 _lib = None
 
 
+def block_tree(centroid, h, leaf_size=64, eta_adm=1.0, dense=False):
+    """The block partition of the operator (host only): (perm, near (n, 4), far (m, 4)) int32 arrays,
+    blocks as (row begin, rows, column begin, columns) in tree positions."""
+    lib = load_library()
+    c = np.ascontiguousarray(centroid, dtype=np.float64).reshape(-1, 3)
+    hh = np.ascontiguousarray(h, dtype=np.float64).ravel()
+    ne = c.shape[0]
+    nn, nf = ctypes.c_int64(), ctypes.c_int64()
+    perm = np.zeros(ne, dtype=np.int32)
+    rc = lib.bem_block_tree(_ptr(c), _ptr(hh), ne, int(leaf_size), float(eta_adm), 1 if dense else 0, _ptr(perm), 0,
+                            None, None, ctypes.byref(nn), ctypes.byref(nf))
+    if rc != 0:
+        raise BemError(rc, "bem_block_tree")
+    near = np.zeros((nn.value, 4), dtype=np.int32)
+    far = np.zeros((nf.value, 4), dtype=np.int32)
+    n = max(nn.value, nf.value)
+    nb = np.zeros((n, 4), dtype=np.int32)
+    fb = np.zeros((n, 4), dtype=np.int32)
+    rc = lib.bem_block_tree(_ptr(c), _ptr(hh), ne, int(leaf_size), float(eta_adm), 1 if dense else 0, _ptr(perm), n,
+                            _ptr(nb), _ptr(fb), ctypes.byref(nn), ctypes.byref(nf))
+    if rc != 0:
+        raise BemError(rc, "bem_block_tree")
+    near[:] = nb[:nn.value]
+    far[:] = fb[:nf.value]
+    return perm, near, far
+
+
 def load_library(path: str = LIB_PATH):
     """Loads libbem.so (raises if it has not been built)."""
     global _lib
@@ -122,6 +149,8 @@ def load_library(path: str = LIB_PATH):
         "bem_set_aca_reuse": (ctypes.c_int, [P, ctypes.c_int]),
         "bem_far_block_info": (ctypes.c_int, [P, I64, P, P]),
         "bem_set_far_storage": (ctypes.c_int, [P, ctypes.c_int32, I64]),
+        "bem_block_tree": (ctypes.c_int, [P, P, I64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, P, I64, P, P,
+                                          P, P]),
         "bem_add_mesh": (ctypes.c_int, [P, P, I64, P, I64, P, P, P]),
         "bem_mesh_count": (ctypes.c_int, [P]),
         "bem_solve_sweep_batched": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int32, P, P, P, P]),

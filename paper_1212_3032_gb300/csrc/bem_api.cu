@@ -2066,6 +2066,35 @@ extern "C" int bem_set_aca_reuse(bem_ctx* ctx, int on) {
   return BEM_OK;
 }
 
+extern "C" int bem_block_tree(const double* centroid, const double* h, int64_t ne, int32_t leaf_size,
+                              double eta_adm, int32_t dense, int32_t* perm, int64_t nmax, int32_t* near_blocks,
+                              int32_t* far_blocks, int64_t* n_near, int64_t* n_far) {
+  if (!centroid || !h || ne <= 0 || ne > 0x7fffffff || leaf_size < 1 || !(eta_adm > 0) || !n_near || !n_far ||
+      nmax < 0 || (nmax > 0 && (!near_blocks || !far_blocks)))
+    return BEM_ERR_INVALID_ARG;
+  ClusterTree tr;
+  build_cluster_tree(centroid, h, (int)ne, leaf_size, eta_adm, RHO2_NEAR, dense != 0, tr);
+  *n_near = (int64_t)tr.near.size();
+  *n_far = (int64_t)tr.far.size();
+  if (perm)
+    for (int64_t k = 0; k < ne; ++k) perm[k] = tr.perm[k];
+  auto put = [&](const std::vector<BlockPair>& v, int32_t* out) {
+    for (int64_t b = 0; b < std::min<int64_t>(nmax, (int64_t)v.size()); ++b) {
+      const Cluster& t = tr.nodes[v[b].tau];
+      const Cluster& s2 = tr.nodes[v[b].sigma];
+      out[4 * b] = t.begin;
+      out[4 * b + 1] = t.size();
+      out[4 * b + 2] = s2.begin;
+      out[4 * b + 3] = s2.size();
+    }
+  };
+  if (nmax > 0) {
+    put(tr.near, near_blocks);
+    put(tr.far, far_blocks);
+  }
+  return BEM_OK;
+}
+
 extern "C" int bem_set_far_storage(bem_ctx* ctx, int32_t mode, int64_t workspace_bytes) {
   if (!ctx) return BEM_ERR_INVALID_ARG;
   if (mode < BEM_FAR_AUTO || mode > BEM_FAR_COMPACT) return fail(ctx, BEM_ERR_INVALID_ARG, "unknown storage mode");
