@@ -82,3 +82,17 @@ def test_ball_with_void():
     vol = np.sum(np.einsum("ij,ij->i", p[:, 0], np.cross(p[:, 1], p[:, 2]))) / 6
     assert abs(vol - 4 / 3 * np.pi * (1 - 0.3 ** 3)) < 0.1
     assert inputs.ball_with_void().ne == 20180
+
+
+def test_rod_problem():
+    m = inputs.rod_problem(h=0.25)
+    assert m.ne == 2 * 32 + 4 * 96
+    assert _edges_closed(m.tri)
+    c = m.xyz[m.tri].mean(axis=1)
+    fixed = np.abs(c[:, 0]) < 1e-9
+    loaded = np.abs(c[:, 0] - 3.0) < 1e-9
+    assert fixed.sum() == 32 and loaded.sum() == 32
+    assert np.all(m.bc_type[fixed] == inputs.BC_DISPLACEMENT) and np.all(m.bc_type[~fixed] == inputs.BC_TRACTION)
+    assert np.allclose(m.pattern[loaded], [-1.0, 0.0, 0.0])  # compressive traction on the end x = 3
+    assert np.all(m.pattern[~loaded] == 0)
+    assert inputs.rod_problem().ne == 12348
