@@ -101,3 +101,39 @@ def test_cluster_preconditioner_on_the_rod():
     for x in (x3, xg):
         assert np.linalg.norm(x - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
     assert itg < 0.7 * it3
+
+
+def test_paper_iteration_trends_on_the_rod():
+    """The paper's qualitative trends (Sec. 5.1, Table 1) on the oracle: on the
+    rod (252 triangles, T = 26.8 L/c, the first 9 of 16 samples), a larger
+    damping (kappa 4 against 2) does not need more GMRES steps, and the
+    solution extrapolation (K = 4) cuts them by over a quarter."""
+    import math
+    from oracle import transforms as tr
+    mat = kernels.Material(1.0, 0.0, 1.0)
+    rod = inputs.rod_problem(h=1 / 3)
+    g = bem.geometry(rod.xyz, rod.tri)
+    T, N = 26.8 * 3.0, 16
+    hist = inputs.heaviside_history(N)
+    its = {}
+    for kappa in (2, 4):
+        eta = tr.eta_from_kappa(kappa, T)
+        Pk = tr.dft_mft(hist, T, eta)
+        zero = sem = 0
+        prev = []
+        for k in range(N // 2 + 1):
+            s = eta + 1j * k * 2 * math.pi / T
+            A, b = bem.system_rows(g, rod.bc_type, rod.pattern * Pk[k], s, mat)
+            x, it, rel = solvers.gmres(A, b, tol=1e-5)
+            assert rel <= 1e-5
+            zero += it
+            if kappa == 4:
+                K = min(k, 4)
+                X = np.stack(prev[-K:][::-1], axis=1) if K else np.zeros((b.size, 0))
+                a0, _ = solvers.sem_guess(A, b, X)
+                _, it2, _ = solvers.gmres(A, b, x0=a0, tol=1e-5)
+                sem += it2
+            prev.append(x)
+        its[kappa] = (zero, sem)
+    assert its[4][0] <= its[2][0]
+    assert its[4][1] <= 0.75 * its[4][0]
