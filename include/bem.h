@@ -45,7 +45,7 @@ extern "C" {
 #define BEM_ERR_OOM (-3)
 #define BEM_ERR_CUDA (-4)
 #define BEM_ERR_NOT_CONVERGED (-5)
-#define BEM_ERR_TIMEOUT (-6)
+#define BEM_ERR_TIMEOUT (-6) /* reserved: no entry point returns it (no call waits on the device) */
 #define BEM_ERR_STATE (-7)
 
 /* element boundary-condition kind (Sec. 2.1: Gamma_sigma / Gamma_u) */

@@ -412,8 +412,13 @@ extern "C" int bem_create(bem_ctx** out, int device, void* stream) {
     delete ctx;
     return BEM_ERR_OOM;
   }
-  if (cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->asm_stream, cudaStreamNonBlocking) != cudaSuccess ||
+  int prio_least = 0, prio_greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) prio_least = prio_greatest = 0;
+  if (cudaStreamCreateWithPriority(&ctx->aux_stream, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&ctx->asm_stream, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&ctx->solve_stream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_solve_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_solve_out, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_asm_done, cudaEventDisableTiming) != cudaSuccess) {
@@ -439,6 +444,12 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
     cudaStreamSynchronize(ctx->asm_stream);
     cudaStreamDestroy(ctx->asm_stream);
   }
+  if (ctx->solve_stream) {
+    cudaStreamSynchronize(ctx->solve_stream);
+    cudaStreamDestroy(ctx->solve_stream);
+  }
+  if (ctx->ev_solve_in) cudaEventDestroy(ctx->ev_solve_in);
+  if (ctx->ev_solve_out) cudaEventDestroy(ctx->ev_solve_out);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_asm_done) cudaEventDestroy(ctx->ev_asm_done);
@@ -1344,16 +1355,24 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
     BEM_CUDA_TRY(cudaEventRecord(ctx->col_events[j], st));
     return BEM_OK;
   };
+  // the restart residuals use FP32 products (FP64 sums across tasks) when the
+  // tolerance allows; a solve is accepted only on the residual with FP64
+  // products and sums, after which every restart uses those
+  bool exact = !(mixed && o.tol >= 1e-6);
   while (true) {
-    // true residual, FP64 sums (FP32 products when the tolerance allows)
-    if (mixed && o.tol >= 1e-6) TRY(apply_fast(ctx, x, ctx->y64.p, 1));
-    else TRY(apply64(ctx, x, ctx->y64.p, 1));
-    launch_residual(b, ctx->y64.p, ctx->r64.p, N, st);
-    CK("residual");
-    std::complex<double> rr;
-    TRY(dot_host(ctx, ctx->r64.p, ctx->r64.p, N, rr));
-    double rnorm = std::sqrt(std::max(0.0, rr.real()));
-    rel = bnorm > 0 ? rnorm / bnorm : 0.0;
+    double rnorm = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (exact) TRY(apply64(ctx, x, ctx->y64.p, 1));
+      else TRY(apply_fast(ctx, x, ctx->y64.p, 1));
+      launch_residual(b, ctx->y64.p, ctx->r64.p, N, st);
+      CK("residual");
+      std::complex<double> rr;
+      TRY(dot_host(ctx, ctx->r64.p, ctx->r64.p, N, rr));
+      rnorm = std::sqrt(std::max(0.0, rr.real()));
+      rel = bnorm > 0 ? rnorm / bnorm : 0.0;
+      if (exact || !(rel <= o.tol || rnorm == 0.0)) break;
+      exact = true;  // below the tolerance with FP32 products: confirm in FP64
+    }
     if (cycles == 0 && stats) stats->guess_residual = rel;
     if (rel <= o.tol || rnorm == 0.0) {
       converged = true;
@@ -1778,7 +1797,7 @@ extern "C" int bem_idft(bem_ctx* ctx, double T, int32_t n_omega, double eta, int
 // ---------------------------------------------------------------------------
 // the sweep
 // ---------------------------------------------------------------------------
-static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_dev, const bem_opts& o,
+static int sweep_body(bem_ctx* ctx, double T, int n_omega, const double* load_dev, const bem_opts& o,
                       bem_freq_stats* stats) {
   cudaStream_t st = ctx->stream;
   const long long N = ctx->N;
@@ -1886,6 +1905,25 @@ static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_de
   }
   if (worst != BEM_OK) fail(ctx, worst, "at least one frequency did not reach the tolerance");
   return worst;
+}
+
+// The sweep runs on the context's greatest-priority stream, forked from and
+// joined back to the caller's stream: the block scheduler then dispatches the
+// guess and GMRES work of frequency k ahead of pending blocks of the
+// least-priority assembly of k + 1, which otherwise occupies the SMs the
+// short solver kernels wait for.
+static int sweep_impl(bem_ctx* ctx, double T, int n_omega, const double* load_dev, const bem_opts& o,
+                      bem_freq_stats* stats) {
+  cudaStream_t caller = ctx->stream;
+  BEM_CUDA_TRY(cudaEventRecord(ctx->ev_solve_in, caller));
+  BEM_CUDA_TRY(cudaStreamWaitEvent(ctx->solve_stream, ctx->ev_solve_in, 0));
+  ctx->stream = ctx->solve_stream;
+  int rc = sweep_body(ctx, T, n_omega, load_dev, o, stats);
+  ctx->stream = caller;
+  cudaError_t e = cudaEventRecord(ctx->ev_solve_out, ctx->solve_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, ctx->ev_solve_out, 0);
+  if (e != cudaSuccess && rc == BEM_OK) return fail_cuda(ctx, e, "join the solve stream", __FILE__, __LINE__);
+  return rc;
 }
 
 static int sweep_checks(bem_ctx* ctx, double T, int32_t n_omega, const bem_opts& o) {

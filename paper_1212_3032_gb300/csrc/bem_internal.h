@@ -214,6 +214,11 @@ struct bem_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t asm_stream = nullptr;  // a sweep assembles frequency k + 1 here while GMRES(k) runs
   cudaEvent_t ev_asm_done = nullptr;
+  // a sweep runs the caller's part of its work (guess, GMRES, IDFT) on this
+  // stream of the device's greatest priority, so that blocks of the
+  // overlapped assembly (least priority) do not delay it; joined to `stream`
+  cudaStream_t solve_stream = nullptr;
+  cudaEvent_t ev_solve_in = nullptr, ev_solve_out = nullptr;
   bem::OpSet back;                    // the operator set not in use (see swap_ops)
   bem::DevBuf<int> leaf_cnt;          // per leaf: tasks completed in the current product (reset to 0 after it)
   bem::DevBuf<int> task_ptr;          // CSR of tasks over leaves
