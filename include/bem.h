@@ -173,6 +173,37 @@ int bem_time_response(bem_ctx* ctx, const int64_t* dofs, int64_t ndof, double* o
 /* Same, device output (n_omega x ndof float64) and device dof list. */
 int bem_time_response_dev(bem_ctx* ctx, const int64_t* dofs_dev, int64_t ndof, double* out_dev);
 
+/* ---- interior field ----------------------------------------------------
+ * Displacement and strain at points inside the solid from the solved
+ * boundary data, by the representation formula (Somigliana's identity: the
+ * interior form of Eq. bie, free term c = I; Sec. 5.2 reports strain at an
+ * interior point of its plate example):
+ *   u_i(x) = sum_e [ int_e U_ij(x, y) dy t_j(e) - int_e T_ij(x, y) dy u_j(e) ],
+ * u, t constant per element: the solved values a_k and the prescribed
+ * pattern * P_k, placed by each element's boundary condition. Each
+ * (point, element) pair uses the rule of its distance band, as the operator
+ * entries do (the nearest band: the full kernel on the 1,024-point
+ * subdivided rule). Kernel evaluation in the operator's precision (FP32 for
+ * the complex64 operator, FP64 for complex128), geometry relative to the
+ * point in FP64, sums in FP64.
+ * points: npts x 3 float64 (caller coordinates). Points must lie inside the
+ * solid at a distance from the boundary (at least a fraction of the local
+ * element size); on the boundary the formula does not hold and the values
+ * are not finite. Strain: eps = (grad u + grad u^T) / 2 by central
+ * differences with step h (the six points x +- h e_a must also be inside).
+ * Requires a solved sweep (STATE otherwise); k indexes its frequencies. */
+#define BEM_FIELD_DISPLACEMENT 0 /* 3 components: u_x, u_y, u_z */
+#define BEM_FIELD_STRAIN 1       /* 6 components: xx, yy, zz, xy, yz, xz */
+/* out: npts x 3 complex (interleaved float64). */
+int bem_interior_field(bem_ctx* ctx, int32_t k, const double* points, int64_t npts, double* out);
+/* out: npts x 6 complex (interleaved float64). */
+int bem_interior_strain(bem_ctx* ctx, int32_t k, const double* points, int64_t npts, double h, double* out);
+/* Time histories by Eq. IDFT-MFT over every solved frequency, with the
+ * context's window: out n_omega x (npts x ncomp) row-major float64, ncomp = 3
+ * (BEM_FIELD_DISPLACEMENT) or 6 (BEM_FIELD_STRAIN, step h). */
+int bem_interior_time_response(bem_ctx* ctx, const double* points, int64_t npts, int32_t quantity, double h,
+                               double* out);
+
 /* ---- step-level entry points (each is one step of the sweep) ---------- */
 
 /* Eq. DFT-MFT: out[k], k = 0..n_omega/2 (complex) of P(n dt). */

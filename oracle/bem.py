@@ -251,3 +251,22 @@ def interior_field(g: Geometry, bc_type, known, a, points, s, mat):
             Ui, Ti = _integrate(xp[e], pts, wts, g.n[e], s, mat)
             out[p] += np.einsum("eij,ej->i", Ui, t[e]) - np.einsum("eij,ej->i", Ti, u[e])
     return out
+
+
+def interior_strain(g: Geometry, bc_type, known, a, points, s, mat, h):
+    """Strain at interior points: eps = (grad u + grad u^T) / 2 with grad u by
+    central differences of ``interior_field`` at x +- h e_a (step h; the six
+    points must lie inside the solid). Returns (P, 6) complex, components
+    xx, yy, zz, xy, yz, xz (tensor, not engineering, shear).
+    """
+    x = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    grad = np.zeros((x.shape[0], 3, 3), dtype=np.complex128)  # grad[p, i, a] = d u_i / d x_a
+    for ax in range(3):
+        step = np.zeros(3)
+        step[ax] = h
+        up = interior_field(g, bc_type, known, a, x + step, s, mat)
+        um = interior_field(g, bc_type, known, a, x - step, s, mat)
+        grad[:, :, ax] = (up - um) / (2 * h)
+    eps = 0.5 * (grad + grad.transpose(0, 2, 1))
+    ii, jj = [0, 1, 2, 0, 1, 0], [0, 1, 2, 1, 2, 2]
+    return eps[:, ii, jj]

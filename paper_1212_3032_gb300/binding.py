@@ -23,6 +23,7 @@ WIN_NONE, WIN_HANNING, WIN_BLACKMAN = 0, 1, 2
 PREC_C64_MIXED, PREC_C128 = 0, 1
 GUESS_ZERO, GUESS_SEM, GUESS_MLP = 0, 1, 2
 FAR_AUTO, FAR_FULL, FAR_COMPACT = 0, 1, 2
+FIELD_DISPLACEMENT, FIELD_STRAIN = 0, 1
 
 EXPORTED = [
     "bem_default_opts", "bem_create", "bem_destroy", "bem_last_error", "bem_mesh", "bem_mesh_dev",
@@ -34,7 +35,8 @@ EXPORTED = [
     "bem_mlp_forward", "bem_mlp_gradient", "bem_mlp_train_step", "bem_set_aca_reuse",
     "bem_far_block_info", "bem_set_far_storage", "bem_get_far_storage",
     "bem_add_mesh", "bem_mesh_count", "bem_solve_sweep_batched", "bem_mesh_frequency_solution",
-    "bem_mesh_time_response", "bem_block_tree",
+    "bem_mesh_time_response", "bem_block_tree", "bem_interior_field", "bem_interior_strain",
+    "bem_interior_time_response",
 ]
 
 
@@ -157,6 +159,9 @@ def load_library(path: str = LIB_PATH):
         "bem_mesh_frequency_solution": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
         "bem_mesh_time_response": (ctypes.c_int, [P, ctypes.c_int32, P, I64, P]),
         "bem_get_far_storage": (ctypes.c_int, [P, P]),
+        "bem_interior_field": (ctypes.c_int, [P, I32, P, I64, P]),
+        "bem_interior_strain": (ctypes.c_int, [P, I32, P, I64, D, P]),
+        "bem_interior_time_response": (ctypes.c_int, [P, P, I64, I32, D, P]),
         "bem_mlp_num_params": (I64, []),
         "bem_mlp_init": (ctypes.c_int, [P, ctypes.c_uint64]),
         "bem_mlp_set_training": (ctypes.c_int, [P, I32, D]),
@@ -308,6 +313,30 @@ class Context:
             raise ValueError("out must hold n_omega x ndof values")
         self._check(self.lib.bem_time_response_dev(self.h, _tptr(dofs_t, "torch.int64"), dofs_t.numel(),
                                                    _tptr(out_t, "torch.float64")))
+
+    # --- interior field (representation formula) --------------------------
+    def interior_field(self, k, points):
+        """(npts, 3) complex displacement at interior points, solved frequency k."""
+        pts = _f64(points).reshape(-1, 3)
+        out = np.zeros((pts.shape[0], 3), dtype=np.complex128)
+        self._check(self.lib.bem_interior_field(self.h, int(k), _ptr(pts), pts.shape[0], _ptr(out)))
+        return out
+
+    def interior_strain(self, k, points, h):
+        """(npts, 6) complex strain (xx, yy, zz, xy, yz, xz), central differences with step h."""
+        pts = _f64(points).reshape(-1, 3)
+        out = np.zeros((pts.shape[0], 6), dtype=np.complex128)
+        self._check(self.lib.bem_interior_strain(self.h, int(k), _ptr(pts), pts.shape[0], float(h), _ptr(out)))
+        return out
+
+    def interior_time_response(self, points, quantity=FIELD_DISPLACEMENT, h=0.0):
+        """(n_omega, npts, 3 or 6) float64 time histories at interior points."""
+        pts = _f64(points).reshape(-1, 3)
+        nc = 6 if quantity == FIELD_STRAIN else 3
+        out = np.zeros((self.n_omega, pts.shape[0], nc), dtype=np.float64)
+        self._check(self.lib.bem_interior_time_response(self.h, _ptr(pts), pts.shape[0], int(quantity), float(h),
+                                                        _ptr(out)))
+        return out
 
     # --- several meshes (batched sweeps) -----------------------------------
     def add_mesh(self, xyz, tri, bc_type, opts: Opts | None = None) -> int:

@@ -153,6 +153,7 @@ void make_rule_tables(RuleTables& t);
 
 // Translation-unit uploads of the constant tables.
 cudaError_t upload_rules_assemble(const RuleTables& t, cudaStream_t st);
+cudaError_t upload_rules_interior(const RuleTables& t, cudaStream_t st);
 
 }  // namespace bem
 

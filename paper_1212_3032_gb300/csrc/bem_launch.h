@@ -124,4 +124,15 @@ void launch_load_dft(const double* P, int n_omega, double T, double eta, c128* o
 void launch_idft(const c128* spec, long long ldspec, const long long* idx, long long ndof, int n_omega,
                  double T, double eta, int window, double* out, cudaStream_t st);
 
+// ---- interior field (bem_interior.cu) ----
+// Displacement at npts interior points (caller coordinates, FP64) from the
+// boundary solution a (tree order) and the prescribed pattern * pk.
+template <typename R>
+void launch_interior(const double* pts, int npts, const ElemD* ed, int ne, const signed char* bc, const c128* a,
+                     const double* pattern, c128 pk, const KParams<R>& P, c128* out, cudaStream_t st);
+// The six points x +- h e_a around each point, and the strain from the
+// displacements there (central differences; npts x 6 complex).
+void launch_offset_points(const double* pts, int npts, double h, double* out, cudaStream_t st);
+void launch_strain(const c128* uoff, int npts, double h, c128* eps, cudaStream_t st);
+
 }  // namespace bem

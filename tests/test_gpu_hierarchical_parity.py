@@ -6,10 +6,10 @@ with FP64 refinement, the windowed inverse DFT -- is compared with the FP64
 oracle's direct solves (dense collocation, LU), element by element:
 
 * operator products ``y = A x`` against the oracle's full matrix;
-* whole sweeps on a 2,000-element cavity and a 2,368-element cube with two
-  cavities and a fixed bottom (mixed boundary conditions). Both meshes have
-  admissible blocks above 256 elements (one CTA each in ACA) and leaves with
-  several product tasks;
+* whole sweeps on a 2,000-element cavity (17 frequencies) and a
+  4,528-element cube with two cavities and a fixed bottom (mixed boundary
+  conditions; 5 frequencies), whose admissible blocks include 228 above 256
+  elements (one CTA each in ACA);
 * the benchmark mesh itself (5,120 elements, 15,360 unknowns, T = 64,
   256 samples) at frequencies k = 1 and k = 96 against an LU of the full
   oracle system.
@@ -80,18 +80,20 @@ def test_hmatrix_product_matches_oracle_matrix(ctx, B, prec, aca_tol, bound):
 
 
 def _cavity2000():
-    return inputs.cavity_problem(10), 12.0           # h ~ 0.12: ~4 elements per S wavelength at k = 16
+    # h ~ 0.12: about 4 elements per S wavelength at k = 16; 17 frequencies
+    return inputs.cavity_problem(10), 12.0, 32
 
 
 def _cube_mixed():
-    # unit cube, 12 x 12 cells per face (1,728) + two cavities (2 x 320); bottom fixed
-    return inputs.cube_with_cavities(n_face=12, n_cav=2, cav_radius=0.12, cav_n=4, seed=5), 8.0
+    # unit cube, 18 x 18 cells per face (3,888) + two cavities (2 x 320) = 4,528
+    # elements, bottom fixed; 228 admissible blocks above 256 elements (one CTA
+    # each in ACA); 5 frequencies up to omega = 2 pi
+    return inputs.cube_with_cavities(n_face=18, n_cav=2, cav_radius=0.12, cav_n=4, seed=5), 4.0, 8
 
 
 @pytest.fixture(scope="module", params=["cavity2000", "cube_mixed"])
 def sweep_case(request):
-    mesh, T = {"cavity2000": _cavity2000, "cube_mixed": _cube_mixed}[request.param]()
-    N = 32
+    mesh, T, N = {"cavity2000": _cavity2000, "cube_mixed": _cube_mixed}[request.param]()
     eta = 5.0 / T
     load = inputs.heaviside_history(N)
     with pool.RowPool(mesh, MAT) as P:
@@ -110,8 +112,9 @@ def test_hierarchical_sweep_matches_oracle(ctx, B, sweep_case):
     prof = ctx.get_profile()
     ctx.set_profiling(False)
     info = ctx.far_block_info()
-    # the one-CTA-per-block ACA path and pivot reuse are exercised
-    assert int((info[:, 0] + info[:, 1]).max()) > 256, name
+    # pivot reuse is exercised, and on the cube the one-CTA-per-block ACA path
+    if name == "cube_mixed":
+        assert int((info[:, 0] + info[:, 1] > 256).sum()) > 100, name
     assert prof["aca_stepped"] < prof["aca_blocks"]
     assert all(s["converged"] == 1 for s in stats), name
     errs = []
@@ -150,5 +153,6 @@ def test_benchmark_mesh_solution_matches_oracle_lu(ctx, B, bench_mesh_pool, k):
     assert _rel(b, b_ref) <= 2e-5
     x_ref = np.linalg.solve(A_ref, b_ref)
     assert _rel(x, x_ref) <= FTOL, k
-    # the accepted solution's residual against the oracle's own operator
+    # the accepted solution's residual against the oracle's own operator: the
+    # tolerance plus the operator's error (ACA 1e-5, FP32 entries)
     assert _rel(A_ref @ x, b_ref) <= 1e-4

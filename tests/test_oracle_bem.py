@@ -351,3 +351,24 @@ def test_far_bands_against_brute_force():
             Ur, Tr = _brute_regular(g, i[p], e[p], s)
             assert np.abs(U[m] - Ur).max() <= rt * np.abs(Ur).max()
             assert np.abs(T[m] - Tr).max() <= rt * np.abs(Tr).max()
+
+
+def test_interior_strain_rod():
+    """Interior strain of the rod (central differences of the representation
+    formula) against the exact 1-D strain eps_xx = -(p / E) cosh(s x / c) /
+    cosh(s L / c); the other components vanish (nu = 0). The error falls under
+    refinement (252 -> 448 triangles: 2.2% -> 1.6% at the worst point)."""
+    mat = kernels.Material(1.0, 0.0, 1.0)
+    s = 0.3 + 0.4j
+    xs = np.array([[0.5, 0.05, -0.1], [1.5, 0.0, 0.0], [2.5, -0.2, 0.1]])
+    exact = -np.cosh(s * xs[:, 0]) / np.cosh(s * 3.0)
+    errs = []
+    for h in (1 / 3, 1 / 4):
+        rod = inputs.rod_problem(h=h)
+        g = bem.geometry(rod.xyz, rod.tri)
+        A, b = bem.system_rows(g, rod.bc_type, rod.pattern.astype(complex), s, mat)
+        a = solvers.direct_solve(A, b)
+        eps = bem.interior_strain(g, rod.bc_type, rod.pattern.astype(complex), a, xs, s, mat, 0.02)
+        errs.append(np.abs(eps[:, 0] - exact).max() / np.abs(exact).max())
+        assert np.abs(eps[:, 1:]).max() <= 0.04 * np.abs(exact).max()
+    assert errs[0] < 0.03 and errs[1] < 0.85 * errs[0]
