@@ -79,6 +79,15 @@ extern "C" {
                              their actual ranks; one operator set (no overlap of
                              the next frequency's assembly with the solve) */
 
+/* block-diagonal preconditioner of GMRES (Sec. 3.1, Sec. 5: "block diagonal",
+ * block size not stated) */
+#define BEM_PRECOND_BLOCK3 0 /* the 3 x 3 diagonal block of each element (default) */
+#define BEM_PRECOND_LEAF 1   /* the diagonal block of each cluster-tree leaf (up to
+                                64 elements: 192 x 192), inverted per frequency; needs
+                                leaf_size <= 64 */
+#define BEM_PRECOND_AUTO 2   /* a sweep solves its first frequency with k > 0 with
+                                both and keeps the one that took fewer GMRES steps */
+
 typedef struct bem_ctx bem_ctx;
 
 typedef struct bem_opts {
@@ -92,6 +101,7 @@ typedef struct bem_opts {
   int32_t guess;      /* BEM_GUESS_* */
   int32_t sem_k;      /* K previous solutions for the extrapolation (Sec. 4.2: 3-4) */
   int32_t dense;      /* 1: every block dense (no ACA); for small meshes and tests */
+  int32_t precond;    /* BEM_PRECOND_* (Sec. 5: block diagonal; block size unstated) */
 } bem_opts;
 
 typedef struct bem_freq_stats {
@@ -114,6 +124,11 @@ typedef struct bem_freq_stats {
                              (products in the operator's precision); with
                              BEM_GUESS_MLP, compare with guess_residual to see
                              what the learned column added; 1 without a guess */
+  int32_t precond;        /* BEM_PRECOND_BLOCK3 or BEM_PRECOND_LEAF: the one the
+                             accepted solve used */
+  int32_t trial_iters;    /* BEM_PRECOND_AUTO: Arnoldi steps of the comparison
+                             solve with the other preconditioner (included in
+                             iters); 0 otherwise */
 } bem_freq_stats;
 
 /* Fill *opts with the defaults: tol 1e-5, restart 50, max_iters 5000,
@@ -223,6 +238,13 @@ int bem_assemble(bem_ctx* ctx, double s_re, double s_im, const bem_opts* opts);
  * far-field entries reconstructed from the low-rank factors). */
 int bem_operator_rows(bem_ctx* ctx, const int64_t* rows, int64_t nrows, double* out);
 
+/* y = M^-1 x with the assembled operator's block-diagonal preconditioner
+ * (Sec. 3.1, Sec. 5): BEM_PRECOND_BLOCK3, the inverses of the 3 x 3 diagonal
+ * blocks (FP64), or BEM_PRECOND_LEAF, the inverses of the leaves' diagonal
+ * blocks (complex64 operator: FP32 Gauss-Jordan; complex128: FP64), which
+ * need an assembly with precond = BEM_PRECOND_LEAF (STATE otherwise).
+ * x, y: N complex (caller order). */
+int bem_apply_preconditioner(bem_ctx* ctx, int32_t precond, const double* x, double* y);
 /* y = A x with the assembled operator (FP64 accumulation). x, y: N complex. */
 int bem_apply(bem_ctx* ctx, const double* x, double* y);
 
@@ -395,6 +417,8 @@ typedef struct bem_profile {
   int64_t kernel_launches;  /* kernels launched by the library since profiling was (re)enabled */
   int64_t aca_blocks;       /* admissible blocks assembled */
   int64_t aca_stepped;      /* of which took ACA steps (were not settled by pivot reuse alone) */
+  int64_t aca_failures;     /* admissible blocks of the last assembly whose ACA reached the rank
+                               cap (min(3 min(rows, cols), 256)) without meeting aca_tol */
 } bem_profile;
 
 /* Enable (1) or disable (0) event timing of the H-matrix products and of

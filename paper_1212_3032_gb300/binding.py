@@ -24,6 +24,7 @@ PREC_C64_MIXED, PREC_C128 = 0, 1
 GUESS_ZERO, GUESS_SEM, GUESS_MLP = 0, 1, 2
 FAR_AUTO, FAR_FULL, FAR_COMPACT = 0, 1, 2
 FIELD_DISPLACEMENT, FIELD_STRAIN = 0, 1
+PRECOND_BLOCK3, PRECOND_LEAF, PRECOND_AUTO = 0, 1, 2
 
 EXPORTED = [
     "bem_default_opts", "bem_create", "bem_destroy", "bem_last_error", "bem_mesh", "bem_mesh_dev",
@@ -36,7 +37,7 @@ EXPORTED = [
     "bem_far_block_info", "bem_set_far_storage", "bem_get_far_storage",
     "bem_add_mesh", "bem_mesh_count", "bem_solve_sweep_batched", "bem_mesh_frequency_solution",
     "bem_mesh_time_response", "bem_block_tree", "bem_interior_field", "bem_interior_strain",
-    "bem_interior_time_response",
+    "bem_interior_time_response", "bem_apply_preconditioner",
 ]
 
 
@@ -50,7 +51,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("aca_tol", ctypes.c_double), ("leaf_size", ctypes.c_int32), ("eta_adm", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("guess", ctypes.c_int32), ("sem_k", ctypes.c_int32),
-                ("dense", ctypes.c_int32)]
+                ("dense", ctypes.c_int32), ("precond", ctypes.c_int32)]
 
 
 class FreqStats(ctypes.Structure):
@@ -59,7 +60,8 @@ class FreqStats(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("guess_residual", ctypes.c_double),
                 ("assemble_ms", ctypes.c_double), ("guess_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("near_bytes", ctypes.c_int64), ("far_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int32),
-                ("aca_failures", ctypes.c_int32), ("sem_residual", ctypes.c_double)]
+                ("aca_failures", ctypes.c_int32), ("sem_residual", ctypes.c_double),
+                ("precond", ctypes.c_int32), ("trial_iters", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -69,7 +71,7 @@ class Profile(ctypes.Structure):
     _fields_ = [("hmv_launches", ctypes.c_int64), ("hmv_ms", ctypes.c_double), ("hmv_bytes", ctypes.c_double),
                 ("assemble_calls", ctypes.c_int64), ("assemble_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("aca_blocks", ctypes.c_int64),
-                ("aca_stepped", ctypes.c_int64)]
+                ("aca_stepped", ctypes.c_int64), ("aca_failures", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -160,6 +162,7 @@ def load_library(path: str = LIB_PATH):
         "bem_mesh_time_response": (ctypes.c_int, [P, ctypes.c_int32, P, I64, P]),
         "bem_get_far_storage": (ctypes.c_int, [P, P]),
         "bem_interior_field": (ctypes.c_int, [P, I32, P, I64, P]),
+        "bem_apply_preconditioner": (ctypes.c_int, [P, I32, P, P]),
         "bem_interior_strain": (ctypes.c_int, [P, I32, P, I64, D, P]),
         "bem_interior_time_response": (ctypes.c_int, [P, P, I64, I32, D, P]),
         "bem_mlp_num_params": (I64, []),
@@ -416,6 +419,13 @@ class Context:
         x = _c128(x)
         y = np.zeros_like(x)
         self._check(self.lib.bem_apply(self.h, _ptr(x), _ptr(y)))
+        return y
+
+    def apply_preconditioner(self, x, precond=PRECOND_BLOCK3):
+        """M^-1 x with the assembled operator's 3 x 3 or leaf-block preconditioner."""
+        x = _c128(x)
+        y = np.zeros_like(x)
+        self._check(self.lib.bem_apply_preconditioner(self.h, int(precond), _ptr(x), _ptr(y)))
         return y
 
     def rhs(self, p, pattern):

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbem.so")
 
-SOURCES = ["bem_assemble.cu", "bem_solve.cu", "bem_api.cu", "bem_noalloc.cu", "bem_mlp.cu", "bem_interior.cu", "bem_tree.cpp"]
+SOURCES = ["bem_assemble.cu", "bem_solve.cu", "bem_api.cu", "bem_noalloc.cu", "bem_mlp.cu", "bem_interior.cu", "bem_precond.cu", "bem_tree.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]

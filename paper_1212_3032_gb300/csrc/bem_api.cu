@@ -304,6 +304,9 @@ void swap_ops(bem_ctx* ctx) {
   swap_buf(ctx->u64, o.u64);
   swap_buf(ctx->v64, o.v64);
   swap_buf(ctx->prec_inv, o.prec_inv);
+  swap_buf(ctx->minv32, o.minv32);
+  swap_buf(ctx->minv64, o.minv64);
+  std::swap(ctx->minv_ready, o.minv_ready);
   swap_buf(ctx->b64, o.b64);
   swap_buf(ctx->rank, o.rank);
   swap_buf(ctx->aca_fail, o.aca_fail);
@@ -385,6 +388,7 @@ extern "C" void bem_default_opts(bem_opts* o) {
   o->guess = BEM_GUESS_SEM;
   o->sem_k = 4;
   o->dense = 0;
+  o->precond = BEM_PRECOND_BLOCK3;
 }
 
 extern "C" void bem_destroy(bem_ctx* ctx);
@@ -588,7 +592,7 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
     fb.c0 = s.begin;
     fb.nc = s.size();
     int mn = 3 * std::min(fb.nr, fb.nc);
-    fb.rmax = std::min(mn, 128);
+    fb.rmax = std::min(mn, ACA_RANK_CAP);
     fb.toff = toff;
     ucap += 3LL * fb.nr * fb.rmax;
     vcap += 3LL * fb.nc * fb.rmax;
@@ -772,7 +776,137 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   BEM_CUDA_TRY(cudaMemsetAsync(ctx->leaf_cnt.p, 0, std::max(1, L) * sizeof(int), st));
   BEM_CUDA_TRY(ctx->tasks.alloc(std::max<size_t>(1, tk.size())));
   BEM_CUDA_TRY(ctx->task_ptr.alloc(L + 1));
-  BEM_CUDA_TRY(ctx->part.alloc(std::max<long long>(1, 8 * slot)));  // 4 rhs x complex FP64
+  // fused product items: the near tasks (their panels) and one item per
+  // admissible block; each leaf's contributions in a fixed order (its near
+  // tasks, then the blocks over its rows by block index)
+  {
+    std::vector<HItem> hi;
+    std::vector<double> cost;
+    std::vector<std::vector<long long>> contrib(L);
+    long long hs = 0;
+    for (const Task& t : tk) {
+      if (t.kind != 0) continue;
+      HItem it;
+      it.slot = hs;
+      it.kind = 0;
+      it.p0 = t.p0;
+      it.p1 = t.p1;
+      it.l0 = t.leaf;
+      it.l1 = t.leaf + 1;
+      double c = 0;
+      for (int p = t.p0; p < t.p1; ++p) c += 3.0 * nr[t.leaf] * pan[p].ncols;
+      contrib[t.leaf].push_back(hs);
+      hs += 3LL * nr[t.leaf] + 1;  // +1: rows are written in pairs
+      hi.push_back(it);
+      cost.push_back(c);
+    }
+    // far items: the admissible blocks of one row cluster, in runs bounded in
+    // count, in summed rank caps (the V^T x values stay in shared memory) and
+    // in estimated entries (ranks are known on the device only; a typical
+    // rank of 48 stands for them)
+    std::vector<int> fl(ctx->far_h.size());
+    for (size_t b = 0; b < fl.size(); ++b) fl[b] = (int)b;
+    std::stable_sort(fl.begin(), fl.end(), [&](int a, int b) {
+      const FarBlk &A = ctx->far_h[a], &Bq = ctx->far_h[b];
+      return A.r0 != Bq.r0 ? A.r0 < Bq.r0 : A.nr < Bq.nr;
+    });
+    const double ITEM_ENTRIES = 131072.0;
+    int tcols_max = 0;
+    for (size_t i = 0; i < fl.size();) {
+      const FarBlk& f0 = ctx->far_h[fl[i]];
+      size_t j = i;
+      int tcols = 0;
+      double c = 0;
+      while (j < fl.size()) {
+        const FarBlk& fj = ctx->far_h[fl[j]];
+        if (fj.r0 != f0.r0 || fj.nr != f0.nr) break;
+        const double cj = std::min(fj.rmax, 48) * 3.0 * (fj.nr + fj.nc);
+        if (j > i && ((int)(j - i) >= HITEM_MAX_BLOCKS || tcols + fj.rmax > HITEM_MAX_TCOLS || c + cj > ITEM_ENTRIES))
+          break;
+        tcols += fj.rmax;
+        c += cj;
+        ++j;
+      }
+      HItem it;
+      it.slot = hs;
+      it.kind = 1;
+      it.p0 = (int)i;
+      it.p1 = (int)j;
+      it.l0 = (int)(std::lower_bound(r0.begin(), r0.end(), f0.r0) - r0.begin());
+      int l = it.l0;
+      for (; l < L && r0[l] + nr[l] <= f0.r0 + f0.nr; ++l) contrib[l].push_back(hs + 3LL * (r0[l] - f0.r0));
+      it.l1 = l;
+      cost.push_back(c);
+      hs += 3LL * f0.nr + 1;
+      hi.push_back(it);
+      tcols_max = std::max(tcols_max, tcols);
+      i = j;
+    }
+    ctx->hitem_tcols = tcols_max;
+    BEM_CUDA_TRY(ctx->hfar_list.alloc(std::max<size_t>(1, fl.size())));
+    if (!fl.empty())
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->hfar_list.p, fl.data(), fl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    std::vector<int> ord(hi.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<HItem> hs_sorted(hi.size());
+    for (size_t i = 0; i < ord.size(); ++i) hs_sorted[i] = hi[ord[i]];
+    std::vector<int> cptr(L + 1, 0);
+    std::vector<long long> coff;
+    for (int l = 0; l < L; ++l) {
+      cptr[l] = (int)coff.size();
+      coff.insert(coff.end(), contrib[l].begin(), contrib[l].end());
+    }
+    cptr[L] = (int)coff.size();
+    ctx->nhitems = (int)hs_sorted.size();
+    ctx->hpart_rows = hs;
+    BEM_CUDA_TRY(ctx->hitems.alloc(std::max<size_t>(1, hs_sorted.size())));
+    BEM_CUDA_TRY(ctx->hc_ptr.alloc(L + 1));
+    BEM_CUDA_TRY(ctx->hc_off.alloc(std::max<size_t>(1, coff.size())));
+    if (!hs_sorted.empty())
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->hitems.p, hs_sorted.data(), hs_sorted.size() * sizeof(HItem),
+                                   cudaMemcpyHostToDevice, st));
+    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->hc_ptr.p, cptr.data(), (L + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!coff.empty())
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->hc_off.p, coff.data(), coff.size() * sizeof(long long),
+                                   cudaMemcpyHostToDevice, st));
+    BEM_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors outlive the copies
+  }
+  // leaf-block preconditioner: each leaf's diagonal block is its near block
+  // with itself; unavailable when a leaf exceeds LEAF_PRE_MAX_ELEMS
+  {
+    std::vector<LeafPre> lp(L);
+    bool ok = L > 0;
+    long long oo = 0;
+    std::vector<int> self_blk(L, -1);
+    for (size_t b = 0; b < tr.near.size(); ++b)
+      if (tr.near[b].tau == tr.near[b].sigma && leaf_idx[tr.near[b].tau] >= 0) self_blk[leaf_idx[tr.near[b].tau]] = (int)b;
+    for (int l = 0; l < L && ok; ++l) {
+      if (nr[l] > LEAF_PRE_MAX_ELEMS || self_blk[l] < 0) {
+        ok = false;
+        break;
+      }
+      const NearBlk& nb = ctx->near_h[self_blk[l]];
+      lp[l].off = nb.off;
+      lp[l].ld = nb.ld;
+      lp[l].m = 3 * nr[l];
+      lp[l].ldo = (3 * nr[l] + 1) & ~1;
+      lp[l].e0 = r0[l];
+      lp[l].ooff = oo;
+      oo += (long long)lp[l].ldo * lp[l].m;
+    }
+    ctx->nleaf_pre = ok ? L : 0;
+    ctx->leaf_pre_entries = ok ? oo : 0;
+    ctx->minv_ready = false;
+    ctx->back.minv_ready = false;
+    if (ok) {
+      BEM_CUDA_TRY(ctx->leaf_pre.alloc(L));
+      BEM_CUDA_TRY(cudaMemcpyAsync(ctx->leaf_pre.p, lp.data(), L * sizeof(LeafPre), cudaMemcpyHostToDevice, st));
+      BEM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+  }
+  // 4 rhs x complex FP64, for the task product and the fused product
+  BEM_CUDA_TRY(ctx->part.alloc(std::max<long long>(1, 8 * std::max(slot, ctx->hpart_rows))));
   if (!tk.empty())
     BEM_CUDA_TRY(cudaMemcpyAsync(ctx->tasks.p, tk.data(), tk.size() * sizeof(Task), cudaMemcpyHostToDevice, st));
   BEM_CUDA_TRY(cudaMemcpyAsync(ctx->task_ptr.p, tptr.data(), (L + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1093,6 +1227,9 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
   // near field run on the caller's stream; they write disjoint storage and
   // join before the assembly ends.
   const bool mixed = is_mixed(ctx);
+  // leaf-block inverses: asked for, or a sweep's AUTO choice still open or made for them
+  const bool want_leaf = ctx->nleaf_pre > 0 && (o.precond == BEM_PRECOND_LEAF ||
+                                                (o.precond == BEM_PRECOND_AUTO && ctx->pre_auto != 1));
   KParams<float> Pf = make_params<float>(ctx, sre, sim);
   if (mixed) {
     if (ctx->near32.n < (size_t)std::max<long long>(1, ctx->near_entries)) ctx->near_zero_pending = true;
@@ -1138,6 +1275,11 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
                                     ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pf, ctx->near32.p,
                                     b ? ctx->patf.p : nullptr, b ? ctx->pattern.p : nullptr, pk, b, st);
     CK("near_regular");
+    if (want_leaf) {
+      BEM_CUDA_TRY(ctx->minv32.ensure(std::max<long long>(1, ctx->leaf_pre_entries)));
+      BEM_CUDA_TRY(launch_leaf_inverse<float>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->near32.p, ctx->prec_inv.p,
+                                              ctx->minv32.p, st));
+    }
     long long n9 = 9LL * ctx->ne;
     count_if(true);
     k_pinv_cast<<<(unsigned)((n9 + 255) / 256), 256, 0, st>>>(ctx->prec_inv.p, ctx->prec_inv32.p, n9);
@@ -1154,7 +1296,13 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
                                       ctx->poff.p, ctx->pcount.p, ctx->ef.p, ctx->ed.p, ctx->bc.p, Pd, ctx->near64.p,
                                       b ? ctx->patf.p : nullptr, b ? ctx->pattern.p : nullptr, pk, b, st);
     CK("near_regular");
+    if (want_leaf) {
+      BEM_CUDA_TRY(ctx->minv64.ensure(std::max<long long>(1, ctx->leaf_pre_entries)));
+      BEM_CUDA_TRY(launch_leaf_inverse<double>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->near64.p, ctx->prec_inv.p,
+                                               ctx->minv64.p, st));
+    }
   }
+  ctx->minv_ready = want_leaf;
   if (mixed) TRY((far_field_finish<float, c64>(ctx, Pf, ctx->u32, ctx->v32, ctx->ws32, o, st)));
   else TRY((far_field_finish<double, c128>(ctx, Pd, ctx->u64, ctx->v64, ctx->ws64, o, st)));
   prof_end(ctx, ev, 1, 0.0, 0.0, st);
@@ -1320,6 +1468,7 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
   TRY(ensure_host_cols(ctx, slot_len * (m + 1), m + 1));
   double* hcol = ctx->host_cols;
   const Pm* pinv = basis_pinv<Pm>(ctx);
+  const bool leaf = ctx->use_leaf_pre && ctx->minv_ready;
   Vb* V = Vbuf.p;
   int its = 0, cycles = 0;
   double rel = 1.0;
@@ -1331,7 +1480,16 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
   auto enqueue = [&](int j) -> int {
     Vb* vj = V + (long long)j * N;
     c128* hd = hdev + j * slot_len;
-    launch_precond<Pm, Vb, Vb>(pinv, vj, zbuf.p, ctx->ne, st);
+    if (leaf) {
+      if constexpr (mixed)
+        launch_leaf_apply<c64, c64, c64>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv32.p,
+                                         reinterpret_cast<const c64*>(vj), reinterpret_cast<c64*>(zbuf.p), st);
+      else
+        launch_leaf_apply<c128, c128, c128>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv64.p,
+                                            reinterpret_cast<const c128*>(vj), reinterpret_cast<c128*>(zbuf.p), st);
+    } else {
+      launch_precond<Pm, Vb, Vb>(pinv, vj, zbuf.p, ctx->ne, st);
+    }
     cudaEvent_t ev = prof_begin(ctx);
     if (mixed)
       launch_hmatvec<c64, c64, c64, float>(ctx, ctx->near32.p, ctx->u32.p, ctx->v32.p,
@@ -1450,7 +1608,14 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
     }
     BEM_CUDA_TRY(cudaMemcpyAsync(hdev, hh, jdone * sizeof(c128), cudaMemcpyHostToDevice, st));
     launch_combine<Vb>(V, N, jdone, hdev, ctx->tmp64.p, N, st);
-    launch_precond<c128, c128, c128>(ctx->prec_inv.p, ctx->tmp64.p, ctx->tmp64.p + N, ctx->ne, st);
+    if (leaf && mixed)
+      launch_leaf_apply<c64, c128, c128>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv32.p, ctx->tmp64.p,
+                                         ctx->tmp64.p + N, st);
+    else if (leaf)
+      launch_leaf_apply<c128, c128, c128>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv64.p, ctx->tmp64.p,
+                                          ctx->tmp64.p + N, st);
+    else
+      launch_precond<c128, c128, c128>(ctx->prec_inv.p, ctx->tmp64.p, ctx->tmp64.p + N, ctx->ne, st);
     launch_axpy(c128{1.0, 0.0}, ctx->tmp64.p + N, x, N, st);
     CK("update x");
     BEM_CUDA_TRY(cudaStreamSynchronize(st));  // hh reused next cycle
@@ -1462,6 +1627,7 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
     stats->cycles = cycles;
     stats->rel_residual = rel;
     stats->converged = converged ? 1 : 0;
+    stats->precond = leaf ? BEM_PRECOND_LEAF : BEM_PRECOND_BLOCK3;
   }
   return converged ? BEM_OK : BEM_ERR_NOT_CONVERGED;
 }
@@ -1654,6 +1820,33 @@ extern "C" int bem_apply(bem_ctx* ctx, const double* x, double* y) {
   return BEM_OK;
 }
 
+extern "C" int bem_apply_preconditioner(bem_ctx* ctx, int32_t precond, const double* x, double* y) {
+  if (!ctx || !x || !y) return BEM_ERR_INVALID_ARG;
+  if (!ctx->assembled) return fail(ctx, BEM_ERR_STATE, "operator not assembled");
+  if (precond != BEM_PRECOND_BLOCK3 && precond != BEM_PRECOND_LEAF)
+    return fail(ctx, BEM_ERR_INVALID_ARG, "precond must be BEM_PRECOND_BLOCK3 or BEM_PRECOND_LEAF");
+  if (precond == BEM_PRECOND_LEAF && !ctx->minv_ready)
+    return fail(ctx, BEM_ERR_STATE, "no leaf-block inverses: assemble with precond = BEM_PRECOND_LEAF");
+  TRY(set_device(ctx));
+  std::vector<c128> xt;
+  to_tree(ctx, x, xt);
+  DevBuf<c128> xd, yd;
+  BEM_CUDA_TRY(xd.alloc(ctx->N));
+  BEM_CUDA_TRY(yd.alloc(ctx->N));
+  BEM_CUDA_TRY(cudaMemcpyAsync(xd.p, xt.data(), ctx->N * sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+  if (precond == BEM_PRECOND_BLOCK3)
+    launch_precond<c128, c128, c128>(ctx->prec_inv.p, xd.p, yd.p, ctx->ne, ctx->stream);
+  else if (is_mixed(ctx))
+    launch_leaf_apply<c64, c128, c128>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv32.p, xd.p, yd.p, ctx->stream);
+  else
+    launch_leaf_apply<c128, c128, c128>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv64.p, xd.p, yd.p, ctx->stream);
+  CK("apply preconditioner");
+  BEM_CUDA_TRY(cudaMemcpyAsync(xt.data(), yd.p, ctx->N * sizeof(c128), cudaMemcpyDeviceToHost, ctx->stream));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  from_tree(ctx, xt, y);
+  return BEM_OK;
+}
+
 extern "C" int bem_rhs(bem_ctx* ctx, double p_re, double p_im, const double* pattern, double* b) {
   if (!ctx || !pattern || !b) return BEM_ERR_INVALID_ARG;
   if (!ctx->assembled) return fail(ctx, BEM_ERR_STATE, "operator not assembled");
@@ -1707,6 +1900,10 @@ extern "C" int bem_solve_assembled(bem_ctx* ctx, const double* b, const double* 
   BEM_CUDA_TRY(ctx->x64.ensure(ctx->N));
   BEM_CUDA_TRY(cudaMemcpyAsync(ctx->b64.p, bt.data(), ctx->N * sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
   BEM_CUDA_TRY(cudaMemcpyAsync(ctx->x64.p, xt.data(), ctx->N * sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+  if (o.precond == BEM_PRECOND_LEAF && !ctx->minv_ready)
+    return fail(ctx, BEM_ERR_STATE, "assemble with precond = BEM_PRECOND_LEAF first");
+  ctx->use_leaf_pre = ctx->minv_ready && (o.precond == BEM_PRECOND_LEAF ||
+                                          (o.precond == BEM_PRECOND_AUTO && ctx->pre_auto == 2));
   bem_freq_stats s{};
   auto t0 = std::chrono::steady_clock::now();
   int rc = gmres(ctx, ctx->b64.p, ctx->x64.p, o, &s);
@@ -1820,6 +2017,7 @@ static int sweep_body(bem_ctx* ctx, double T, int n_omega, const double* load_de
   // GMRES of frequency k run on the caller's stream (compact storage keeps one
   // operator set: frequency k + 1 is assembled after frequency k is solved)
   const bool pipe = !ctx->far_compact;
+  ctx->pre_auto = 0;
   cudaEventRecord(ta[0].a, st);
   TRY(assemble_impl(ctx, ctx->eta, 0.0, o, ctx->pattern.p, ctx->Pk_host[0], ctx->b64.p, st));
   cudaEventRecord(ta[0].b, st);
@@ -1858,7 +2056,44 @@ static int sweep_body(bem_ctx* ctx, double T, int n_omega, const double* load_de
     }
     cudaEventRecord(t1.b, st);
     cudaEventRecord(t2.a, st);
-    int rc = gmres(ctx, ctx->b64.p, xk, o, &s);
+    int rc;
+    if (o.precond == BEM_PRECOND_AUTO && ctx->pre_auto == 0 && k >= 1 && ctx->minv_ready) {
+      // the first frequency with k > 0 is solved with both preconditioners
+      // from the same initial guess; the one with fewer Arnoldi steps is kept
+      // for the rest of the sweep (both solutions meet the tolerance)
+      BEM_CUDA_TRY(ctx->w64.ensure(2 * N));
+      c128* x0 = ctx->w64.p;
+      c128* x3 = ctx->w64.p + N;
+      BEM_CUDA_TRY(cudaMemcpyAsync(x0, xk, N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
+      bem_freq_stats s3 = s;
+      ctx->use_leaf_pre = false;
+      const int rc3 = gmres(ctx, ctx->b64.p, xk, o, &s3);
+      if (rc3 != BEM_OK && rc3 != BEM_ERR_NOT_CONVERGED) return rc3;
+      BEM_CUDA_TRY(cudaMemcpyAsync(x3, xk, N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
+      BEM_CUDA_TRY(cudaMemcpyAsync(xk, x0, N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
+      ctx->use_leaf_pre = true;
+      rc = gmres(ctx, ctx->b64.p, xk, o, &s);
+      if (rc != BEM_OK && rc != BEM_ERR_NOT_CONVERGED) return rc;
+      const bool leaf_wins = rc == BEM_OK && (rc3 != BEM_OK || s.iters < s3.iters);
+      ctx->pre_auto = leaf_wins ? 2 : 1;
+      const int trial = leaf_wins ? s3.iters : s.iters;
+      if (!leaf_wins) {
+        BEM_CUDA_TRY(cudaMemcpyAsync(xk, x3, N * sizeof(c128), cudaMemcpyDeviceToDevice, st));
+        s.iters = s3.iters;
+        s.cycles = s3.cycles;
+        s.rel_residual = s3.rel_residual;
+        s.converged = s3.converged;
+        s.precond = s3.precond;
+        rc = rc3;
+      }
+      s.guess_residual = s3.guess_residual;
+      s.trial_iters = trial;
+      s.iters += trial;
+    } else {
+      ctx->use_leaf_pre = ctx->minv_ready && (o.precond == BEM_PRECOND_LEAF ||
+                                              (o.precond == BEM_PRECOND_AUTO && ctx->pre_auto == 2));
+      rc = gmres(ctx, ctx->b64.p, xk, o, &s);
+    }
     cudaEventRecord(t2.b, st);
     s.sem_residual = fit ? ctx->host_red[SEM_RES_SLOT] : 1.0;  // gmres synchronised the stream
     if (rc != BEM_OK && rc != BEM_ERR_NOT_CONVERGED) return rc;
@@ -1934,6 +2169,10 @@ static int sweep_checks(bem_ctx* ctx, double T, int32_t n_omega, const bem_opts&
     return fail(ctx, BEM_ERR_INVALID_ARG, "unknown precision");
   if (o.guess != BEM_GUESS_ZERO && o.guess != BEM_GUESS_SEM && o.guess != BEM_GUESS_MLP)
     return fail(ctx, BEM_ERR_INVALID_ARG, "unknown initial guess");
+  if (o.precond != BEM_PRECOND_BLOCK3 && o.precond != BEM_PRECOND_LEAF && o.precond != BEM_PRECOND_AUTO)
+    return fail(ctx, BEM_ERR_INVALID_ARG, "unknown preconditioner");
+  if (o.precond == BEM_PRECOND_LEAF && ctx->nleaf_pre == 0)
+    return fail(ctx, BEM_ERR_INVALID_ARG, "the leaf-block preconditioner needs leaves of at most 64 elements");
   return BEM_OK;
 }
 
@@ -2182,6 +2421,10 @@ extern "C" int bem_get_profile(bem_ctx* ctx, bem_profile* out) {
   out->kernel_launches = launch_count() - ctx->launches_at_reset;
   out->aca_blocks = ctx->prof_aca_blocks;
   out->aca_stepped = ctx->prof_aca_continued + (ctx->prof_dev.p ? lr[0] : 0);
+  int fails = 0;
+  if (ctx->assembled && ctx->aca_fail.p)
+    BEM_CUDA_TRY(cudaMemcpy(&fails, ctx->aca_fail.p, sizeof(int), cudaMemcpyDeviceToHost));
+  out->aca_failures = fails;
   return BEM_OK;
 }
 

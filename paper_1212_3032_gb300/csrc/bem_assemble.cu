@@ -1007,7 +1007,7 @@ __device__ __forceinline__ void aca_col3(const ElemF* ef, const ElemD* ed, const
 // ---------------------------------------------------------------------------
 constexpr int ACA_THREADS = 128;
 constexpr int ACA_WARPS = ACA_THREADS / 32;
-constexpr int ACA_RMAX = 128;
+constexpr int ACA_RMAX = ACA_RANK_CAP;
 constexpr int ACA_EXTRA = 2;  // pivots recorded past the stopping point (spares for the next frequency)
 
 template <typename T> struct AcaShared {
@@ -1098,7 +1098,8 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
   using T = decltype(Op{}.re);
   const T eps = T(eps_d);
   const int bi = list[blockIdx.x];
-  if (st.done && st.done[bi]) return;
+  const int dstate = st.done ? st.done[bi] : 0;
+  if (dstate == 1) return;
   FarBlk B = blks[bi];
   const int m = 3 * B.nr, n = 3 * B.nc;
   Op* Ub = Ustore + B.uoff;
@@ -1109,9 +1110,18 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
   const int rmax = min(B.rmax, ACA_RMAX);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int k = st.kstart ? min(st.kstart[bi], rmax) : 0;
+  const int k0 = k;
   int istar = 0;
   T normS2 = k ? T(st.norm0[bi]) : T(0);
-  if (k > 0) {
+  int kconv = -1;  // rank at which the stopping test first held
+  // dstate 2: the reused steps met the stopping test (rank set by the reuse);
+  // only the check rows remain, as after any converged ACA
+  bool check_only = dstate == 2 && k > 0;
+  if (check_only) {
+    for (int l = threadIdx.x; l < k; l += blockDim.x) sh.rows_used[l] = piv_i[l];
+    kconv = rank[bi];
+    __syncthreads();
+  } else if (k > 0) {
     // continue from a reused cross approximation of rank k: its pivot rows
     // are used, the next row is the largest entry of u_{k-1} outside them
     for (int l = threadIdx.x; l < k; l += blockDim.x) sh.rows_used[l] = piv_i[l];
@@ -1138,10 +1148,14 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
     istar = inext;
     __syncthreads();
   }
-  int kconv = -1;         // rank at which the stopping test first held
   int vnext = 0;          // components whose check row has been examined
   bool have_row = false;  // V[:, k] already holds the residual row of istar
   while (k < rmax) {
+   bool stop = false;
+   if (check_only) {
+    check_only = false;
+    stop = true;
+   } else {
     // --- residual row istar -> V[:, k]
     if (!have_row) aca_residual_row<R, T, Op>(ef, ed, bc, P, B, Ub, Vb, m, n, k, istar, threadIdx.x, blockDim.x);
     have_row = false;
@@ -1157,7 +1171,6 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
       }
     }
     aca_argmax(best, jstar, sh);
-    bool stop = false;
     if (!(best > T(0))) {
       if (kconv < 0) kconv = k;  // zero residual row
       stop = true;
@@ -1259,6 +1272,7 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
         }
       }
     }
+   }
     __syncthreads();
     if (!stop) continue;
     // --- the test held: check rows (residual into V[:, k]) before stopping
@@ -1295,6 +1309,7 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
     rank[bi] = kconv >= 0 ? kconv : k;
     st.npiv[bi] = k;
     if (kconv < 0) atomicAdd(fails, 1);
+    if (dstate == 2) st.done[bi] = k == k0 ? 1 : 0;  // settled by the reuse, or ACA steps were needed
   }
 }
 
@@ -1331,7 +1346,8 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
   const int item = blockIdx.x * ACAW_WARPS + wid;
   if (item >= count) return;
   const int bi = list[item];
-  if (st.done && st.done[bi]) return;
+  const int dstate = st.done ? st.done[bi] : 0;
+  if (dstate == 1) return;
   __shared__ int rows_used_all[ACAW_WARPS][ACA_RMAX];
   int* rows_used = rows_used_all[wid];
   const T eps = T(eps_d);
@@ -1343,9 +1359,16 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
   int* piv_j = st.piv_j + B.toff;
   const int rmax = min(B.rmax, ACA_RMAX);
   int k = st.kstart ? min(st.kstart[bi], rmax) : 0;
+  const int k0 = k;
   int istar = 0;
   T normS2 = k ? T(st.norm0[bi]) : T(0);
-  if (k > 0) {
+  int kconv = -1;
+  bool check_only = dstate == 2 && k > 0;  // only the check rows remain (see k_aca)
+  if (check_only) {
+    for (int l = lane; l < k; l += 32) rows_used[l] = piv_i[l];
+    kconv = rank[bi];
+    __syncwarp();
+  } else if (k > 0) {
     // continue from a reused cross approximation of rank k (see k_aca)
     for (int l = lane; l < k; l += 32) rows_used[l] = piv_i[l];
     const int prev = piv_i[k - 1];
@@ -1371,10 +1394,14 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
     istar = inext;
     __syncwarp();
   }
-  int kconv = -1;
   int vnext = 0;          // components whose check row has been examined (see k_aca)
   bool have_row = false;  // V[:, k] already holds the residual row of istar
   while (k < rmax) {
+   bool stop = false;
+   if (check_only) {
+    check_only = false;
+    stop = true;
+   } else {
     if (!have_row) aca_residual_row<R, T, Op>(ef, ed, bc, P, B, Ub, Vb, m, n, k, istar, lane, 32);
     have_row = false;
     __syncwarp();
@@ -1389,7 +1416,6 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
       }
     }
     warp_argmax(best, jstar);
-    bool stop = false;
     if (!(best > T(0))) {
       if (kconv < 0) kconv = k;
       stop = true;
@@ -1468,6 +1494,7 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
         }
       }
     }
+   }
     __syncwarp();
     if (!stop) continue;
     // the test held: check rows before stopping (see k_aca)
@@ -1499,6 +1526,7 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
     rank[bi] = kconv >= 0 ? kconv : k;
     st.npiv[bi] = k;
     if (kconv < 0) atomicAdd(fails, 1);
+    if (dstate == 2) st.done[bi] = k == k0 ? 1 : 0;
   }
 }
 
@@ -1814,12 +1842,14 @@ __global__ void __launch_bounds__(NT) k_aca_warm_solve(const FarBlk* __restrict_
     }
     const int conv = lastfail + 1 < ls ? 1 : 0;
     const int kc = conv ? lastfail + 2 : ls;
-    kstart[bi] = kc;
+    // converged: every validated step stays (the ones past the rank as
+    // spares) and the ACA kernels evaluate the check rows against all of them
+    kstart[bi] = ls;
     norm0[bi] = double(S);
-    done[bi] = conv;
+    done[bi] = conv ? 2 : 0;
     if (conv) {
       rank[bi] = kc;
-      npiv[bi] = ls;  // the validated pivots past the rank stay as spares
+      npiv[bi] = ls;
     }
   }
 }

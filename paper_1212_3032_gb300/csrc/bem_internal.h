@@ -42,6 +42,9 @@ struct NearBlk {
   int ld;         // leading dimension (even, >= 3 nr)
 };
 
+// Rank cap of the admissible blocks: rmax = min(3 min(nr, nc), ACA_RANK_CAP).
+constexpr int ACA_RANK_CAP = 256;
+
 // Low-rank far-field block A ~ U V^T; U: (3 nr) x rmax column-major,
 // V: (3 nc) x rmax column-major; rank[b] <= rmax set by ACA.
 struct FarBlk {
@@ -74,6 +77,31 @@ struct Task {
   int kind;    // 0: near panels, 1: far panels
 };
 
+// One leaf's diagonal block for the leaf-block preconditioner: the near
+// block of the leaf with itself (offset, leading dimension, m = 3 nr rows),
+// the leaf's first element (tree order) and its inverse's place (column-major,
+// leading dimension ldo, even).
+constexpr int LEAF_PRE_MAX_ELEMS = 64;
+struct LeafPre {
+  long long off;
+  long long ooff;
+  int ld, m, ldo, e0;
+};
+
+// Work item of the fused H-matrix product (one CTA each): kind 0 = the
+// dense near panels [p0, p1) of leaf l0 (a near Task's panels); kind 1 = the
+// admissible blocks far_list[p0, p1), all with the same row cluster (t = V^T x
+// for each, then sum_b U_b t_b over the row cluster, leaves [l0, l1)). Its
+// rows go to the partial buffer from row `slot` on.
+struct HItem {
+  long long slot;
+  int kind;
+  int p0, p1;  // kind 1: a range of the far-block list (blocks of one row cluster)
+  int l0, l1;
+};
+constexpr int HITEM_MAX_BLOCKS = 24;    // admissible blocks per far item
+constexpr int HITEM_MAX_TCOLS = 2048;   // their rank caps summed (V^T x values kept in shared memory)
+
 // Singular (SELF) and near-singular (NEAR) element pairs, FP64 path.
 struct SingPair {
   int i, e;         // collocation element, integration element (tree order)
@@ -85,12 +113,13 @@ struct SingPair {
 // Start state of the ACA kernels (cross-frequency pivot reuse). Pivots are
 // recorded for every block at offset FarBlk::toff; kstart / norm0 / done may
 // be null (every block starts from rank 0).
-constexpr int WARM_RMAX = 128;  // largest reused rank (= the rank cap)
+constexpr int WARM_RMAX = 128;  // largest reused rank (blocks above restart ACA at every frequency)
 constexpr int WARM_SPLIT = 64;  // rank classes of the reuse solve: (0, 64] and above
 struct AcaState {
   const int* kstart;    // per far block: rank to continue from
   const double* norm0;  // per far block: ||S||_F^2 estimate at that rank
-  const int* done;      // per far block: 1 = converged already (skip)
+  int* done;            // per far block: 1 = converged already (skip); 2 = converged on the
+                        // reused pivots, check rows pending (set to 1 or 0 by the ACA kernels)
   int* piv_i;           // pivot row of each step (block-local scalar index)
   int* piv_j;           // pivot column of each step
   int* npiv;            // per far block: pivots recorded (rank plus spares)
@@ -130,11 +159,12 @@ struct MlpState;  // learned initial guess (bem_mlp.cu)
 // keeps two: frequency k + 1 is assembled into one while GMRES runs on the
 // other (the context's fields hold the set in use; swap_ops exchanges them).
 struct OpSet {
-  DevBuf<c64> near32, u32, v32, prec_inv32;
-  DevBuf<c128> near64, u64, v64, prec_inv, b64;
+  DevBuf<c64> near32, u32, v32, prec_inv32, minv32;
+  DevBuf<c128> near64, u64, v64, prec_inv, b64, minv64;
   DevBuf<int> rank, aca_fail, status;
   DevBuf<long long> fbase;
   bool near_zero_pending = true;
+  bool minv_ready = false;
   bool fbase_ready = false;
   int prof_slot = 0;
 };
@@ -211,6 +241,15 @@ struct bem_ctx {
   long long part_rows = 0;            // rows of the partial buffer per right-hand side
   bem::DevBuf<bem::Task> tasks;
   bem::DevBuf<int> task_order;        // task indices by size, largest first (launch order)
+  // fused product: items in launch order (largest estimated cost first), and
+  // per leaf the partial-buffer offsets of its rows in each contribution
+  int nhitems = 0;
+  long long hpart_rows = 0;           // rows of the partial buffer per right-hand side
+  bem::DevBuf<bem::HItem> hitems;
+  bem::DevBuf<int> hfar_list;         // admissible blocks grouped by row cluster (far items' ranges)
+  int hitem_tcols = 0;                // largest sum of rank caps over a far item
+  bem::DevBuf<int> hc_ptr;            // CSR over leaves
+  bem::DevBuf<long long> hc_off;
   cudaStream_t aux_stream = nullptr;  // the far-field assembly runs here, joined back to stream
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t asm_stream = nullptr;  // a sweep assembles frequency k + 1 here while GMRES(k) runs
@@ -270,6 +309,17 @@ struct bem_ctx {
   bem::DevBuf<int> status;             // singular 3x3 diagonal block flag
   bem::DevBuf<bem::c128> prec_inv;     // ne x 9 inverse diagonal blocks
   bem::DevBuf<bem::c64> prec_inv32;
+  // leaf-block preconditioner (BEM_PRECOND_LEAF): the leaves' diagonal blocks,
+  // their inverses at the current frequency, and which preconditioner the
+  // solves use (a sweep with BEM_PRECOND_AUTO decides at its first k > 0)
+  int nleaf_pre = 0;                   // 0: leaves above LEAF_PRE_MAX_ELEMS (unavailable)
+  long long leaf_pre_entries = 0;
+  bem::DevBuf<bem::LeafPre> leaf_pre;
+  bem::DevBuf<bem::c64> minv32;
+  bem::DevBuf<bem::c128> minv64;
+  bool minv_ready = false;             // inverses of the set in use match its operator
+  bool use_leaf_pre = false;           // the solves apply the leaf inverses
+  int pre_auto = 0;                    // BEM_PRECOND_AUTO in a sweep: 0 undecided, 1 3x3 kept, 2 leaf kept
 
   // solver workspace
   bem::DevBuf<bem::c64> V32;           // Krylov basis (m+1) x N

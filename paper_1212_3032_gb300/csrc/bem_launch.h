@@ -135,4 +135,15 @@ void launch_interior(const double* pts, int npts, const ElemD* ed, int ne, const
 void launch_offset_points(const double* pts, int npts, double h, double* out, cudaStream_t st);
 void launch_strain(const c128* uoff, int npts, double h, c128* eps, cudaStream_t st);
 
+// ---- leaf-block preconditioner (bem_precond.cu) ----
+// Inverses of the leaves' diagonal blocks of the near storage (FP32 Gauss-
+// Jordan for complex64 blocks, FP64 for complex128); pinv3: the 3 x 3 block
+// inverses a leaf falls back to if its block is singular.
+template <typename R>
+cudaError_t launch_leaf_inverse(const LeafPre* leaves, int nleaves, const cplx<R>* near, const c128* pinv3,
+                                cplx<R>* out, cudaStream_t st);
+// z = M^-1 v with the leaf inverses (tree order vectors)
+template <typename Pm, typename V, typename Z>
+void launch_leaf_apply(const LeafPre* leaves, int nleaves, const Pm* minv, const V* v, Z* z, cudaStream_t st);
+
 }  // namespace bem

@@ -307,22 +307,363 @@ __global__ void __launch_bounds__(256) k_hmv_reduce(const int* __restrict__ leaf
   }
 }
 
+// ---------------------------------------------------------------------------
+// The fused product: one launch, one CTA per work item (HItem), items in
+// decreasing order of estimated cost (CTAs are dispatched in index order).
+//   near item: dense near panels of one leaf row, as hmv_task, but each
+//              thread owns a PAIR of rows and reads both entries of a column
+//              with one 16-byte load (near panels: even ld, even offsets)
+//   far item:  one admissible block b: t = V_b^T x with 16-byte loads that
+//              stream the block's factor columns two at a time as one flat
+//              range (t kept in shared memory), then U_b t over the block's
+//              row cluster (row pairs, 16-byte loads where aligned)
+// Items write their rows to their own slot of the partial buffer; the item
+// that completes a leaf's last contribution (a per-leaf arrival counter)
+// adds the leaf's contributions in a fixed order (FP64) and writes y.
+// ---------------------------------------------------------------------------
+constexpr int HF_THREADS = 384;
+constexpr int HF_WARPS = HF_THREADS / 32;
+
+__device__ __forceinline__ void ld_pair(const c64* p, c64& a, c64& b) {
+  const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+  a = c64{v.x, v.y};
+  b = c64{v.z, v.w};
+}
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+template <typename Acc> __device__ __forceinline__ cplx<Acc> czero() { return cplx<Acc>{Acc(0), Acc(0)}; }
+
+// (V^T x) for the columns l0 (and l0 + 1 if len = 2 n) of one factor V, whose
+// columns of n entries are contiguous: the pair is streamed as one flat range
+// of len entries with 16-byte loads (complex64: two entries per load, one
+// entry before the first 16-byte boundary and one after the last); per-lane
+// partial sums a0 (column l0) and a1 (column l0 + 1)
+template <typename Op, typename X, typename Acc, int NRHS>
+__device__ __forceinline__ void hf_vtx_pair(const Op* __restrict__ base, int len, int n, const X* __restrict__ xs,
+                                            long long N, cplx<Acc> (&a0)[NRHS], cplx<Acc> (&a1)[NRHS]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < NRHS; ++q) a0[q] = a1[q] = czero<Acc>();
+  // entry f of the range: column l0 + (f >= n), row f - n (f >= n)
+  auto add = [&](int f, const Op& v) {
+    const bool c1 = f >= n;
+    const int row = c1 ? f - n : f;
+    const cplx<Acc> vv = up<Acc>(v);
+#pragma unroll
+    for (int q = 0; q < NRHS; ++q) {
+      const cplx<Acc> xv = up<Acc>(xs[q * N + row]);
+      if (c1) cmac(a1[q], vv, xv);
+      else cmac(a0[q], vv, xv);
+    }
+  };
+  if constexpr (sizeof(Op) == 8) {
+    const int head = aligned16(base) ? 0 : 1;
+    if (head && lane == 0) add(0, ld_stream(base));
+    const int body = (len - head) >> 1;
+    const Op* bp = base + head;
+    int c = lane;
+    for (; c + 96 < body; c += 128) {
+      Op v[8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ld_pair(bp + 2 * (c + 32 * u), v[2 * u], v[2 * u + 1]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        add(head + 2 * (c + 32 * u), v[2 * u]);
+        add(head + 2 * (c + 32 * u) + 1, v[2 * u + 1]);
+      }
+    }
+    for (; c < body; c += 32) {
+      Op v0, v1;
+      ld_pair(bp + 2 * c, v0, v1);
+      add(head + 2 * c, v0);
+      add(head + 2 * c + 1, v1);
+    }
+    if (((len - head) & 1) && lane == 0) add(len - 1, ld_stream(base + len - 1));
+  } else {
+    int f = lane;
+    for (; f + 96 < len; f += 128) {
+      Op v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = ld_stream(base + f + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) add(f + 32 * u, v[u]);
+    }
+    for (; f < len; f += 32) add(f, ld_stream(base + f));
+  }
+}
+
+// The admissible blocks of one far item (all with the same row cluster),
+// as read by hf_item_rows: factor offsets, column-cluster sizes and starts,
+// and the prefix sums of their ranks (columns) and of their column pairs.
+struct HfBlocks {
+  long long u[HITEM_MAX_BLOCKS], v[HITEM_MAX_BLOCKS];
+  int n[HITEM_MAX_BLOCKS], c0[HITEM_MAX_BLOCKS];
+  int cpre[HITEM_MAX_BLOCKS + 1], ppre[HITEM_MAX_BLOCKS + 1];
+  int nb;
+};
+
+// E consecutive rows of one column at p (E = 2 for complex64, 1 for complex128)
+__device__ __forceinline__ void ld_rows(const c64* p, bool pair_ok, c64 (&v)[2]) {
+  if (pair_ok && aligned16(p)) {
+    ld_pair(p, v[0], v[1]);
+  } else {
+    v[0] = ld_stream(p);
+    v[1] = pair_ok ? ld_stream(p + 1) : c64{0.f, 0.f};
+  }
+}
+__device__ __forceinline__ void ld_rows(const c128* p, bool, c128 (&v)[1]) { v[0] = ld_stream(p); }
+
+// Rows [0, m) of one item: kind 0 sums its near panels against x, kind 1
+// sums the r columns of U (column stride m) against ts; each thread owns E
+// consecutive rows and one of G column groups (the groups are added in
+// shared memory). Writes rows [0, m) (and the pad row m for m odd) to the
+// item's slot.
+template <typename Op, typename X, typename Acc, int NRHS>
+__device__ __forceinline__ void hf_item_rows(const HItem& it, int m, const Panel* __restrict__ panels,
+                                             const Op* __restrict__ near, const Op* __restrict__ U,
+                                             const HfBlocks& fb, int tsn, const X* __restrict__ x, long long N,
+                                             const cplx<Acc>* ts, cplx<Acc>* __restrict__ part, long long pstride,
+                                             cplx<Acc>* red) {
+  constexpr int E = 16 / (int)sizeof(Op);
+  const int RP = (m + E - 1) / E;
+  for (int rbase = 0; rbase < RP; rbase += HF_THREADS) {
+    const int rc = min(RP - rbase, HF_THREADS);
+    const int G = max(1, HF_THREADS / rc);
+    const int g = threadIdx.x / rc;
+    const int rl = threadIdx.x % rc;
+    const int row = (rl + rbase) * E;
+    const bool active = g < G;
+    cplx<Acc> acc[E][NRHS];
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int q = 0; q < NRHS; ++q) acc[e][q] = czero<Acc>();
+    if (active) {
+      if (it.kind == 0) {
+        for (int p = it.p0; p < it.p1; ++p) {
+          const Panel P = panels[p];
+          const long long ld = P.ld;
+          const Op* d = near + P.data + row;  // pairs of rows: even ld and offsets, pad row stored
+          const X* xs = x + P.xoff;
+          const int nc = P.ncols;
+          int j = g;
+          for (; j + 7 * G < nc; j += 8 * G) {
+            Op av[8][E];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) ld_rows(d + (long long)(j + u * G) * ld, true, av[u]);
+            X xv[NRHS][8];
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+              for (int u = 0; u < 8; ++u) xv[q][u] = xs[q * N + j + u * G];
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int e = 0; e < E; ++e) cmac(acc[e][q], up<Acc>(av[u][e]), up<Acc>(xv[q][u]));
+          }
+          for (; j < nc; j += G) {
+            Op av[E];
+            ld_rows(d + (long long)j * ld, true, av);
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q) {
+              const cplx<Acc> xq = up<Acc>(xs[q * N + j]);
+#pragma unroll
+              for (int e = 0; e < E; ++e) cmac(acc[e][q], up<Acc>(av[e]), xq);
+            }
+          }
+        }
+      } else {
+        // the columns of all the item's factors U_b, c < C, in block order;
+        // column c of block i (cpre[i] <= c < cpre[i + 1]) is its column c - cpre[i]
+        const bool pair_ok = row + E - 1 < m;
+        const int C = fb.cpre[fb.nb];
+        int cur = 0;
+        int c = g;
+        for (; c + 3 * G < C; c += 4 * G) {
+          Op av[4][E];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int cc = c + u * G;
+            while (cc >= fb.cpre[cur + 1]) ++cur;
+            ld_rows(U + fb.u[cur] + (long long)(cc - fb.cpre[cur]) * m + row, pair_ok, av[u]);
+          }
+#pragma unroll
+          for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const cplx<Acc> tq = ts[q * tsn + c + u * G];
+#pragma unroll
+              for (int e = 0; e < E; ++e) cmac(acc[e][q], up<Acc>(av[u][e]), tq);
+            }
+        }
+        for (; c < C; c += G) {
+          while (c >= fb.cpre[cur + 1]) ++cur;
+          Op av[E];
+          ld_rows(U + fb.u[cur] + (long long)(c - fb.cpre[cur]) * m + row, pair_ok, av);
+#pragma unroll
+          for (int q = 0; q < NRHS; ++q) {
+            const cplx<Acc> tq = ts[q * tsn + c];
+#pragma unroll
+            for (int e = 0; e < E; ++e) cmac(acc[e][q], up<Acc>(av[e]), tq);
+          }
+        }
+      }
+    }
+    if (G > 1) {
+      if (active && g > 0) {
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+          for (int e = 0; e < E; ++e) red[((q * G + g) * rc + rl) * E + e] = acc[e][q];
+      }
+      __syncthreads();
+      if (active && g == 0) {
+        for (int gg = 1; gg < G; ++gg)
+#pragma unroll
+          for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const cplx<Acc> o = red[((q * G + gg) * rc + rl) * E + e];
+              acc[e][q].re += o.re;
+              acc[e][q].im += o.im;
+            }
+      }
+      __syncthreads();
+    }
+    if (active && g == 0) {
+#pragma unroll
+      for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (row + e <= m) part[q * pstride + it.slot + row + e] = acc[e][q];
+    }
+  }
+}
+
+template <typename Op, typename X, typename Y, typename Acc, int NRHS>
+__global__ void __launch_bounds__(HF_THREADS, (NRHS == 1 && sizeof(Acc) == 4) ? 3 : 2) k_hmv_fused(
+    const HItem* __restrict__ items, const int* __restrict__ far_list, const int* __restrict__ leaf_r0,
+    const int* __restrict__ leaf_nr, const Panel* __restrict__ panels, const FarBlk* __restrict__ far,
+    const int* __restrict__ rank, const long long* __restrict__ fbase, const Op* __restrict__ near,
+    const Op* __restrict__ U, const Op* __restrict__ V, const X* __restrict__ x, long long N, int tsn,
+    cplx<Acc>* __restrict__ part, long long pstride, const int* __restrict__ hc_ptr,
+    const long long* __restrict__ hc_off, int* __restrict__ leaf_cnt, Y* __restrict__ y) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<Acc>* ts = reinterpret_cast<cplx<Acc>*>(smem_raw);  // NRHS x tsn: the items' V^T x values
+  cplx<Acc>* red = ts + NRHS * tsn;                        // NRHS x HF_THREADS x E
+  __shared__ HfBlocks fb;
+  __shared__ int last;
+  const HItem it = items[blockIdx.x];
+  if (it.kind == 0) {
+    if (threadIdx.x == 0) fb.nb = 0;
+    __syncthreads();
+    hf_item_rows<Op, X, Acc, NRHS>(it, 3 * leaf_nr[it.l0], panels, near, U, fb, tsn, x, N, ts, part, pstride, red);
+  } else {
+    int nrows = 0;
+    if (threadIdx.x == 0) {
+      int c = 0, pp = 0, nb = 0;
+      for (int i = it.p0; i < it.p1; ++i, ++nb) {
+        const int b = far_list[i];
+        const FarBlk Bk = far[b];
+        const int r = min(rank[b], Bk.rmax);
+        fb.u[nb] = fbase[2 * b];
+        fb.v[nb] = fbase[2 * b + 1];
+        fb.n[nb] = 3 * Bk.nc;
+        fb.c0[nb] = Bk.c0;
+        fb.cpre[nb] = c;
+        fb.ppre[nb] = pp;
+        c += r;
+        pp += (r + 1) / 2;
+      }
+      fb.cpre[nb] = c;
+      fb.ppre[nb] = pp;
+      fb.nb = nb;
+    }
+    nrows = 3 * far[far_list[it.p0]].nr;
+    __syncthreads();
+    // t = V_b^T x of every block, column pairs over the warps
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int cur = 0;
+    for (int pp = warp; pp < fb.ppre[fb.nb]; pp += HF_WARPS) {
+      while (pp >= fb.ppre[cur + 1]) ++cur;
+      const int r = fb.cpre[cur + 1] - fb.cpre[cur];
+      const int l0 = 2 * (pp - fb.ppre[cur]);
+      const int n = fb.n[cur];
+      cplx<Acc> a0[NRHS], a1[NRHS];
+      hf_vtx_pair<Op, X, Acc, NRHS>(V + fb.v[cur] + (long long)l0 * n, min(2, r - l0) * n, n, x + 3LL * fb.c0[cur],
+                                    N, a0, a1);
+#pragma unroll
+      for (int q = 0; q < NRHS; ++q) {
+        const Acc r0 = wsum(a0[q].re), i0 = wsum(a0[q].im), r1 = wsum(a1[q].re), i1 = wsum(a1[q].im);
+        if (lane == 0) {
+          ts[q * tsn + fb.cpre[cur] + l0] = cplx<Acc>{r0, i0};
+          if (l0 + 1 < r) ts[q * tsn + fb.cpre[cur] + l0 + 1] = cplx<Acc>{r1, i1};
+        }
+      }
+    }
+    __syncthreads();
+    hf_item_rows<Op, X, Acc, NRHS>(it, nrows, panels, near, U, fb, tsn, x, N, ts, part, pstride, red);
+  }
+  __threadfence();  // this item's partials are visible before its arrivals are counted
+  __syncthreads();
+  for (int l = it.l0; l < it.l1; ++l) {
+    const int c0 = hc_ptr[l], c1 = hc_ptr[l + 1];
+    if (threadIdx.x == 0) last = atomicAdd(&leaf_cnt[l], 1) == c1 - c0 - 1;
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      const int rows = 3 * leaf_nr[l];
+      const long long row0 = 3LL * leaf_r0[l];
+      for (int rr = threadIdx.x; rr < rows; rr += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q) {
+          cplx<double> sum{0, 0};
+          for (int k = c0; k < c1; ++k) {
+            const cplx<Acc> v = ld_global_cg(part + q * pstride + hc_off[k] + rr);
+            sum.re += v.re;
+            sum.im += v.im;
+          }
+          Y o;
+          o.re = decltype(o.re)(sum.re);
+          o.im = decltype(o.im)(sum.im);
+          y[q * N + row0 + rr] = o;
+        }
+      }
+      if (threadIdx.x == 0) leaf_cnt[l] = 0;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename Op, typename X, typename Y, typename Acc, int NRHS>
 static void hmv_impl(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V, cplx<Acc>* t,
                      const X* x, Y* y, cudaStream_t st) {
-  int nfar = (int)ctx->far_h.size();
-  if (count_if(nfar))
-    k_hmv_t<Op, X, Acc, NRHS><<<nfar, 256, 0, st>>>(ctx->far_d.p, ctx->rank.p, ctx->fbase.p, V, x, ctx->N, t,
-                                                    ctx->t_entries);
+  (void)t;
+  if (!ctx->nhitems) return;
+  constexpr int E = 16 / (int)sizeof(Op);
+  const int tsn = std::max(1, ctx->hitem_tcols);
+  const size_t sm = (size_t)NRHS * (tsn + (size_t)HF_THREADS * E) * sizeof(cplx<Acc>);
+  // the attribute is per function and device: set once per device, to the
+  // largest size any mesh can ask for
+  const size_t sm_max = (size_t)NRHS * (HITEM_MAX_TCOLS + (size_t)HF_THREADS * E) * sizeof(cplx<Acc>);
+  if (sm_max > 48 * 1024) {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+      cudaFuncSetAttribute(k_hmv_fused<Op, X, Y, Acc, NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm_max);
+      if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+  }
   cplx<Acc>* part = reinterpret_cast<cplx<Acc>*>(ctx->part.p);
-  size_t sm = (size_t)HMV_THREADS * NRHS * sizeof(cplx<Acc>);  // red: NRHS x G x rows <= NRHS x threads
-  // every task, largest first (CTAs are dispatched in index order: the long
-  // tasks start early and the short ones fill the tail)
-  if (count_if(ctx->ntasks))
-    k_hmv_tasks_list<Op, X, Y, Acc, NRHS><<<ctx->ntasks, HMV_THREADS, sm, st>>>(
-        ctx->task_order.p, ctx->tasks.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p, ctx->fbase.p,
-        near, U, t, ctx->t_entries, x, ctx->N, part, ctx->part_rows, ctx->leaf_r0.p, ctx->task_ptr.p,
-        ctx->leaf_cnt.p, y);
+  count_if(true);
+  k_hmv_fused<Op, X, Y, Acc, NRHS><<<ctx->nhitems, HF_THREADS, sm, st>>>(
+      ctx->hitems.p, ctx->hfar_list.p, ctx->leaf_r0.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p,
+      ctx->fbase.p, near, U, V, x, ctx->N, tsn, part, ctx->hpart_rows, ctx->hc_ptr.p, ctx->hc_off.p,
+      ctx->leaf_cnt.p, y);
 }
 
 template <typename Op, typename X, typename Y, typename Acc>

@@ -28,14 +28,15 @@ def test_builds_and_exports_every_declared_symbol():
 
 
 def test_struct_layouts_match_header():
-    # bem_opts: 10 fields with natural alignment; bem_freq_stats likewise
-    assert ctypes.sizeof(binding.Opts) == 56
-    assert ctypes.sizeof(binding.FreqStats) == 16 + 7 * 8 + 2 * 8 + 8 + 8
-    assert ctypes.sizeof(binding.Profile) == 8 * 8
+    # bem_opts: 11 fields with natural alignment; bem_freq_stats likewise
+    assert ctypes.sizeof(binding.Opts) == 64
+    assert ctypes.sizeof(binding.FreqStats) == 16 + 7 * 8 + 2 * 8 + 8 + 8 + 8
+    assert ctypes.sizeof(binding.Profile) == 9 * 8
     assert ctypes.sizeof(binding.FarStorage) == 4 + 4 + 3 * 8 + 4 + 4
     o = binding.default_opts()
     assert o.tol == 1e-5 and o.restart == 50 and o.leaf_size == 64 and o.sem_k == 4
     assert o.precision == binding.PREC_C64_MIXED and o.guess == binding.GUESS_SEM
+    assert o.precond == binding.PRECOND_BLOCK3
 
 
 def test_create_without_device_fails_cleanly():

@@ -113,7 +113,9 @@ def test_compact_sweep_equals_pipelined_sweep(B):
 def test_flat_face_blocks(B, prec, aca_tol):
     # cube faces: coplanar admissible blocks couple normal rows only to
     # tangential columns and tangential rows only to normal columns; ACA must
-    # approximate both parts (its per-component check rows)
+    # approximate both parts (its per-component check rows), also when the
+    # previous frequency's pivots are reused. k = 16 (|s| = 12.6): the ranks
+    # of the largest flat-face blocks go above 128; none may stop at the cap
     mesh = inputs.cube_with_cavities(n_face=24, n_cav=2, cav_radius=0.15, cav_n=8, seed=3032)
     c = _ctx(B, B.FAR_AUTO)
     try:
@@ -122,18 +124,19 @@ def test_flat_face_blocks(B, prec, aca_tol):
         g = bem.geometry(mesh.xyz, mesh.tri)
         rows_e = np.array([10, 500, 1500, 3000, 4000, 6000, mesh.ne - 5])
         sel = (3 * rows_e[:, None] + np.arange(3)).ravel()
-        for k in (8, 9):  # fresh ACA, then pivot reuse (ranks well below the cap of 128)
+        for k in (16, 17):  # fresh ACA, then pivot reuse
             s = 4.0 / T + 1j * k * 2 * math.pi / T
+            c.set_profiling(True)
             c.assemble(s, o)
+            prof = c.get_profile()
+            c.set_profiling(False)
+            assert prof["aca_failures"] == 0, k
             A_ref, _ = bem.system_rows(g, mesh.bc_type, mesh.pattern.astype(complex), s, MAT, rows=rows_e)
             got = c.operator_rows(sel)
-            info = c.far_block_info()
-            at_cap = int(np.sum((info[:, 2] >= 128) & (3 * np.minimum(info[:, 0], info[:, 1]) > 128)))
             err = np.array([_rel(got[q], A_ref[q]) for q in range(len(sel))])
             # ACA's stopping test bounds a block's Frobenius error by about
-            # aca_tol; one row of it may carry a few tens of that. A block
-            # missing its second part is off by 1e3 aca_tol and more.
-            assert np.sqrt(np.mean(err ** 2)) <= 30 * aca_tol and err.max() <= 100 * aca_tol, (k, at_cap, err)
+            # aca_tol; a block missing its second part is off by 1e3 aca_tol
+            assert err.max() <= 30 * aca_tol, (k, err)
     finally:
         c.close()
 
