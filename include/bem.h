@@ -306,9 +306,9 @@ int bem_far_block_info(bem_ctx* ctx, int64_t nmax, int32_t* info, int64_t* count
 
 /* Far-field factor storage of the meshes set after this call (mode
  * BEM_FAR_AUTO, _FULL or _COMPACT). The admissible blocks' factors at their
- * rank caps (3 min(rows, cols) elements, at most 128 columns) need
- * 3 (rows + cols) x cap complex entries per block: at 231k elements that is
- * 374 GB in complex64, though ACA stops at a fraction of the cap. Compact
+ * rank caps (3 min(rows, cols) elements, at most 512 columns) need
+ * 3 (rows + cols) x cap complex entries per block: at 231k elements that is far
+ * above the device memory, though ACA stops at a fraction of the cap. Compact
  * storage runs ACA over consecutive runs of blocks (batches) whose capped
  * factors fit a workspace of `workspace_bytes` (0: 8 GiB for complex64,
  * 16 GiB for complex128, raised to the largest block when smaller) and
@@ -418,7 +418,7 @@ typedef struct bem_profile {
   int64_t aca_blocks;       /* admissible blocks assembled */
   int64_t aca_stepped;      /* of which took ACA steps (were not settled by pivot reuse alone) */
   int64_t aca_failures;     /* admissible blocks of the last assembly whose ACA reached the rank
-                               cap (min(3 min(rows, cols), 256)) without meeting aca_tol */
+                               cap (min(3 min(rows, cols), 512)) without meeting aca_tol */
 } bem_profile;
 
 /* Enable (1) or disable (0) event timing of the H-matrix products and of

@@ -581,7 +581,7 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   ctx->near_entries = noff;
   ctx->near_zero_pending = true;
   ctx->back.near_zero_pending = true;  // the other operator set's padding rows too
-  long long ucap = 0, vcap = 0, bigcap = 0;
+  long long ucap = 0, vcap = 0, bigcap = 0, uinit = 0, vinit = 0;
   int toff = 0;
   for (const BlockPair& bp : tr.far) {
     const Cluster& t = tr.nodes[bp.tau];
@@ -596,12 +596,16 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
     fb.toff = toff;
     ucap += 3LL * fb.nr * fb.rmax;
     vcap += 3LL * fb.nc * fb.rmax;
+    uinit += 3LL * fb.nr * std::min(fb.rmax, POOL_INIT_RANK);
+    vinit += 3LL * fb.nc * std::min(fb.rmax, POOL_INIT_RANK);
     bigcap = std::max(bigcap, 3LL * std::max(fb.nr, fb.nc) * fb.rmax);
     toff += fb.rmax;
     ctx->far_h.push_back(fb);
   }
   ctx->u_entries = ucap;
   ctx->v_entries = vcap;
+  ctx->u_init = uinit;
+  ctx->v_init = vinit;
   ctx->t_entries = toff;
   // factor storage: full (capped factors in place, two operator sets) unless
   // that would take over a quarter of the device memory, or compact is asked for
@@ -1139,7 +1143,7 @@ constexpr int FAR_CUR_SLOT = 4088;  // pinned host slots (two int64) of the pool
 
 // Compact storage: initial pool capacity (entries) of a factor whose capped
 // size is cap; the pools grow by a quarter over the need on overflow.
-static long long pool_initial(long long cap) { return std::max(1LL, cap / 6); }
+static long long pool_initial(long long init) { return std::max(1LL, init); }
 
 // Far field of one assembly in the precision Op, on the auxiliary stream:
 // storage, pivot-state snapshot (compact storage), ACA.
@@ -1151,8 +1155,8 @@ int far_field_begin(bem_ctx* ctx, const KParams<R>& P, DevBuf<Op>& U, DevBuf<Op>
     BEM_CUDA_TRY(U.ensure(std::max<long long>(1, ctx->u_entries)));
     BEM_CUDA_TRY(V.ensure(std::max<long long>(1, ctx->v_entries)));
   } else {
-    if (U.n == 0) BEM_CUDA_TRY(U.alloc(pool_initial(ctx->u_entries)));
-    if (V.n == 0) BEM_CUDA_TRY(V.alloc(pool_initial(ctx->v_entries)));
+    if (U.n == 0) BEM_CUDA_TRY(U.alloc(pool_initial(ctx->u_init)));
+    if (V.n == 0) BEM_CUDA_TRY(V.alloc(pool_initial(ctx->v_init)));
     BEM_CUDA_TRY(ws.ensure(std::max<long long>(2, 2 * ctx->ws_entries)));
     // the pivot state this assembly starts from, kept for a redo
     ctx->far_was_ok = ctx->aca_warm_ok;

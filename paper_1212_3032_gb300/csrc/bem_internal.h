@@ -43,7 +43,10 @@ struct NearBlk {
 };
 
 // Rank cap of the admissible blocks: rmax = min(3 min(nr, nc), ACA_RANK_CAP).
-constexpr int ACA_RANK_CAP = 256;
+constexpr int ACA_RANK_CAP = 512;
+// Compact storage: the pools start at every block's factors at this rank (or
+// its cap if lower) and grow on demand.
+constexpr int POOL_INIT_RANK = 20;
 
 // Low-rank far-field block A ~ U V^T; U: (3 nr) x rmax column-major,
 // V: (3 nc) x rmax column-major; rank[b] <= rmax set by ACA.
@@ -218,6 +221,7 @@ struct bem_ctx {
   bem::DevBuf<bem::NearBlk> near_d;
   bem::DevBuf<bem::FarBlk> far_d;
   long long near_entries = 0, u_entries = 0, v_entries = 0;  // u/v: factors at their rank caps
+  long long u_init = 0, v_init = 0;   // compact pools' first size (entries)
   int t_entries = 0;
   // far-field factor storage (bem_set_far_storage): full = every block at its
   // rank cap, written in place by ACA; compact = ACA runs batch by batch in a
