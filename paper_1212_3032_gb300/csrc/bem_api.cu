@@ -1467,7 +1467,7 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
   c128* hdev = part + 64LL * (m + 2);
   if (m + 1 > 512) return fail(ctx, BEM_ERR_INVALID_ARG, "restart length above 511");
   // partial sums of the cooperative orthogonalisation step
-  BEM_CUDA_TRY(ctx->orth_part.ensure((size_t)(2 * (m + 1) + 1) * arnoldi_orth_max_blocks()));
+  BEM_CUDA_TRY(ctx->orth_part.ensure((size_t)(2 * (m + 1) + 2) * arnoldi_orth_max_blocks()));
   c128* orth_part = ctx->orth_part.p;
   TRY(ensure_host_cols(ctx, slot_len * (m + 1), m + 1));
   double* hcol = ctx->host_cols;

@@ -543,7 +543,7 @@ __device__ __forceinline__ void hf_item_rows(const HItem& it, int m, const Panel
 }
 
 template <typename Op, typename X, typename Y, typename Acc, int NRHS>
-__global__ void __launch_bounds__(HF_THREADS, (NRHS == 1 && sizeof(Acc) == 4) ? 3 : 2) k_hmv_fused(
+__global__ void __launch_bounds__(HF_THREADS, (NRHS == 1 && sizeof(Acc) == 4) ? 4 : 2) k_hmv_fused(
     const HItem* __restrict__ items, const int* __restrict__ far_list, const int* __restrict__ leaf_r0,
     const int* __restrict__ leaf_nr, const Panel* __restrict__ panels, const FarBlk* __restrict__ far,
     const int* __restrict__ rank, const long long* __restrict__ fbase, const Op* __restrict__ near,
@@ -873,6 +873,21 @@ __device__ __forceinline__ void orth_partials(const Vb* __restrict__ V, long lon
     if (lane == 0) part[(long long)l * gridDim.x + blockIdx.x] = c128{dre, dim};
   }
 }
+// part[slot * nblk + block] = ||w||^2 over the slice (warp 0)
+template <typename Vb>
+__device__ __forceinline__ void orth_partials_self(const Vb* __restrict__ w, int slot, long long i0, long long i1,
+                                                   c128* __restrict__ part) {
+  using T = decltype(Vb{}.re);
+  if ((threadIdx.x >> 5) != 0) return;
+  const int lane = threadIdx.x & 31;
+  T s = 0;
+  for (long long i = i0 + lane; i < i1; i += 32) {
+    const Vb a = w[i];
+    s = fma(a.re, a.re, fma(a.im, a.im, s));
+  }
+  const double d = wsum((double)s);
+  if (lane == 0) part[(long long)slot * gridDim.x + blockIdx.x] = c128{d, 0.0};
+}
 // out[l] = sum_b part[l * nblk + b] for l < nvec, in block order (into shared memory)
 __device__ __forceinline__ void orth_sums(const c128* __restrict__ part, int nvec, c128* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -926,7 +941,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_arnoldi_orth(Vb* __restrict__ 
   const long long i0 = min(n, (long long)blockIdx.x * per), i1 = min(n, i0 + per);
   c128* p1 = part;
   c128* p2 = part + (long long)nvec * gridDim.x;
-  c128* p3 = p2 + (long long)nvec * gridDim.x;
+  c128* p3 = p2 + (long long)(nvec + 1) * gridDim.x;
   orth_partials<Vb>(V, ldv, nvec, w, i0, i1, p1);
   grid.sync();
   orth_sums(p1, nvec, h);
@@ -938,10 +953,15 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_arnoldi_orth(Vb* __restrict__ 
   __syncthreads();
   orth_update<Vb>(V, ldv, nvec, hT, w, i0, i1);
   __syncthreads();  // this block's slice of w is complete before its second pass reads it
+  // second projection's partials and ||w1||^2 of the slice (slot nvec of p2)
   orth_partials<Vb>(V, ldv, nvec, w, i0, i1, p2);
+  orth_partials_self<Vb>(w, nvec, i0, i1, p2);
   grid.sync();
-  orth_sums(p2, nvec, h);
+  orth_sums(p2, nvec + 1, h);
   __syncthreads();
+  const double n1 = h[nvec].re;
+  double h2sq = 0;
+  for (int l = 0; l < nvec; ++l) h2sq += h[l].re * h[l].re + h[l].im * h[l].im;  // same order in every block
   for (int l = threadIdx.x; l < nvec; l += blockDim.x) {
     hT[l] = mk<T>(T(h[l].re), T(h[l].im));
     if (blockIdx.x == 0) hcol[m + 1 + l] = h[l];
@@ -949,11 +969,17 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_arnoldi_orth(Vb* __restrict__ 
   __syncthreads();
   orth_update<Vb>(V, ldv, nvec, hT, w, i0, i1);
   __syncthreads();
-  orth_partials<Vb>(w, 0, 1, w, i0, i1, p3);  // ||w||^2 of the slice
-  grid.sync();
-  orth_sums(p3, 1, h);
-  __syncthreads();
-  const double nrm2 = h[0].re;
+  // ||w2||^2 = ||w1||^2 - ||h2||^2 (w1 = w2 + V h2 with w2 orthogonal to V);
+  // where that cancels (w nearly in the span of V) the norm is summed anew,
+  // a decision every block takes alike from the same sums
+  double nrm2 = n1 - h2sq;
+  if (!(nrm2 > 1e-2 * n1)) {
+    orth_partials<Vb>(w, 0, 1, w, i0, i1, p3);  // ||w||^2 of the slice
+    grid.sync();
+    orth_sums(p3, 1, h);
+    __syncthreads();
+    nrm2 = h[0].re;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) hcol[2 * (m + 1)] = c128{nrm2, 0.0};
   const T sc = T(nrm2 > 0 ? 1.0 / sqrt(nrm2) : 0.0);
   Vb* vn = V + (long long)(j + 1) * ldv;
