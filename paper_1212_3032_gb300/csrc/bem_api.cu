@@ -1507,7 +1507,12 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
                                                reinterpret_cast<c128*>(wbuf.p), 1, st);
     CK("arnoldi matvec");
     prof_end_hmv(ctx, ev, sizeof(Vb), sizeof(Vb), sizeof(Vb), 1);
-    BEM_CUDA_TRY(launch_arnoldi_orth<Vb>(V, N, j, wbuf.p, N, orth_part, hd, m, st));
+    {
+      CoopLane lane(ctx, st);
+      BEM_CUDA_TRY(lane.status());
+      BEM_CUDA_TRY(launch_arnoldi_orth<Vb>(V, N, j, wbuf.p, N, orth_part, hd, m, lane.stream()));
+      BEM_CUDA_TRY(lane.join());
+    }
     CK("arnoldi");
     BEM_CUDA_TRY(cudaMemcpyAsync(hcol + 2 * j * slot_len, hd, slot_len * sizeof(c128), cudaMemcpyDeviceToHost, st));
     BEM_CUDA_TRY(cudaEventRecord(ctx->col_events[j], st));

@@ -1094,12 +1094,12 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const int* __restrict__ lis
                                                      const signed char* __restrict__ bc, KParams<R> P,
                                                      Op* __restrict__ Ustore, Op* __restrict__ Vstore,
                                                      int* __restrict__ rank, int* __restrict__ fails, double eps_d,
-                                                     AcaState st, int want) {
+                                                     AcaState st) {
   using T = decltype(Op{}.re);
   const T eps = T(eps_d);
   const int bi = list[blockIdx.x];
   const int dstate = st.done ? st.done[bi] : 0;
-  if (dstate == 1 || (want >= 0 && dstate != want)) return;
+  if (dstate == 1) return;
   FarBlk B = blks[bi];
   const int m = 3 * B.nr, n = 3 * B.nc;
   Op* Ub = Ustore + B.uoff;
@@ -1340,14 +1340,14 @@ __global__ void __launch_bounds__(32 * ACAW_WARPS) k_aca_warp(const int* __restr
                                                               const signed char* __restrict__ bc, KParams<R> P,
                                                               Op* __restrict__ Ustore, Op* __restrict__ Vstore,
                                                               int* __restrict__ rank, int* __restrict__ fails,
-                                                              double eps_d, AcaState st, int want) {
+                                                              double eps_d, AcaState st) {
   using T = decltype(Op{}.re);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * ACAW_WARPS + wid;
   if (item >= count) return;
   const int bi = list[item];
   const int dstate = st.done ? st.done[bi] : 0;
-  if (dstate == 1 || (want >= 0 && dstate != want)) return;
+  if (dstate == 1) return;
   __shared__ int rows_used_all[ACAW_WARPS][ACA_RMAX];
   int* rows_used = rows_used_all[wid];
   const T eps = T(eps_d);
@@ -1915,21 +1915,16 @@ void launch_aca(const FarBlk* blks, const int* small_list, int nsmall, const int
                 const ElemF* ef, const ElemD* ed, const signed char* bc, const KParams<R>& P, Op* U, Op* V, int* rank,
                 int* fails, double eps, const AcaState& state, cudaStream_t st) {
   if (count_if(nlarge))
-    k_aca<R, Op><<<nlarge, ACA_THREADS, 0, st>>>(large_list, blks, ef, ed, bc, P, U, V, rank, fails, eps, state, -1);
+    k_aca<R, Op><<<nlarge, ACA_THREADS, 0, st>>>(large_list, blks, ef, ed, bc, P, U, V, rank, fails, eps, state);
   if (!nsmall) return;
   count_if(true);
   if (state.done) {
-    // after pivot reuse: the blocks the reuse did not settle continue ACA
-    // with one CTA each (fewer blocks, several steps: a CTA shortens each
-    // step); the blocks settled on reused steps only evaluate their check
-    // rows, one warp each (the launches' other blocks exit at once)
-    k_aca<R, Op><<<nsmall, ACA_THREADS, 0, st>>>(small_list, blks, ef, ed, bc, P, U, V, rank, fails, eps, state, 0);
-    count_if(true);
-    k_aca_warp<R, Op><<<(nsmall + ACAW_WARPS - 1) / ACAW_WARPS, 32 * ACAW_WARPS, 0, st>>>(
-        small_list, nsmall, blks, ef, ed, bc, P, U, V, rank, fails, eps, state, 2);
+    // continuation after pivot reuse: few blocks, a few steps each; one CTA
+    // per block shortens each step (blocks already settled exit at once)
+    k_aca<R, Op><<<nsmall, ACA_THREADS, 0, st>>>(small_list, blks, ef, ed, bc, P, U, V, rank, fails, eps, state);
   } else {
     k_aca_warp<R, Op><<<(nsmall + ACAW_WARPS - 1) / ACAW_WARPS, 32 * ACAW_WARPS, 0, st>>>(
-        small_list, nsmall, blks, ef, ed, bc, P, U, V, rank, fails, eps, state, -1);
+        small_list, nsmall, blks, ef, ed, bc, P, U, V, rank, fails, eps, state);
   }
 }
 

@@ -86,7 +86,7 @@ void launch_precond(const Pm* pinv, const V* v, Z* z, int ne, cudaStream_t st);
 template <typename Vb, typename W>
 int launch_dots(const Vb* V, long long ldv, int nvec, const W* w, long long n, c128* part, cudaStream_t st);
 // One Arnoldi orthogonalisation step (CGS2 against V_0..V_j, norm, and
-// V_{j+1} = w / ||w||) in four ordinary launches; hcol receives
+// V_{j+1} = w / ||w||) in a single cooperative launch; hcol receives
 // [h1 (m+1) | h2 (m+1) | ||w||^2]; part needs (2 (j+1) + 1) x
 // arnoldi_orth_max_blocks() complex values.
 template <typename Vb>

@@ -927,70 +927,59 @@ __device__ __forceinline__ void orth_update(const Vb* __restrict__ V, long long 
 constexpr int ORTH_THREADS = 256;
 constexpr int ORTH_MAXVEC = 513;  // shared-memory coefficient slots (restart + 1 <= 512)
 
-// CGS2 step of the Arnoldi process over four ordinary launches (no grid-wide
-// barrier, so no launch waits for every block to be resident next to the
-// assembly kernels that share the GPU). Each launch's blocks own one slice of
-// the rows; a launch reads the previous one's per-block partial sums and adds
-// them in block order itself (every block the same sums).
-//   1: p1 = slices of V^H w
-//   2: h1 = sum p1; w -= V h1; p2 = slices of V^H w
-//   3: h2 = sum p2; w -= V h2; p3 = slices of ||w||^2
-//   4: nrm2 = sum p3; v_{j+1} = w / sqrt(nrm2)
-// hcol: [h1 (m + 1) | h2 (m + 1) | nrm2], written by block 0.
 template <typename Vb>
-__device__ __forceinline__ void orth_slice(long long n, long long& i0, long long& i1) {
-  const long long per = (n + gridDim.x - 1) / gridDim.x;
-  i0 = min(n, (long long)blockIdx.x * per);
-  i1 = min(n, i0 + per);
-}
-
-template <typename Vb>
-__global__ void __launch_bounds__(ORTH_THREADS) k_orth1(const Vb* __restrict__ V, long long ldv, int j,
-                                                        const Vb* __restrict__ w, long long n,
-                                                        c128* __restrict__ part) {
-  long long i0, i1;
-  orth_slice<Vb>(n, i0, i1);
-  orth_partials<Vb>(V, ldv, j + 1, w, i0, i1, part);
-}
-
-template <typename Vb>
-__global__ void __launch_bounds__(ORTH_THREADS) k_orth2(const Vb* __restrict__ V, long long ldv, int j,
-                                                        Vb* __restrict__ w, long long n, c128* __restrict__ part,
-                                                        c128* __restrict__ hcol, int m, int pass) {
+__global__ void __launch_bounds__(ORTH_THREADS) k_arnoldi_orth(Vb* __restrict__ V, long long ldv, int j,
+                                                               Vb* __restrict__ w, long long n,
+                                                               c128* __restrict__ part, c128* __restrict__ hcol,
+                                                               int m) {
   using T = decltype(Vb{}.re);
+  cg::grid_group grid = cg::this_grid();
   __shared__ c128 h[ORTH_MAXVEC];
   __shared__ cplx<T> hT[ORTH_MAXVEC];
   const int nvec = j + 1;
-  long long i0, i1;
-  orth_slice<Vb>(n, i0, i1);
-  const c128* pin = part + (pass == 1 ? 0 : (long long)nvec * gridDim.x);
-  c128* pout = part + (pass == 1 ? (long long)nvec * gridDim.x : 2LL * nvec * gridDim.x);
-  orth_sums(pin, nvec, h);
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long i0 = min(n, (long long)blockIdx.x * per), i1 = min(n, i0 + per);
+  c128* p1 = part;
+  c128* p2 = part + (long long)nvec * gridDim.x;
+  c128* p3 = p2 + (long long)(nvec + 1) * gridDim.x;
+  orth_partials<Vb>(V, ldv, nvec, w, i0, i1, p1);
+  grid.sync();
+  orth_sums(p1, nvec, h);
   __syncthreads();
   for (int l = threadIdx.x; l < nvec; l += blockDim.x) {
     hT[l] = mk<T>(T(h[l].re), T(h[l].im));
-    if (blockIdx.x == 0) hcol[(pass == 1 ? 0 : m + 1) + l] = h[l];
+    if (blockIdx.x == 0) hcol[l] = h[l];
   }
   __syncthreads();
   orth_update<Vb>(V, ldv, nvec, hT, w, i0, i1);
-  __syncthreads();  // this block's slice of w is complete before its partials read it
-  if (pass == 1) orth_partials<Vb>(V, ldv, nvec, w, i0, i1, pout);
-  else orth_partials_self<Vb>(w, 0, i0, i1, pout);
-}
-
-template <typename Vb>
-__global__ void __launch_bounds__(ORTH_THREADS) k_orth4(Vb* __restrict__ V, long long ldv, int j,
-                                                        const Vb* __restrict__ w, long long n,
-                                                        const c128* __restrict__ part, c128* __restrict__ hcol,
-                                                        int m) {
-  using T = decltype(Vb{}.re);
-  __shared__ c128 h[1];
-  const int nvec = j + 1;
-  long long i0, i1;
-  orth_slice<Vb>(n, i0, i1);
-  orth_sums(part + 2LL * nvec * gridDim.x, 1, h);
+  __syncthreads();  // this block's slice of w is complete before its second pass reads it
+  // second projection's partials and ||w1||^2 of the slice (slot nvec of p2)
+  orth_partials<Vb>(V, ldv, nvec, w, i0, i1, p2);
+  orth_partials_self<Vb>(w, nvec, i0, i1, p2);
+  grid.sync();
+  orth_sums(p2, nvec + 1, h);
   __syncthreads();
-  const double nrm2 = h[0].re;
+  const double n1 = h[nvec].re;
+  double h2sq = 0;
+  for (int l = 0; l < nvec; ++l) h2sq += h[l].re * h[l].re + h[l].im * h[l].im;  // same order in every block
+  for (int l = threadIdx.x; l < nvec; l += blockDim.x) {
+    hT[l] = mk<T>(T(h[l].re), T(h[l].im));
+    if (blockIdx.x == 0) hcol[m + 1 + l] = h[l];
+  }
+  __syncthreads();
+  orth_update<Vb>(V, ldv, nvec, hT, w, i0, i1);
+  __syncthreads();
+  // ||w2||^2 = ||w1||^2 - ||h2||^2 (w1 = w2 + V h2 with w2 orthogonal to V);
+  // where that cancels (w nearly in the span of V) the norm is summed anew,
+  // a decision every block takes alike from the same sums
+  double nrm2 = n1 - h2sq;
+  if (!(nrm2 > 1e-2 * n1)) {
+    orth_partials<Vb>(w, 0, 1, w, i0, i1, p3);  // ||w||^2 of the slice
+    grid.sync();
+    orth_sums(p3, 1, h);
+    __syncthreads();
+    nrm2 = h[0].re;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) hcol[2 * (m + 1)] = c128{nrm2, 0.0};
   const T sc = T(nrm2 > 0 ? 1.0 / sqrt(nrm2) : 0.0);
   Vb* vn = V + (long long)(j + 1) * ldv;
@@ -1011,7 +1000,7 @@ int orth_grid(long long n) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_orth2<Vb>, ORTH_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi_orth<Vb>, ORTH_THREADS, 0);
     return std::max(1, sms * std::max(1, per));
   }();
   // about 256 rows per block, at most one wave of resident blocks
@@ -1023,15 +1012,9 @@ cudaError_t launch_arnoldi_orth(Vb* V, long long ldv, int j, Vb* w, long long n,
                                 cudaStream_t st) {
   if (j + 1 > ORTH_MAXVEC) return cudaErrorInvalidValue;
   const int nb = orth_grid<Vb>(n);
+  void* args[] = {&V, &ldv, &j, &w, &n, &part, &hcol, &m};
   count_if(true);
-  k_orth1<Vb><<<nb, ORTH_THREADS, 0, st>>>(V, ldv, j, w, n, part);
-  count_if(true);
-  k_orth2<Vb><<<nb, ORTH_THREADS, 0, st>>>(V, ldv, j, w, n, part, hcol, m, 1);
-  count_if(true);
-  k_orth2<Vb><<<nb, ORTH_THREADS, 0, st>>>(V, ldv, j, w, n, part, hcol, m, 2);
-  count_if(true);
-  k_orth4<Vb><<<nb, ORTH_THREADS, 0, st>>>(V, ldv, j, w, n, part, hcol, m);
-  return cudaGetLastError();
+  return cudaLaunchCooperativeKernel((const void*)k_arnoldi_orth<Vb>, dim3(nb), dim3(ORTH_THREADS), args, 0, st);
 }
 template cudaError_t launch_arnoldi_orth<c64>(c64*, long long, int, c64*, long long, c128*, c128*, int,
                                               cudaStream_t);

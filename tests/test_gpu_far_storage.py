@@ -165,7 +165,10 @@ def test_cube_with_cavities_full_size(B):
         assert c.far_storage()["compact"] == 1
         T = 8.0
         s = 4.0 / T + 1j * 16 * 2 * math.pi / T
+        c.set_profiling(True)
         c.assemble(s, o)
+        assert c.get_profile()["aca_failures"] == 0
+        c.set_profiling(False)
         free, total = torch.cuda.mem_get_info()
         assert total - free < 180e9
         st = c.far_storage()
@@ -181,7 +184,7 @@ def test_cube_with_cavities_full_size(B):
         sel = (3 * rows_e[:, None] + np.arange(3)).ravel()
         got = c.operator_rows(sel)
         err = np.array([_rel(got[q], A_ref[q]) for q in range(len(sel))])
-        assert np.sqrt(np.mean(err ** 2)) <= 30 * aca_tol and err.max() <= 100 * aca_tol, err
+        assert err.max() <= 30 * aca_tol, err
         b = c.rhs(1.0, mesh.pattern)
         assert _rel(b[sel], b_ref) <= 1e-4
         x, stats = c.solve_assembled(b, opts=o)
