@@ -1149,7 +1149,16 @@ cudaError_t launch_sem_fit(const c128* const* X, int C, int K, const c128* Y, co
   if (C < 1 || C > SEM_MAXC) return cudaErrorInvalidValue;
   SemCols cols{};
   for (int c = 0; c < C; ++c) cols.x[c] = X[c];
-  const int nb = orth_grid<c128>(n);
+  // resident blocks of this kernel (its shared memory differs from the
+  // Arnoldi kernel's), about 256 rows per block, at most one wave
+  static const int resident = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sem_fit, ORTH_THREADS, 0);
+    return std::max(1, sms * std::max(1, per));
+  }();
+  const int nb = (int)std::max<long long>(1, std::min<long long>(resident, (n + 255) / 256));
   void* args[] = {&cols, &C, &K, &Y, &b, &Q, &part, &a0, &res, &n};
   count_if(true);
   return cudaLaunchCooperativeKernel((const void*)k_sem_fit, dim3(nb), dim3(ORTH_THREADS), args, 0, st);
