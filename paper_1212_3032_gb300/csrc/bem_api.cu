@@ -424,6 +424,7 @@ extern "C" int bem_create(bem_ctx** out, int device, void* stream) {
       cudaStreamCreateWithPriority(&ctx->solve_stream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_solve_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_solve_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_far_cursor, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_asm_done, cudaEventDisableTiming) != cudaSuccess) {
@@ -455,6 +456,7 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
   }
   if (ctx->ev_solve_in) cudaEventDestroy(ctx->ev_solve_in);
   if (ctx->ev_solve_out) cudaEventDestroy(ctx->ev_solve_out);
+  if (ctx->ev_far_cursor) cudaEventDestroy(ctx->ev_far_cursor);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_asm_done) cudaEventDestroy(ctx->ev_asm_done);
@@ -1177,6 +1179,10 @@ int far_field_begin(bem_ctx* ctx, const KParams<R>& P, DevBuf<Op>& U, DevBuf<Op>
   return BEM_OK;
 }
 
+template <typename R, typename Op>
+int far_field_redo_if_needed(bem_ctx* ctx, const KParams<R>& P, DevBuf<Op>& U, DevBuf<Op>& V, DevBuf<Op>& ws,
+                             const bem_opts& o, cudaStream_t st);
+
 // Joins the far field into st. Compact storage: reads the pools' need; on an
 // overflow the pools grow to the need plus a quarter and the far field is
 // redone on st from the pivot state it started from (the same factors).
@@ -1188,7 +1194,26 @@ int far_field_finish(bem_ctx* ctx, const KParams<R>& P, DevBuf<Op>& U, DevBuf<Op
   if (!ctx->far_compact || !nf) return BEM_OK;
   long long* hc = reinterpret_cast<long long*>(ctx->host_red + FAR_CUR_SLOT);
   BEM_CUDA_TRY(cudaMemcpyAsync(hc, ctx->fbase.p + 2 * nf, 2 * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  if (ctx->far_defer) {
+    // checked by far_field_verify when this operator set comes into use
+    BEM_CUDA_TRY(cudaEventRecord(ctx->ev_far_cursor, st));
+    ctx->far_verify_pending = true;
+    ctx->far_pending_s[0] = P.s.re;
+    ctx->far_pending_s[1] = P.s.im;
+    return BEM_OK;
+  }
   BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return far_field_redo_if_needed<R, Op>(ctx, P, U, V, ws, o, st);
+}
+
+// Compact storage: if the last assembly's need exceeded the pools, grow them
+// to the need plus a quarter and redo the far field on st from the pivot
+// state it started from (the same factors). The need is in the pinned slot.
+template <typename R, typename Op>
+int far_field_redo_if_needed(bem_ctx* ctx, const KParams<R>& P, DevBuf<Op>& U, DevBuf<Op>& V, DevBuf<Op>& ws,
+                             const bem_opts& o, cudaStream_t st) {
+  const size_t nf = ctx->far_h.size();
+  long long* hc = reinterpret_cast<long long*>(ctx->host_red + FAR_CUR_SLOT);
   if (hc[0] <= (long long)U.n && hc[1] <= (long long)V.n) return BEM_OK;
   ctx->far_regrows += 1;
   const long long nu = std::min(ctx->u_entries, hc[0] + hc[0] / 4 + 1);
@@ -1326,6 +1351,23 @@ int assemble_impl(bem_ctx* ctx, double sre, double sim, const bem_opts& o, const
     }
     prof_harvest(ctx);
   }
+  return BEM_OK;
+}
+
+// Compact storage in a pipelined sweep: the deferred check of the assembly
+// whose operator set has just come into use (after its event), and a redo on
+// the context's stream when it overflowed the pools.
+int far_field_verify(bem_ctx* ctx, const bem_opts& o) {
+  if (!ctx->far_verify_pending) return BEM_OK;
+  ctx->far_verify_pending = false;
+  BEM_CUDA_TRY(cudaEventSynchronize(ctx->ev_far_cursor));
+  const double sre = ctx->far_pending_s[0], sim = ctx->far_pending_s[1];
+  if (is_mixed(ctx))
+    TRY((far_field_redo_if_needed<float, c64>(ctx, make_params<float>(ctx, sre, sim), ctx->u32, ctx->v32, ctx->ws32,
+                                              o, ctx->stream)));
+  else
+    TRY((far_field_redo_if_needed<double, c128>(ctx, make_params<double>(ctx, sre, sim), ctx->u64, ctx->v64,
+                                                ctx->ws64, o, ctx->stream)));
   return BEM_OK;
 }
 
@@ -2020,11 +2062,24 @@ static int sweep_body(bem_ctx* ctx, double T, int n_omega, const double* load_de
   // assembled on asm_stream into the other operator set while the guess and
   // GMRES of frequency k run on the caller's stream (compact storage keeps one
   // operator set: frequency k + 1 is assembled after frequency k is solved)
-  const bool pipe = !ctx->far_compact;
   ctx->pre_auto = 0;
+  ctx->far_verify_pending = false;
   cudaEventRecord(ta[0].a, st);
   TRY(assemble_impl(ctx, ctx->eta, 0.0, o, ctx->pattern.p, ctx->Pk_host[0], ctx->b64.p, st));
   cudaEventRecord(ta[0].b, st);
+  // compact storage overlaps too when a second operator set (near blocks,
+  // pools at their current size, leaf inverses) fits in a fifth of the free
+  // device memory (of this context's share of it in a batched sweep)
+  bool pipe = !ctx->far_compact;
+  if (ctx->far_compact) {
+    size_t freeb = 0, totalb = 0;
+    BEM_CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
+    const double esz = is_mixed(ctx) ? 8.0 : 16.0;
+    const double pools = is_mixed(ctx) ? (double)(ctx->u32.n + ctx->v32.n) : (double)(ctx->u64.n + ctx->v64.n);
+    const double set_bytes =
+        esz * ((double)ctx->near_entries + 1.25 * pools + (double)ctx->leaf_pre_entries) + 16.0 * (double)N;
+    pipe = set_bytes <= 0.2 * ctx->mem_share * (double)freeb;
+  }
   BEM_CUDA_TRY(cudaEventRecord(ctx->ev_asm_done, st));
   for (int k = 0; k < nf; ++k) {
     bem_freq_stats s{};
@@ -2041,7 +2096,11 @@ static int sweep_body(bem_ctx* ctx, double T, int n_omega, const double* load_de
       cudaStream_t as = ctx->asm_stream;
       BEM_CUDA_TRY(cudaStreamWaitEvent(as, ctx->ev_asm_done, 0));  // keeps assemblies in order
       cudaEventRecord(ta[(k + 1) & 1].a, as);
-      TRY(assemble_impl(ctx, ctx->eta, (k + 1) * dw, o, ctx->pattern.p, ctx->Pk_host[k + 1], ctx->b64.p, as));
+      ctx->far_defer = ctx->far_compact;
+      const int arc = assemble_impl(ctx, ctx->eta, (k + 1) * dw, o, ctx->pattern.p, ctx->Pk_host[k + 1], ctx->b64.p,
+                                    as);
+      ctx->far_defer = false;
+      TRY(arc);
       cudaEventRecord(ta[(k + 1) & 1].b, as);
       BEM_CUDA_TRY(cudaEventRecord(ctx->ev_asm_done, as));
       swap_ops(ctx);
@@ -2122,6 +2181,7 @@ static int sweep_body(bem_ctx* ctx, double T, int n_omega, const double* load_de
       // frequency k + 1's operator and right-hand side become the set in use
       BEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_asm_done, 0));
       swap_ops(ctx);
+      TRY(far_field_verify(ctx, o));
     } else if (next) {
       cudaEventRecord(ta[(k + 1) & 1].a, st);
       TRY(assemble_impl(ctx, ctx->eta, (k + 1) * dw, o, ctx->pattern.p, ctx->Pk_host[k + 1], ctx->b64.p, st));
@@ -2492,6 +2552,7 @@ extern "C" int bem_solve_sweep_batched(bem_ctx* ctx, double T, int32_t n_omega, 
     TRY(bem_set_window(c, ctx->eta, ctx->window));
   }
   const int nf = n_omega / 2 + 1;
+  for (bem_ctx* c : ctx->batch) c->mem_share = 1.0 / nm;  // the meshes' second operator sets share the memory
   std::vector<int> rc(nm, BEM_OK);
   // a bounded pool of host threads takes the meshes in turn
   const int hw = (int)std::thread::hardware_concurrency();

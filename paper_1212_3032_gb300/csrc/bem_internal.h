@@ -233,6 +233,14 @@ struct bem_ctx {
   std::vector<bem::FarBatch> far_batches;
   long long ws_entries = 0;            // workspace entries per factor (U half, V half)
   int far_regrows = 0;                 // pool regrowths (assemblies re-run after an overflow)
+  // compact storage in a pipelined sweep: the pools' need of the assembly
+  // made on the assembly stream is read (and an overflow redone) only when
+  // its operator set comes into use, so that the host does not wait for it
+  bool far_defer = false;              // set around such an assembly
+  double mem_share = 1.0;              // share of the free device memory a second operator set may take (batch: 1 / meshes)
+  bool far_verify_pending = false;
+  double far_pending_s[2] = {0, 0};    // its s (re, im)
+  cudaEvent_t ev_far_cursor = nullptr;
   bool far_was_ok = false;             // the current assembly started from stored pivots
   bem::DevBuf<bem::c64> ws32;          // 2 x ws_entries
   bem::DevBuf<bem::c128> ws64;

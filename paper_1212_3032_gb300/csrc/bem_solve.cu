@@ -322,6 +322,20 @@ __global__ void __launch_bounds__(256) k_hmv_reduce(const int* __restrict__ leaf
 // adds the leaf's contributions in a fixed order (FP64) and writes y.
 // ---------------------------------------------------------------------------
 constexpr int HF_THREADS = 384;
+// loads in flight per thread: near panels (columns of two rows), U columns,
+// and 16-byte V loads per lane; CTAs per SM of the GMRES product
+#ifndef HF_NEAR_DEPTH
+#define HF_NEAR_DEPTH 8
+#endif
+#ifndef HF_U_DEPTH
+#define HF_U_DEPTH 4
+#endif
+#ifndef HF_V_DEPTH
+#define HF_V_DEPTH 4
+#endif
+#ifndef HF_CTAS
+#define HF_CTAS 3
+#endif
 constexpr int HF_WARPS = HF_THREADS / 32;
 
 __device__ __forceinline__ void ld_pair(const c64* p, c64& a, c64& b) {
@@ -362,12 +376,12 @@ __device__ __forceinline__ void hf_vtx_pair(const Op* __restrict__ base, int len
     const int body = (len - head) >> 1;
     const Op* bp = base + head;
     int c = lane;
-    for (; c + 96 < body; c += 128) {
-      Op v[8];
+    for (; c + 32 * (HF_V_DEPTH - 1) < body; c += 32 * HF_V_DEPTH) {
+      Op v[2 * HF_V_DEPTH];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) ld_pair(bp + 2 * (c + 32 * u), v[2 * u], v[2 * u + 1]);
+      for (int u = 0; u < HF_V_DEPTH; ++u) ld_pair(bp + 2 * (c + 32 * u), v[2 * u], v[2 * u + 1]);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < HF_V_DEPTH; ++u) {
         add(head + 2 * (c + 32 * u), v[2 * u]);
         add(head + 2 * (c + 32 * u) + 1, v[2 * u + 1]);
       }
@@ -447,19 +461,19 @@ __device__ __forceinline__ void hf_item_rows(const HItem& it, int m, const Panel
           const X* xs = x + P.xoff;
           const int nc = P.ncols;
           int j = g;
-          for (; j + 7 * G < nc; j += 8 * G) {
-            Op av[8][E];
+          for (; j + (HF_NEAR_DEPTH - 1) * G < nc; j += HF_NEAR_DEPTH * G) {
+            Op av[HF_NEAR_DEPTH][E];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) ld_rows(d + (long long)(j + u * G) * ld, true, av[u]);
-            X xv[NRHS][8];
-#pragma unroll
-            for (int q = 0; q < NRHS; ++q)
-#pragma unroll
-              for (int u = 0; u < 8; ++u) xv[q][u] = xs[q * N + j + u * G];
+            for (int u = 0; u < HF_NEAR_DEPTH; ++u) ld_rows(d + (long long)(j + u * G) * ld, true, av[u]);
+            X xv[NRHS][HF_NEAR_DEPTH];
 #pragma unroll
             for (int q = 0; q < NRHS; ++q)
 #pragma unroll
-              for (int u = 0; u < 8; ++u)
+              for (int u = 0; u < HF_NEAR_DEPTH; ++u) xv[q][u] = xs[q * N + j + u * G];
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+              for (int u = 0; u < HF_NEAR_DEPTH; ++u)
 #pragma unroll
                 for (int e = 0; e < E; ++e) cmac(acc[e][q], up<Acc>(av[u][e]), up<Acc>(xv[q][u]));
           }
@@ -481,10 +495,10 @@ __device__ __forceinline__ void hf_item_rows(const HItem& it, int m, const Panel
         const int C = fb.cpre[fb.nb];
         int cur = 0;
         int c = g;
-        for (; c + 3 * G < C; c += 4 * G) {
-          Op av[4][E];
+        for (; c + (HF_U_DEPTH - 1) * G < C; c += HF_U_DEPTH * G) {
+          Op av[HF_U_DEPTH][E];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < HF_U_DEPTH; ++u) {
             const int cc = c + u * G;
             while (cc >= fb.cpre[cur + 1]) ++cur;
             ld_rows(U + fb.u[cur] + (long long)(cc - fb.cpre[cur]) * m + row, pair_ok, av[u]);
@@ -492,7 +506,7 @@ __device__ __forceinline__ void hf_item_rows(const HItem& it, int m, const Panel
 #pragma unroll
           for (int q = 0; q < NRHS; ++q)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < HF_U_DEPTH; ++u) {
               const cplx<Acc> tq = ts[q * tsn + c + u * G];
 #pragma unroll
               for (int e = 0; e < E; ++e) cmac(acc[e][q], up<Acc>(av[u][e]), tq);
@@ -543,7 +557,7 @@ __device__ __forceinline__ void hf_item_rows(const HItem& it, int m, const Panel
 }
 
 template <typename Op, typename X, typename Y, typename Acc, int NRHS>
-__global__ void __launch_bounds__(HF_THREADS, (NRHS == 1 && sizeof(Acc) == 4) ? 3 : 2) k_hmv_fused(
+__global__ void __launch_bounds__(HF_THREADS, (NRHS == 1 && sizeof(Acc) == 4) ? HF_CTAS : 2) k_hmv_fused(
     const HItem* __restrict__ items, const int* __restrict__ far_list, const int* __restrict__ leaf_r0,
     const int* __restrict__ leaf_nr, const Panel* __restrict__ panels, const FarBlk* __restrict__ far,
     const int* __restrict__ rank, const long long* __restrict__ fbase, const Op* __restrict__ near,
