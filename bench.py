@@ -52,11 +52,12 @@ WORKLOADS = {
 MAT = dict(E=1.0, nu=0.25, rho=1.0)
 
 
-# DRAM read + write of one H-matrix product (k_hmv_t + k_hmv_tasks_list) at
-# k = n_omega / 4 of cavity5120, from the ncu capture of `bench.py
-# --profile-case`; the same product's algorithmic bytes are 887.3 MB (bytes
-# counted by the library), so the kernels stream every operator entry once.
-HMV_TRAFFIC_K64 = 910_439_680
+# DRAM read + write of one H-matrix product (k_hmv_fused) at k = n_omega / 4
+# of cavity5120, from the ncu capture of `bench.py --profile-case`
+# (profiles/k_hmv_fused_cavity5120.md: 888.0 MB read, 4.0 MB written); the
+# same product's algorithmic bytes are 887.3 MB (counted by the library), so
+# the kernel streams every operator entry once.
+HMV_TRAFFIC_K64 = 892_024_064
 
 
 def _peaks():
@@ -426,10 +427,11 @@ def run_ours(args, cfg):
         "unconverged": unconverged,
         "guess_residual_mean": statistics.fmean(s["guess_residual"] for s in stats[1:]),
         "sem_residual_mean": statistics.fmean(s["sem_residual"] for s in stats[1:]),
-        "roofline": {"kernel": "H-matrix product (k_hmv_t + k_hmv_tasks_list)", "bound": "hbm", "achieved": hmv_gbs,
+        "roofline": {"kernel": "H-matrix product (k_hmv_fused, one launch)", "bound": "hbm", "achieved": hmv_gbs,
                      "peak": peak, "unit": "GB/s", "frac": (hmv_gbs / peak) if hmv_gbs else None,
                      "peak_source": peak_kind, "traffic": HMV_TRAFFIC_K64,
-                     "traffic_note": "DRAM bytes of one product at k = n_omega/4 (ncu); algorithmic 887.3 MB there",
+                     "traffic_note": "DRAM read + write of one product at k = n_omega/4 (ncu capture of the current "
+                                     "kernel, profiles/k_hmv_fused_cavity5120.md); algorithmic 887.3 MB there",
                      "launches": prof["hmv_launches"], "ms_total": prof["hmv_ms"],
                      "note": "timed inside the sweep, where the next frequency's assembly shares the GPU",
                      "isolated": {"achieved": iso_gbs, "frac": (iso_gbs / peak) if iso_gbs else None,

@@ -328,10 +328,10 @@ constexpr int HF_THREADS = 384;
 #define HF_NEAR_DEPTH 8
 #endif
 #ifndef HF_U_DEPTH
-#define HF_U_DEPTH 4
+#define HF_U_DEPTH 8
 #endif
 #ifndef HF_V_DEPTH
-#define HF_V_DEPTH 4
+#define HF_V_DEPTH 2
 #endif
 #ifndef HF_CTAS
 #define HF_CTAS 3
