@@ -54,10 +54,10 @@ MAT = dict(E=1.0, nu=0.25, rho=1.0)
 
 # DRAM read + write of one H-matrix product (k_hmv_fused) at k = n_omega / 4
 # of cavity5120, from the ncu capture of `bench.py --profile-case`
-# (profiles/k_hmv_fused_cavity5120.md: 888.0 MB read, 4.0 MB written); the
+# (profiles/k_hmv_fused_cavity5120.md: 888.1 MB read, 3.8 MB written); the
 # same product's algorithmic bytes are 887.3 MB (counted by the library), so
 # the kernel streams every operator entry once.
-HMV_TRAFFIC_K64 = 892_024_064
+HMV_TRAFFIC_K64 = 891_892_992
 
 
 def _peaks():
@@ -238,7 +238,8 @@ def workload_config(args, cfg):
     return {"workload": args.workload, "triangles": ne, "unknowns": 3 * ne, "n_omega": cfg["n_omega"],
             "solves_per_step": cfg["n_omega"] // 2 + 1, "T": cfg["T"], "eta": cfg["eta"], "window": "hanning",
             "aca_tol": cfg["aca_tol"], "leaf": cfg["leaf"], "gmres_tol": cfg["tol"],
-            "guess": GUESS_LABEL[args.guess], "l2": "flushed (256 MB write) before every timed step"}
+            "guess": GUESS_LABEL[args.guess], "precond": getattr(args, "precond", "block3"),
+            "l2": "flushed (256 MB write) before every timed step"}
 
 
 def run_reference(args, cfg):
@@ -313,8 +314,10 @@ def run_ours(args, cfg):
     nf = n_omega // 2 + 1
     load = inputs.heaviside_history(n_omega)
     guess = {"sem": binding.GUESS_SEM, "mlp": binding.GUESS_MLP, "zero": binding.GUESS_ZERO}[args.guess]
+    precond = {"block3": binding.PRECOND_BLOCK3, "leaf": binding.PRECOND_LEAF,
+               "auto": binding.PRECOND_AUTO}[args.precond]
     opts = binding.default_opts(leaf_size=cfg["leaf"], aca_tol=cfg["aca_tol"], tol=cfg["tol"],
-                                precision=binding.PREC_C64_MIXED, guess=guess, sem_k=4)
+                                precision=binding.PREC_C64_MIXED, guess=guess, sem_k=4, precond=precond)
     if args.profile_case:
         return profile_case(ctx, binding, mesh, cfg, opts)
     # device-resident inputs
@@ -587,6 +590,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--guess", default="sem", choices=["sem", "mlp", "zero"])
+    ap.add_argument("--precond", default="block3", choices=["block3", "leaf", "auto"],
+                    help="GMRES preconditioner: 3x3 element blocks (default), leaf blocks, or chosen by the sweep")
     ap.add_argument("--no-aca-reuse", action="store_true",
                     help="assemble every frequency with a fresh ACA (no reuse of the previous pivots)")
     ap.add_argument("--profile-case", action="store_true",
