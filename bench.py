@@ -530,7 +530,7 @@ def run_batched(args):
 def run_large(args):
     """The 231,088-triangle cube with 8 spherical cavities (693,264 unknowns):
     bottom face fixed, top face under a step traction, the rest free; E = 1,
-    nu = 0.3, rho = 1; 128 samples (65 solves), T = 8, eta = 5/T; complex64
+    nu = 0.3, rho = 1; 128 samples (65 solves), T = 8 (--large-T), eta = 5/T; complex64
     operator with ACA tolerance 1e-4, compact far-field storage, leaf-block
     preconditioner, extrapolated guesses, GMRES 1e-5. One sweep, timed with
     CUDA events on the library's stream; device memory in use sampled after
@@ -543,7 +543,7 @@ def run_large(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     mesh = inputs.cube_with_cavities()
-    T, n_omega = 8.0, 128
+    T, n_omega = float(args.large_T), 128
     eta = 5.0 / T
     nf = n_omega // 2 + 1
     stream = torch.cuda.current_stream(dev)
@@ -600,6 +600,7 @@ def main():
                     help="the 16-mesh batched sweep against the same meshes one after another (separate line)")
     ap.add_argument("--large", action="store_true",
                     help="one sweep of the 231,088-triangle cube with cavities (separate line)")
+    ap.add_argument("--large-T", type=float, default=8.0, help="time window of the --large sweep")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
     if args.large:

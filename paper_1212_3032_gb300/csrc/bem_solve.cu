@@ -3,13 +3,19 @@
 // Fourier transforms (Sec. 3.3, Eqs. DFT-MFT and IDFT-MFT).
 //
 // H-matrix product (HBM-bound): y = D_near x + sum_b U_b (V_b^T x)
-//   k_hmv_t     t_b = V_b^T x for every admissible block (one CTA per block,
-//               one warp per factor column, coalesced column reads)
-//   k_hmv_tasks one CTA per task (a run of panels of one leaf row: dense near
-//               blocks and slices of the U_b factors), every stored entry
-//               read once, coalesced across rows (column-major storage),
-//               partial row sums to a per-task slot; no atomics
-//   k_hmv_reduce per leaf row, the task slots summed in a fixed order
+//   k_hmv_fused  the product of the solver: one launch, one CTA per work item
+//                (near panels of a leaf row, or the admissible blocks of one
+//                row cluster), 16-byte loads, per-item partial rows summed in
+//                a fixed order by the item that completes a leaf
+//   k_hmv_t, k_hmv_tasks, k_hmv_reduce  the same product in three launches
+//                with caller-provided scratch (bem_apply_noalloc):
+//     k_hmv_t     t_b = V_b^T x for every admissible block (one CTA per block,
+//                 one warp per factor column, coalesced column reads)
+//     k_hmv_tasks one CTA per task (a run of panels of one leaf row: dense near
+//                 blocks and slices of the U_b factors), every stored entry
+//                 read once, coalesced across rows (column-major storage),
+//                 partial row sums to a per-task slot; no atomics
+//     k_hmv_reduce per leaf row, the task slots summed in a fixed order
 #include <algorithm>
 
 #include <cooperative_groups.h>
@@ -232,52 +238,6 @@ __global__ void __launch_bounds__(HMV_THREADS, 2) k_hmv_tasks(
   cplx<Acc>* red = reinterpret_cast<cplx<Acc>*>(smem_raw);
   hmv_task<Op, X, Acc, NRHS>(tasks[blockIdx.x], leaf_nr, panels, far, rank, fbase, near, U, t, tstride, x, N, part,
                              pstride, red);
-}
-
-// The same task kernel over a list of task indices (the launch order), with
-// the per-leaf reduction fused in: the CTA that completes the last task of a
-// leaf (a per-leaf arrival counter) adds the leaf's task partials in task
-// order (FP64) and writes y; it then resets the counter for the next product.
-// Three CTAs per SM for the complex64 single-right-hand-side product (the
-// GMRES product: measured 197 us against 216 us with two), two otherwise.
-template <typename Op, typename X, typename Y, typename Acc, int NRHS>
-__global__ void __launch_bounds__(HMV_THREADS, (NRHS == 1 && sizeof(Acc) == 4) ? 3 : 2) k_hmv_tasks_list(
-    const int* __restrict__ list, const Task* __restrict__ tasks, const int* __restrict__ leaf_nr,
-    const Panel* __restrict__ panels, const FarBlk* __restrict__ far, const int* __restrict__ rank,
-    const long long* __restrict__ fbase, const Op* __restrict__ near, const Op* __restrict__ U,
-    const cplx<Acc>* __restrict__ t, int tstride, const X* __restrict__ x, long long N,
-    cplx<Acc>* __restrict__ part, long long pstride, const int* __restrict__ leaf_r0, const int* __restrict__ task_ptr, int* __restrict__ leaf_cnt,
-    Y* __restrict__ y) {
-  extern __shared__ unsigned char smem_raw[];
-  cplx<Acc>* red = reinterpret_cast<cplx<Acc>*>(smem_raw);
-  __shared__ int last;
-  const Task tk = tasks[list[blockIdx.x]];
-  hmv_task<Op, X, Acc, NRHS>(tk, leaf_nr, panels, far, rank, fbase, near, U, t, tstride, x, N, part, pstride, red);
-  __threadfence();  // this task's partials are visible before its arrival is counted
-  __syncthreads();
-  const int t0 = task_ptr[tk.leaf], t1 = task_ptr[tk.leaf + 1];
-  if (threadIdx.x == 0) last = atomicAdd(&leaf_cnt[tk.leaf], 1) == t1 - t0 - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  const int rows = 3 * leaf_nr[tk.leaf];
-  const long long row0 = 3LL * leaf_r0[tk.leaf];
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < NRHS; ++q) {
-      cplx<double> sum{0, 0};
-      for (int k = t0; k < t1; ++k) {
-        const cplx<Acc> v = ld_global_cg(part + q * pstride + tasks[k].slot + r);
-        sum.re += v.re;
-        sum.im += v.im;
-      }
-      Y o;
-      o.re = decltype(o.re)(sum.re);
-      o.im = decltype(o.im)(sum.im);
-      y[q * N + row0 + r] = o;
-    }
-  }
-  if (threadIdx.x == 0) leaf_cnt[tk.leaf] = 0;
 }
 
 // phase 3: y[rows of leaf] = sum over the leaf's tasks, in task order

@@ -205,10 +205,21 @@ def test_rod_mixed_bc_full_size(B):
         etime = np.max(np.abs(u_t - u_t_ref)) / np.max(np.abs(u_t_ref))
         print(f"rod {rod.ne}: {conv.sum()} of {conv.size} converged, {sum(s['iters'] for s in stats)} iterations; "
               f"spectrum error free-end u {eu:.2e}, fixed-end t {et:.2e}; time trace {etime:.2e}")
+        # strain history at the rod's mid-point (the paper's Sec. 5.2 reports strain at a point): the
+        # representation formula's central differences against the exact 1-D strain
+        # eps_xx(x, s) = -(p / E) cosh(s x / c) / cosh(s L / c), through the same windowed transform
+        xm = np.array([[1.5, 0.0, 0.0]])
+        eps_t = c.interior_time_response(xm, B.FIELD_STRAIN, 0.02)[:, 0, 0]
+        c_bar = math.sqrt(mat.E / mat.rho)
+        eps_ref = -(1.0 / mat.E) * np.cosh(sk * 1.5 / c_bar) / np.cosh(sk * L / c_bar) * Pk
+        eps_t_ref = tr.idft_mft(eps_ref, T, eta, tr.WIN_HANNING, N)
+        estrain = np.max(np.abs(eps_t - eps_t_ref)) / np.max(np.abs(eps_t_ref))
+        print(f"rod mid-point strain history error {estrain:.2e}")
         assert conv.all()
         assert all(s["precond"] == B.PRECOND_LEAF for s in stats)
         assert eu <= 0.02 and et <= 0.05
         assert etime <= 0.05
+        assert estrain <= 0.05
     finally:
         c.close()
 
