@@ -562,6 +562,29 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   ctx->bc_host.resize(ne);
   BEM_CUDA_TRY(cudaMemcpyAsync(ctx->bc_host.data(), ctx->bc.p, ne, cudaMemcpyDeviceToHost, st));
 
+  // element normals (tree order), for the flat-face test of the far blocks
+  std::vector<ElemD> ed_h(ne);
+  BEM_CUDA_TRY(cudaMemcpyAsync(ed_h.data(), ctx->ed.p, (size_t)ne * sizeof(ElemD), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  // a cluster [b0, b0 + nb) is faceted when at least half of its elements
+  // share their normal with its first, middle or last element (flat faces of
+  // boxes and cubes; on a curved surface every element has its own normal)
+  auto faceted = [&](int b0, int nb) {
+    const int ref[3] = {b0, b0 + nb / 2, b0 + nb - 1};
+    int same = 0;
+    for (int e = b0; e < b0 + nb; ++e) {
+      const ElemD& E = ed_h[e];
+      for (int q = 0; q < 3; ++q) {
+        const ElemD& R = ed_h[ref[q]];
+        if (E.n[0] * R.n[0] + E.n[1] * R.n[1] + E.n[2] * R.n[2] > 1.0 - 1e-9) {
+          ++same;
+          break;
+        }
+      }
+    }
+    return 2 * same >= nb && nb > 3;
+  };
+
   // near / far block descriptors
   ctx->near_h.clear();
   ctx->far_h.clear();
@@ -596,6 +619,7 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
     int mn = 3 * std::min(fb.nr, fb.nc);
     fb.rmax = std::min(mn, ACA_RANK_CAP);
     fb.toff = toff;
+    fb.flat = faceted(fb.r0, fb.nr) || faceted(fb.c0, fb.nc) ? 1 : 0;
     ucap += 3LL * fb.nr * fb.rmax;
     vcap += 3LL * fb.nc * fb.rmax;
     uinit += 3LL * fb.nr * std::min(fb.rmax, POOL_INIT_RANK);

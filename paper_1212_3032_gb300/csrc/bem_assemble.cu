@@ -1843,10 +1843,12 @@ __global__ void __launch_bounds__(NT) k_aca_warm_solve(const FarBlk* __restrict_
     const int conv = lastfail + 1 < ls ? 1 : 0;
     const int kc = conv ? lastfail + 2 : ls;
     // converged: every validated step stays (the ones past the rank as
-    // spares) and the ACA kernels evaluate the check rows against all of them
+    // spares); on a block with flat faces, where partial pivoting can miss
+    // the part of the block it has not visited, the ACA kernels evaluate the
+    // check rows against all of them first
     kstart[bi] = ls;
     norm0[bi] = double(S);
-    done[bi] = conv ? 2 : 0;
+    done[bi] = conv ? (B.flat ? 2 : 1) : 0;
     if (conv) {
       rank[bi] = kc;
       npiv[bi] = ls;

@@ -57,6 +57,7 @@ struct FarBlk {
   int r0, nr, c0, nc;
   int rmax;
   int toff;  // offset of this block's t = V^T x in the t buffer
+  int flat;  // one of its clusters is faceted (flat faces: most elements share a few normals)
 };
 
 // One column panel of a leaf row of the matrix-vector product:
