@@ -288,14 +288,14 @@ class CoopLane {
   cudaError_t e_ = cudaSuccess;
 };
 
-// Exchanges the operator set in use with the other one (host pointers only:
-// work already enqueued keeps the buffers it was given).
+// Exchanges the operator set in use with the set back[i] (host pointers
+// only: work already enqueued keeps the buffers it was given).
 template <typename T> void swap_buf(DevBuf<T>& a, DevBuf<T>& b) {
   std::swap(a.p, b.p);
   std::swap(a.n, b.n);
 }
-void swap_ops(bem_ctx* ctx) {
-  OpSet& o = ctx->back;
+void swap_ops(bem_ctx* ctx, int i) {
+  OpSet& o = ctx->back[i];
   swap_buf(ctx->near32, o.near32);
   swap_buf(ctx->u32, o.u32);
   swap_buf(ctx->v32, o.v32);
@@ -417,6 +417,13 @@ extern "C" int bem_create(bem_ctx** out, int device, void* stream) {
     delete ctx;
     return BEM_ERR_OOM;
   }
+  // the solver state's host copy: mapped, written by the solver kernels
+  if (cudaHostAlloc(&ctx->gm_mirror, sizeof(GmCtl), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(&ctx->gm_mirror_dev, ctx->gm_mirror, 0) != cudaSuccess) {
+    bem_destroy(ctx);
+    return BEM_ERR_OOM;
+  }
+  std::memset(ctx->gm_mirror, 0, sizeof(GmCtl));
   int prio_least = 0, prio_greatest = 0;
   if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) prio_least = prio_greatest = 0;
   if (cudaStreamCreateWithPriority(&ctx->aux_stream, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
@@ -427,7 +434,12 @@ extern "C" int bem_create(bem_ctx** out, int device, void* stream) {
       cudaEventCreateWithFlags(&ctx->ev_far_cursor, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_asm_done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&ctx->ev_asm_ring[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_asm_ring[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_asm_ring[2], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_free_ring[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_free_ring[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_free_ring[2], cudaEventDisableTiming) != cudaSuccess) {
     bem_destroy(ctx);
     return BEM_ERR_CUDA;
   }
@@ -459,7 +471,10 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
   if (ctx->ev_far_cursor) cudaEventDestroy(ctx->ev_far_cursor);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
-  if (ctx->ev_asm_done) cudaEventDestroy(ctx->ev_asm_done);
+  for (int r = 0; r < 3; ++r) {
+    if (ctx->ev_asm_ring[r]) cudaEventDestroy(ctx->ev_asm_ring[r]);
+    if (ctx->ev_free_ring[r]) cudaEventDestroy(ctx->ev_free_ring[r]);
+  }
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -477,6 +492,8 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
     cudaStreamDestroy(ctx->batch_coop);
   }
   mlp_free(ctx);
+  if (ctx->gm_mirror) cudaFreeHost(ctx->gm_mirror);
+  if (ctx->sweep_pin) cudaFreeHost(ctx->sweep_pin);  // the streams writing it are synchronised above
   delete ctx;
 }
 
@@ -605,7 +622,7 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
   }
   ctx->near_entries = noff;
   ctx->near_zero_pending = true;
-  ctx->back.near_zero_pending = true;  // the other operator set's padding rows too
+  for (OpSet& b : ctx->back) b.near_zero_pending = true;  // the other operator sets' padding rows too
   long long ucap = 0, vcap = 0, bigcap = 0, uinit = 0, vinit = 0;
   int toff = 0;
   for (const BlockPair& bp : tr.far) {
@@ -673,16 +690,18 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
       cur.l1 = nl;
       ctx->far_batches.push_back(cur);
     }
-    // a new mesh invalidates both sets' factor offsets; the set not in use
-    // gives back its operator storage (it is reallocated when next used)
+    // a new mesh invalidates every set's factor offsets; the sets not in use
+    // give back their operator storage (it is reallocated when next used)
     ctx->fbase_ready = false;
-    ctx->back.fbase_ready = false;
-    ctx->back.near32.release();
-    ctx->back.u32.release();
-    ctx->back.v32.release();
-    ctx->back.near64.release();
-    ctx->back.u64.release();
-    ctx->back.v64.release();
+    for (OpSet& b : ctx->back) {
+      b.fbase_ready = false;
+      b.near32.release();
+      b.u32.release();
+      b.v32.release();
+      b.near64.release();
+      b.u64.release();
+      b.v64.release();
+    }
     if (ctx->far_compact) {
       // pools are sized by the first assembly's need
       ctx->u32.release();
@@ -928,7 +947,7 @@ static int mesh_impl(bem_ctx* ctx, const double* xyz_d, long long nv, const int*
     ctx->nleaf_pre = ok ? L : 0;
     ctx->leaf_pre_entries = ok ? oo : 0;
     ctx->minv_ready = false;
-    ctx->back.minv_ready = false;
+    for (OpSet& b : ctx->back) b.minv_ready = false;
     if (ok) {
       BEM_CUDA_TRY(ctx->leaf_pre.alloc(L));
       BEM_CUDA_TRY(cudaMemcpyAsync(ctx->leaf_pre.p, lp.data(), L * sizeof(LeafPre), cudaMemcpyHostToDevice, st));
@@ -1508,217 +1527,219 @@ int ensure_host_cols(bem_ctx* ctx, long long ncomplex, int nev) {
 }
 
 // ---------------------------------------------------------------------------
-// GMRES (Sec. 5): right block-Jacobi preconditioning; each restart cycle
-// starts from the true residual r = b - A x accumulated in FP64 (x in FP64),
-// so restarts double as iterative refinement of the c64 Krylov solve.
+// GMRES (Sec. 5): right preconditioning (3 x 3 or leaf blocks); each restart
+// cycle starts from the true residual r = b - A x accumulated in FP64 (x in
+// FP64), so restarts double as iterative refinement of the c64 Krylov solve.
+//
+// The solve is driven by the device (GmCtl): the host enqueues
+//   init    ||b|| and the counters;
+//   test    r = b - A x and ||r||: the solve ends (tolerance met, or the step
+//           limit reached) or a cycle starts from V_0 = r / ||r||;
+//   step j  z = M^-1 V_j, w = A z, the orthogonalisation (V_{j+1}, column j
+//           of H) and the step's Givens rotation and residual estimate, which
+//           end the cycle at the inner target, after m steps, on breakdown or
+//           at the step limit;
+//   update  x += M^-1 V R^-1 g, when a cycle has ended;
+// and waits on none of them. Step kernels do nothing outside a cycle, so the
+// host enqueues steps before it knows whether the cycle still runs: it reads
+// the state's mapped host copy GM_LAG steps behind the newest step it has
+// enqueued (the GPU has that many steps queued meanwhile), stops enqueueing
+// steps once the cycle has ended, then enqueues the update and the next test.
+// The steps enqueued past the end of a cycle or of the solve return at once.
 // ---------------------------------------------------------------------------
+constexpr int GM_LAG = 2;
+
 template <typename Vb, typename Pm, typename Acc>
-int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq_stats* stats, double bnorm) {
+int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq_stats* stats) {
   cudaStream_t st = ctx->stream;
   const long long N = ctx->N;
   const int m = std::max(1, o.restart);
+  if (m + 1 > 512) return fail(ctx, BEM_ERR_INVALID_ARG, "restart length above 511");
   constexpr bool mixed = sizeof(Vb) == sizeof(c64);
   DevBuf<Vb>& Vbuf = basis_buf<Vb>(ctx);
   BEM_CUDA_TRY(Vbuf.ensure((m + 1) * N));
-  DevBuf<Vb> wbuf, zbuf;
-  BEM_CUDA_TRY(wbuf.alloc(N));
-  BEM_CUDA_TRY(zbuf.alloc(N));
+  Vb* V = Vbuf.p;
+  Vb *wv, *zv;
+  if constexpr (mixed) {
+    BEM_CUDA_TRY(ctx->gm_w32.ensure(N));
+    BEM_CUDA_TRY(ctx->gm_z32.ensure(N));
+    wv = reinterpret_cast<Vb*>(ctx->gm_w32.p);
+    zv = reinterpret_cast<Vb*>(ctx->gm_z32.p);
+  } else {
+    BEM_CUDA_TRY(ctx->gm_w64.ensure(N));
+    BEM_CUDA_TRY(ctx->gm_z64.ensure(N));
+    wv = reinterpret_cast<Vb*>(ctx->gm_w64.p);
+    zv = reinterpret_cast<Vb*>(ctx->gm_z64.p);
+  }
   BEM_CUDA_TRY(ctx->r64.ensure(N));
   BEM_CUDA_TRY(ctx->y64.ensure(N));
   BEM_CUDA_TRY(ctx->tmp64.ensure(2 * N));
-  // Hessenberg columns: one slot per Arnoldi step [h1 (m+1) | h2 (m+1) | nrm2]
+  // reduction scratch: [dot partials (64) | Hessenberg column slots | ||b||^2, ||r||^2]
   const long long slot_len = 2LL * (m + 1) + 1;
-  BEM_CUDA_TRY(ctx->red.ensure(2LL * 64 * (m + 2) * 2 + 2 * slot_len * (m + 1) + 8));
+  BEM_CUDA_TRY(ctx->red.ensure(2 * (64 + slot_len * (m + 1) + 2)));
   c128* part = reinterpret_cast<c128*>(ctx->red.p);
-  c128* hdev = part + 64LL * (m + 2);
-  if (m + 1 > 512) return fail(ctx, BEM_ERR_INVALID_ARG, "restart length above 511");
-  // partial sums of the cooperative orthogonalisation step
+  c128* hdev = part + 64;
+  c128* bb_dev = hdev + slot_len * (m + 1);
+  c128* rr_dev = bb_dev + 1;
   BEM_CUDA_TRY(ctx->orth_part.ensure((size_t)(2 * (m + 1) + 2) * arnoldi_orth_max_blocks()));
-  c128* orth_part = ctx->orth_part.p;
-  TRY(ensure_host_cols(ctx, slot_len * (m + 1), m + 1));
-  double* hcol = ctx->host_cols;
+  BEM_CUDA_TRY(ctx->gm_ctl.ensure(1));
+  BEM_CUDA_TRY(ctx->gm_work.ensure((size_t)(m + 1) * m + 3 * (size_t)m + 1));
+  TRY(ensure_host_cols(ctx, 1, m + 1));
+  GmDev d{};
+  d.ctl = ctx->gm_ctl.p;
+  d.mirror = ctx->gm_mirror_dev;
+  d.R = ctx->gm_work.p;
+  d.g = d.R + (long long)(m + 1) * m;
+  d.cs = d.g + (m + 1);
+  d.sn = d.cs + m;
+  d.hcol = hdev;
+  d.slot_len = slot_len;
+  d.m = m;
+  d.max_iters = o.max_iters;
+  d.tol = o.tol;
+  d.floor = mixed ? 2e-6 : 1e-13;
+  const int* act = &d.ctl->active;
+  const int* jcur = &d.ctl->j;
+  const int* upd = &d.ctl->update;
   const Pm* pinv = basis_pinv<Pm>(ctx);
   const bool leaf = ctx->use_leaf_pre && ctx->minv_ready;
-  Vb* V = Vbuf.p;
-  int its = 0, cycles = 0;
-  double rel = 1.0;
-  bool converged = false;
-  const double inner_floor = mixed ? 2e-6 : 1e-13;
-  std::vector<std::complex<double>> H((m + 1) * m), cs(m), sn(m), g(m + 1);
-  double* hh = ctx->host_red;
-  // one Arnoldi step j: V_{j+1} and column j of H (copied to host slot j, event j)
-  auto enqueue = [&](int j) -> int {
-    Vb* vj = V + (long long)j * N;
-    c128* hd = hdev + j * slot_len;
-    if (leaf) {
-      if constexpr (mixed)
-        launch_leaf_apply<c64, c64, c64>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv32.p,
-                                         reinterpret_cast<const c64*>(vj), reinterpret_cast<c64*>(zbuf.p), st);
-      else
-        launch_leaf_apply<c128, c128, c128>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv64.p,
-                                            reinterpret_cast<const c128*>(vj), reinterpret_cast<c128*>(zbuf.p), st);
-    } else {
-      launch_precond<Pm, Vb, Vb>(pinv, vj, zbuf.p, ctx->ne, st);
-    }
-    cudaEvent_t ev = prof_begin(ctx);
-    if (mixed)
-      launch_hmatvec<c64, c64, c64, float>(ctx, ctx->near32.p, ctx->u32.p, ctx->v32.p,
-                                           reinterpret_cast<cplx<float>*>(ctx->t32.p),
-                                           reinterpret_cast<const c64*>(zbuf.p), reinterpret_cast<c64*>(wbuf.p), 1,
-                                           st);
-    else
-      launch_hmatvec<c128, c128, c128, double>(ctx, ctx->near64.p, ctx->u64.p, ctx->v64.p,
-                                               reinterpret_cast<cplx<double>*>(ctx->t64.p),
-                                               reinterpret_cast<const c128*>(zbuf.p),
-                                               reinterpret_cast<c128*>(wbuf.p), 1, st);
-    CK("arnoldi matvec");
-    prof_end_hmv(ctx, ev, sizeof(Vb), sizeof(Vb), sizeof(Vb), 1);
-    {
-      CoopLane lane(ctx, st);
-      BEM_CUDA_TRY(lane.status());
-      BEM_CUDA_TRY(launch_arnoldi_orth<Vb>(V, N, j, wbuf.p, N, orth_part, hd, m, lane.stream()));
-      BEM_CUDA_TRY(lane.join());
-    }
-    CK("arnoldi");
-    BEM_CUDA_TRY(cudaMemcpyAsync(hcol + 2 * j * slot_len, hd, slot_len * sizeof(c128), cudaMemcpyDeviceToHost, st));
-    BEM_CUDA_TRY(cudaEventRecord(ctx->col_events[j], st));
-    return BEM_OK;
-  };
   // true residuals: FP64 sums of FP32 products (tolerances >= 1e-6) or of
   // FP64 products. With FP32 products the residual carries an error of about
   // 1e-7 sqrt(columns per task) |A| |x| (~1.5e-6 |A||x| here), an order below
   // the tolerances it decides; FP64 products are bound by GB300's FP64 pipe
   // (1/64 of the FP32 rate), not by the bandwidth the FP32 product reaches.
   const bool exact = !(mixed && o.tol >= 1e-6);
-  while (true) {
+  // timed products of the steps, kept until the cycles' step counts are known
+  struct StepProf {
+    cudaEvent_t a, b;
+    int cycle, j;
+  };
+  std::vector<StepProf> sprof;
+  int cyc = 0;  // cycles the host has enqueued steps for
+
+  auto step = [&](int q) -> int {
+    if (leaf) {
+      if constexpr (mixed)
+        launch_leaf_apply<c64, c64, c64>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv32.p,
+                                         reinterpret_cast<const c64*>(V), reinterpret_cast<c64*>(zv), st, act,
+                                         jcur, N);
+      else
+        launch_leaf_apply<c128, c128, c128>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv64.p,
+                                            reinterpret_cast<const c128*>(V), reinterpret_cast<c128*>(zv), st,
+                                            act, jcur, N);
+    } else {
+      launch_precond<Pm, Vb, Vb>(pinv, V, zv, ctx->ne, st, act, jcur, N);
+    }
+    cudaEvent_t ev = prof_begin(ctx);
+    if constexpr (mixed)
+      launch_hmatvec<c64, c64, c64, float>(ctx, ctx->near32.p, ctx->u32.p, ctx->v32.p,
+                                           reinterpret_cast<cplx<float>*>(ctx->t32.p),
+                                           reinterpret_cast<const c64*>(zv), reinterpret_cast<c64*>(wv), 1, st,
+                                           act);
+    else
+      launch_hmatvec<c128, c128, c128, double>(ctx, ctx->near64.p, ctx->u64.p, ctx->v64.p,
+                                               reinterpret_cast<cplx<double>*>(ctx->t64.p),
+                                               reinterpret_cast<const c128*>(zv), reinterpret_cast<c128*>(wv), 1,
+                                               st, act);
+    CK("arnoldi matvec");
+    if (ev) {
+      cudaEvent_t e2 = take_event(ctx);
+      cudaEventRecord(e2, st);
+      sprof.push_back({ev, e2, cyc, q});
+    }
+    {
+      CoopLane lane(ctx, st);
+      BEM_CUDA_TRY(lane.status());
+      BEM_CUDA_TRY(launch_arnoldi_orth<Vb>(V, N, 0, wv, N, ctx->orth_part.p, hdev, m, lane.stream(), &d));
+      BEM_CUDA_TRY(lane.join());
+    }
+    CK("arnoldi");
+    BEM_CUDA_TRY(cudaEventRecord(ctx->col_events[q], st));
+    return BEM_OK;
+  };
+  auto test = [&]() -> int {
     if (exact) TRY(apply64(ctx, x, ctx->y64.p, 1));
     else TRY(apply_fast(ctx, x, ctx->y64.p, 1));
     launch_residual(b, ctx->y64.p, ctx->r64.p, N, st);
-    CK("residual");
-    std::complex<double> rr;
-    TRY(dot_host(ctx, ctx->r64.p, ctx->r64.p, N, rr));
-    double rnorm = std::sqrt(std::max(0.0, rr.real()));
-    rel = bnorm > 0 ? rnorm / bnorm : 0.0;
-    if (cycles == 0 && stats) stats->guess_residual = rel;
-    if (rel <= o.tol || rnorm == 0.0) {
-      converged = true;
-      break;
-    }
-    if (its >= o.max_iters) break;
-    // V_0 = r / ||r||
-    if (mixed)
-      launch_copy_cast(ctx->r64.p, reinterpret_cast<c64*>(V), N, 1.0 / rnorm, st);
-    else
-      launch_copy_cast(ctx->r64.p, reinterpret_cast<c128*>(V), N, 1.0 / rnorm, st);
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = rnorm;
-    // inner target: with right preconditioning the Arnoldi estimate |g_{j+1}|
-    // is the true residual up to rounding of the products; a 10% margin keeps
-    // the restarts forced by that rounding rare (measured: 0.5 costs about 13%
-    // more Arnoldi steps on the 5,120-triangle sweep than 0.9)
-    double target = std::max(0.9 * o.tol * bnorm, inner_floor * rnorm);
-    int jdone = 0;
-    // Arnoldi steps are enqueued one ahead of the host's Givens rotations
-    // (the Krylov basis does not depend on them), except where the residual
-    // trend predicts convergence at the step in flight; a step enqueued past
-    // convergence is discarded.
-    TRY(enqueue(0));
-    int enq = 1;
-    double gprev = rnorm, gcur = rnorm;
-    for (int j = 0; j < m; ++j) {
-      if (enq == j + 1 && j + 1 < m && its + 1 < o.max_iters) {
-        double rho = (j >= 1 && gprev > 0) ? gcur / gprev : 1.0;
-        if (gcur * rho > target) {
-          TRY(enqueue(j + 1));
-          ++enq;
-        }
-      }
-      BEM_CUDA_TRY(cudaEventSynchronize(ctx->col_events[j]));
-      prof_harvest(ctx);
-      const double* hj = hcol + 2 * j * slot_len;
-      for (int i = 0; i <= j; ++i)
-        H[i * m + j] = std::complex<double>(hj[2 * i] + hj[2 * (m + 1 + i)], hj[2 * i + 1] + hj[2 * (m + 1 + i) + 1]);
-      double hn = std::sqrt(std::max(0.0, hj[4 * (m + 1)]));
-      H[(j + 1) * m + j] = hn;
-      // Givens (G = [[conj c, conj s], [-s, c]])
-      for (int i = 0; i < j; ++i) {
-        std::complex<double> a = H[i * m + j], c2 = H[(i + 1) * m + j];
-        H[i * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * c2;
-        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c2;
-      }
-      std::complex<double> a = H[j * m + j], c2 = H[(j + 1) * m + j];
-      double den = std::sqrt(std::norm(a) + std::norm(c2));
-      cs[j] = den > 0 ? a / den : 1.0;
-      sn[j] = den > 0 ? c2 / den : 0.0;
-      H[j * m + j] = den;
-      H[(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = std::conj(cs[j]) * g[j];
-      ++its;
-      jdone = j + 1;
-      gprev = gcur;
-      gcur = std::abs(g[j + 1]);
-      if (gcur <= target || its >= o.max_iters || hn == 0.0) break;
-      if (enq == j + 1 && j + 1 < m) {
-        TRY(enqueue(j + 1));
-        ++enq;
-      }
-    }
-    // y = H^{-1} g ; x += M^{-1} V y
-    std::vector<std::complex<double>> y(jdone);
-    for (int i = jdone - 1; i >= 0; --i) {
-      std::complex<double> s = g[i];
-      for (int k2 = i + 1; k2 < jdone; ++k2) s -= H[i * m + k2] * y[k2];
-      y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
-    }
-    for (int i = 0; i < jdone; ++i) {
-      hh[2 * i] = y[i].real();
-      hh[2 * i + 1] = y[i].imag();
-    }
-    BEM_CUDA_TRY(cudaMemcpyAsync(hdev, hh, jdone * sizeof(c128), cudaMemcpyHostToDevice, st));
-    launch_combine<Vb>(V, N, jdone, hdev, ctx->tmp64.p, N, st);
+    const int nblk = launch_dots<c128, c128>(ctx->r64.p, N, 1, ctx->r64.p, N, part, st);
+    launch_dots_final(part, nblk, 1, rr_dev, st);
+    launch_gm_begin<Vb>(d, rr_dev, ctx->r64.p, V, x, N, st);
+    CK("residual test");
+    return BEM_OK;
+  };
+  auto update = [&]() -> int {
+    launch_gm_combine<Vb>(V, N, d, ctx->tmp64.p, N, st);
     if (leaf && mixed)
       launch_leaf_apply<c64, c128, c128>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv32.p, ctx->tmp64.p,
-                                         ctx->tmp64.p + N, st);
+                                         ctx->tmp64.p + N, st, upd);
     else if (leaf)
       launch_leaf_apply<c128, c128, c128>(ctx->leaf_pre.p, ctx->nleaf_pre, ctx->minv64.p, ctx->tmp64.p,
-                                          ctx->tmp64.p + N, st);
+                                          ctx->tmp64.p + N, st, upd);
     else
-      launch_precond<c128, c128, c128>(ctx->prec_inv.p, ctx->tmp64.p, ctx->tmp64.p + N, ctx->ne, st);
-    launch_axpy(c128{1.0, 0.0}, ctx->tmp64.p + N, x, N, st);
+      launch_precond<c128, c128, c128>(ctx->prec_inv.p, ctx->tmp64.p, ctx->tmp64.p + N, ctx->ne, st, upd);
+    launch_axpy(c128{1.0, 0.0}, ctx->tmp64.p + N, x, N, st, upd);
     CK("update x");
-    BEM_CUDA_TRY(cudaStreamSynchronize(st));  // hh reused next cycle
-    prof_harvest(ctx);
-    ++cycles;
+    return BEM_OK;
+  };
+
+  const int nblk = launch_dots<c128, c128>(b, N, 1, b, N, part, st);
+  launch_dots_final(part, nblk, 1, bb_dev, st);
+  launch_gm_init(d, bb_dev, st);
+  CK("solver state");
+  TRY(test());
+  const volatile GmCtl* hm = ctx->gm_mirror;
+  for (;;) {
+    // the next cycle's steps (they return at once if the test ended the solve)
+    bool finished = false, ended = false;
+    int q = 0;
+    while (q < m && !ended) {
+      TRY(step(q));
+      ++q;
+      const int chk = q - 1 - GM_LAG;  // the newest step GM_LAG behind
+      if (chk < 0 && q < m) continue;
+      BEM_CUDA_TRY(cudaEventSynchronize(ctx->col_events[std::max(chk, 0)]));
+      prof_harvest(ctx);
+      if (!hm->live) {
+        finished = true;
+        break;
+      }
+      if (!hm->active) ended = true;
+    }
+    if (finished) break;
+    // the cycle has ended, or all its m steps are enqueued (the last one ends it)
+    TRY(update());
+    TRY(test());
+    ++cyc;
+    // every cycle the device starts takes at least one step, so the step
+    // limit bounds the cycles; more would mean the state does not advance
+    if (cyc > o.max_iters + 1) return fail(ctx, BEM_ERR_STATE, "GMRES state did not advance on the device");
+  }
+  const int its = hm->its, cycles = hm->cycles, converged = hm->converged;
+  // the products of steps that ran (the cycle's step count is on the host copy)
+  for (const StepProf& p : sprof) {
+    const bool ran = p.cycle < cycles && p.cycle < GM_MAX_CYCLES && p.j < hm->jdone[p.cycle];
+    if (ran) {
+      ctx->pending.push_back({p.a, p.b, (double)sizeof(Vb) * ctx->near_entries + (double)N * 2 * sizeof(Vb),
+                              (double)sizeof(Vb), ctx->prof_slot, 0});
+    } else {
+      ctx->event_pool.push_back(p.a);
+      ctx->event_pool.push_back(p.b);
+    }
   }
   if (stats) {
     stats->iters = its;
     stats->cycles = cycles;
-    stats->rel_residual = rel;
-    stats->converged = converged ? 1 : 0;
+    stats->rel_residual = hm->rel;
+    stats->guess_residual = hm->guess_rel;
+    stats->converged = converged;
     stats->precond = leaf ? BEM_PRECOND_LEAF : BEM_PRECOND_BLOCK3;
   }
   return converged ? BEM_OK : BEM_ERR_NOT_CONVERGED;
 }
 
 int gmres(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq_stats* st) {
-  std::complex<double> bb;
-  TRY(dot_host(ctx, b, b, ctx->N, bb));
-  double bnorm = std::sqrt(std::max(0.0, bb.real()));
-  if (bnorm == 0.0) {
-    BEM_CUDA_TRY(cudaMemsetAsync(x, 0, ctx->N * sizeof(c128), ctx->stream));
-    if (st) {
-      st->iters = 0;
-      st->cycles = 0;
-      st->rel_residual = 0;
-      st->converged = 1;
-      st->guess_residual = 0;
-    }
-    return BEM_OK;
-  }
-  if (is_mixed(ctx)) return gmres_impl<c64, c64, float>(ctx, b, x, o, st, bnorm);
-  return gmres_impl<c128, c128, double>(ctx, b, x, o, st, bnorm);
+  if (is_mixed(ctx)) return gmres_impl<c64, c64, float>(ctx, b, x, o, st);
+  return gmres_impl<c128, c128, double>(ctx, b, x, o, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1729,14 +1750,15 @@ int gmres(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq_stat
 // The products A X run as one multi-right-hand-side H-matrix product, the fit
 // as one cooperative kernel. With want_res, the residual estimates
 // (res[0]: X columns alone, res[1]: every column; see launch_sem_fit) are
-// copied to ctx->host_red + SEM_RES_SLOT, valid after the next stream sync.
+// copied to res_host (pinned, two values), valid once the stream has passed
+// the fit.
 // ---------------------------------------------------------------------------
-constexpr int SEM_RES_SLOT = 4094;
 int sem_impl(bem_ctx* ctx, const c128* const* X, int K, const c128* b, c128* a0, const c128* extra = nullptr,
-             bool want_res = false) {
+             double* res_host = nullptr) {
   cudaStream_t st = ctx->stream;
   const long long N = ctx->N;
-  if (want_res) ctx->host_red[SEM_RES_SLOT] = ctx->host_red[SEM_RES_SLOT + 1] = 1.0;
+  const bool want_res = res_host != nullptr;
+  if (want_res) res_host[0] = res_host[1] = 1.0;
   const int C = K + (extra ? 1 : 0);
   if (C <= 0) {
     BEM_CUDA_TRY(cudaMemsetAsync(a0, 0, N * sizeof(c128), st));
@@ -1762,7 +1784,7 @@ int sem_impl(bem_ctx* ctx, const c128* const* X, int K, const c128* b, c128* a0,
   }
   CK("sem fit");
   if (want_res)
-    BEM_CUDA_TRY(cudaMemcpyAsync(ctx->host_red + SEM_RES_SLOT, ctx->sem_res.p, 2 * sizeof(double),
+    BEM_CUDA_TRY(cudaMemcpyAsync(res_host, ctx->sem_res.p, 2 * sizeof(double),
                                  cudaMemcpyDeviceToHost, st));
   return BEM_OK;
 }
@@ -2081,30 +2103,71 @@ static int sweep_body(bem_ctx* ctx, double T, int n_omega, const double* load_de
   const double dw = 2.0 * M_PI / T;
   const double dt = T / n_omega;
   int worst = BEM_OK;
-  Timer ta[2], t1, t2;  // ta: assembly of frequency k in ta[k & 1]
+  // per frequency: assembly, guess and solve events, the ACA failure count
+  // and the extrapolation residuals, read once the sweep has completed (the
+  // host waits on no frequency's end)
+  struct FreqRec {
+    cudaEvent_t a0 = nullptr, a1 = nullptr, g0 = nullptr, g1 = nullptr, s0 = nullptr, s1 = nullptr;
+    bool fit = false;
+  };
+  std::vector<FreqRec> rec(nf);
+  for (FreqRec& r : rec) {
+    r.a0 = take_event(ctx);
+    r.a1 = take_event(ctx);
+    r.g0 = take_event(ctx);
+    r.g1 = take_event(ctx);
+    r.s0 = take_event(ctx);
+    r.s1 = take_event(ctx);
+  }
+  struct RecRelease {
+    bem_ctx* c;
+    std::vector<FreqRec>& r;
+    ~RecRelease() {
+      for (FreqRec& x : r)
+        for (cudaEvent_t e : {x.a0, x.a1, x.g0, x.g1, x.s0, x.s1}) c->event_pool.push_back(e);
+    }
+  } rec_release{ctx, rec};
+  if ((size_t)(3 * nf) > ctx->sweep_pin_n) {
+    if (ctx->sweep_pin) cudaFreeHost(ctx->sweep_pin);
+    ctx->sweep_pin = nullptr;
+    ctx->sweep_pin_n = 0;
+    BEM_CUDA_TRY(cudaMallocHost(&ctx->sweep_pin, 3 * (size_t)nf * sizeof(double)));
+    ctx->sweep_pin_n = 3 * (size_t)nf;
+  }
+  double* sem_h = ctx->sweep_pin;                              // 2 per frequency
+  int* fails_h = reinterpret_cast<int*>(ctx->sweep_pin + 2 * nf);  // 1 per frequency
+  std::vector<bem_freq_stats> sv(nf);
   // frequency 0 on the caller's stream; afterwards frequency k + 1 is
   // assembled on asm_stream into the other operator set while the guess and
   // GMRES of frequency k run on the caller's stream (compact storage keeps one
   // operator set: frequency k + 1 is assembled after frequency k is solved)
   ctx->pre_auto = 0;
   ctx->far_verify_pending = false;
-  cudaEventRecord(ta[0].a, st);
+  cudaEventRecord(rec[0].a0, st);
   TRY(assemble_impl(ctx, ctx->eta, 0.0, o, ctx->pattern.p, ctx->Pk_host[0], ctx->b64.p, st));
-  cudaEventRecord(ta[0].b, st);
+  cudaEventRecord(rec[0].a1, st);
   // compact storage overlaps too when a second operator set (near blocks,
   // pools at their current size, leaf inverses) fits in a fifth of the free
   // device memory (of this context's share of it in a batched sweep)
-  bool pipe = !ctx->far_compact;
-  if (ctx->far_compact) {
-    size_t freeb = 0, totalb = 0;
-    BEM_CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
-    const double esz = is_mixed(ctx) ? 8.0 : 16.0;
-    const double pools = is_mixed(ctx) ? (double)(ctx->u32.n + ctx->v32.n) : (double)(ctx->u64.n + ctx->v64.n);
-    const double set_bytes =
-        esz * ((double)ctx->near_entries + 1.25 * pools + (double)ctx->leaf_pre_entries) + 16.0 * (double)N;
-    pipe = set_bytes <= 0.2 * ctx->mem_share * (double)freeb;
-  }
-  BEM_CUDA_TRY(cudaEventRecord(ctx->ev_asm_done, st));
+  // (full storage: a third set when one fits in that fifth as well)
+  size_t freeb = 0, totalb = 0;
+  BEM_CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
+  const double esz = is_mixed(ctx) ? 8.0 : 16.0;
+  const double pools = ctx->far_compact ? 1.25 * (is_mixed(ctx) ? (double)(ctx->u32.n + ctx->v32.n)
+                                                                 : (double)(ctx->u64.n + ctx->v64.n))
+                                        : (double)(ctx->u_entries + ctx->v_entries);
+  const double set_bytes = esz * ((double)ctx->near_entries + pools + (double)ctx->leaf_pre_entries) + 16.0 * (double)N;
+  const bool set_fits = set_bytes <= 0.2 * ctx->mem_share * (double)freeb;
+  const bool pipe = !ctx->far_compact || set_fits;
+  // depth: operator sets in the ring. Full storage keeps three where they
+  // fit, so that the assembly stream runs up to two frequencies ahead of the
+  // solve and neither stream waits for the other when one frequency takes
+  // longer; compact storage keeps two (one pending pool check at a time).
+  const int depth = !pipe ? 1 : (ctx->far_compact || !set_fits ? 2 : 3);
+  // the sets of frequencies k + 1, k + 2 live in back[bq[0]], back[bq[1]]
+  int bq[2] = {0, 1};
+  BEM_CUDA_TRY(cudaEventRecord(ctx->ev_asm_ring[0], st));
+  int next_asm = 1;  // the next frequency to assemble (pipelined)
   for (int k = 0; k < nf; ++k) {
     bem_freq_stats s{};
     s.k = k;
@@ -2112,37 +2175,43 @@ static int sweep_body(bem_ctx* ctx, double T, int n_omega, const double* load_de
     s.s_im = k * dw;
     c128* xk = ctx->sol.p + (long long)k * N;
     const bool next = k + 1 < nf;
-    if (next && pipe) {
-      // the other set was last used by frequency k - 1, which the host has
-      // seen complete (stream synchronised at the end of its iteration)
-      swap_ops(ctx);
-      BEM_CUDA_TRY(ctx->b64.ensure(N));
-      cudaStream_t as = ctx->asm_stream;
-      BEM_CUDA_TRY(cudaStreamWaitEvent(as, ctx->ev_asm_done, 0));  // keeps assemblies in order
-      cudaEventRecord(ta[(k + 1) & 1].a, as);
-      ctx->far_defer = ctx->far_compact;
-      const int arc = assemble_impl(ctx, ctx->eta, (k + 1) * dw, o, ctx->pattern.p, ctx->Pk_host[k + 1], ctx->b64.p,
-                                    as);
-      ctx->far_defer = false;
-      TRY(arc);
-      cudaEventRecord(ta[(k + 1) & 1].b, as);
-      BEM_CUDA_TRY(cudaEventRecord(ctx->ev_asm_done, as));
-      swap_ops(ctx);
-    }
-    cudaEventRecord(t1.a, st);
+    // the guess first, so that the solve stream has work while the host
+    // enqueues assemblies
+    cudaEventRecord(rec[k].g0, st);
     int K = (o.guess != BEM_GUESS_ZERO) ? std::min(k, std::max(0, std::min(o.sem_k, 4))) : 0;
     const c128* prev[4] = {};
     for (int q = 1; q <= 4 && q <= k; ++q) prev[q - 1] = ctx->sol.p + (long long)(k - q) * N;
     const c128* extra = nullptr;
     if (o.guess == BEM_GUESS_MLP && k >= 4) TRY(mlp_propose(ctx, prev, s.s_re * dt, s.s_im * dt, &extra));
     const bool fit = K > 0 || extra;
+    rec[k].fit = fit;
     if (fit) {
-      TRY(sem_impl(ctx, prev, K, ctx->b64.p, xk, extra, true));
+      TRY(sem_impl(ctx, prev, K, ctx->b64.p, xk, extra, sem_h + 2 * k));
     } else {
       BEM_CUDA_TRY(cudaMemsetAsync(xk, 0, N * sizeof(c128), st));
     }
-    cudaEventRecord(t1.b, st);
-    cudaEventRecord(t2.a, st);
+    cudaEventRecord(rec[k].g1, st);
+    // assemblies of the frequencies up to k + depth - 1, each into the set
+    // last used by frequency f - depth (after that solve: ev_free_ring) and
+    // after the previous assembly (the pivot state passes from one to the next)
+    for (; depth > 1 && next_asm < nf && next_asm <= k + depth - 1; ++next_asm) {
+      const int f = next_asm, slot = f % depth, bi = bq[f - k - 1];
+      swap_ops(ctx, bi);
+      BEM_CUDA_TRY(ctx->b64.ensure(N));
+      cudaStream_t as = ctx->asm_stream;
+      BEM_CUDA_TRY(cudaStreamWaitEvent(as, ctx->ev_asm_ring[(f - 1) % depth], 0));
+      BEM_CUDA_TRY(cudaStreamWaitEvent(as, ctx->ev_free_ring[slot], 0));
+      cudaEventRecord(rec[f].a0, as);
+      ctx->far_defer = ctx->far_compact;
+      const int arc =
+          assemble_impl(ctx, ctx->eta, f * dw, o, ctx->pattern.p, ctx->Pk_host[f], ctx->b64.p, as);
+      ctx->far_defer = false;
+      TRY(arc);
+      cudaEventRecord(rec[f].a1, as);
+      BEM_CUDA_TRY(cudaEventRecord(ctx->ev_asm_ring[slot], as));
+      swap_ops(ctx, bi);
+    }
+    cudaEventRecord(rec[k].s0, st);
     int rc;
     if (o.precond == BEM_PRECOND_AUTO && ctx->pre_auto == 0 && k >= 1 && ctx->minv_ready) {
       // the first frequency with k > 0 is solved with both preconditioners
@@ -2181,36 +2250,45 @@ static int sweep_body(bem_ctx* ctx, double T, int n_omega, const double* load_de
                                               (o.precond == BEM_PRECOND_AUTO && ctx->pre_auto == 2));
       rc = gmres(ctx, ctx->b64.p, xk, o, &s);
     }
-    cudaEventRecord(t2.b, st);
-    s.sem_residual = fit ? ctx->host_red[SEM_RES_SLOT] : 1.0;  // gmres synchronised the stream
+    cudaEventRecord(rec[k].s1, st);
     if (rc != BEM_OK && rc != BEM_ERR_NOT_CONVERGED) return rc;
     if (rc == BEM_ERR_NOT_CONVERGED) worst = rc;
     if (o.guess == BEM_GUESS_MLP && k >= 4)
       TRY(mlp_train(ctx, prev, xk, s.s_re * dt, s.s_im * dt, ctx->mlp_steps, ctx->mlp_lr));
-    int fails = 0;
-    BEM_CUDA_TRY(cudaMemcpyAsync(&fails, ctx->aca_fail.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    BEM_CUDA_TRY(cudaStreamSynchronize(st));
-    float ms;
-    cudaEventElapsedTime(&ms, ta[k & 1].a, ta[k & 1].b);
-    s.assemble_ms = ms;
-    cudaEventElapsedTime(&ms, t1.a, t1.b);
-    s.guess_ms = ms;
-    cudaEventElapsedTime(&ms, t2.a, t2.b);
-    s.solve_ms = ms;
-    s.aca_failures = fails;
+    BEM_CUDA_TRY(cudaMemcpyAsync(fails_h + k, ctx->aca_fail.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // this operator set is free for the assembly of frequency k + depth after here
+    BEM_CUDA_TRY(cudaEventRecord(ctx->ev_free_ring[k % depth], st));
     s.near_bytes = ctx->near_entries * (is_mixed(ctx) ? 8 : 16);
-    if (stats) stats[k] = s;
+    sv[k] = s;
     ctx->nf = k + 1;
-    if (next && pipe) {
-      // frequency k + 1's operator and right-hand side become the set in use
-      BEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_asm_done, 0));
-      swap_ops(ctx);
+    if (next && depth > 1) {
+      // frequency k + 1's operator and right-hand side become the set in use;
+      // frequency k's set goes to the end of the queue
+      BEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_asm_ring[(k + 1) % depth], 0));
+      swap_ops(ctx, bq[0]);
+      if (depth == 3) std::swap(bq[0], bq[1]);
       TRY(far_field_verify(ctx, o));
     } else if (next) {
-      cudaEventRecord(ta[(k + 1) & 1].a, st);
+      cudaEventRecord(rec[k + 1].a0, st);
       TRY(assemble_impl(ctx, ctx->eta, (k + 1) * dw, o, ctx->pattern.p, ctx->Pk_host[k + 1], ctx->b64.p, st));
-      cudaEventRecord(ta[(k + 1) & 1].b, st);
+      cudaEventRecord(rec[k + 1].a1, st);
     }
+  }
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->asm_stream));
+  prof_harvest(ctx);
+  for (int k = 0; k < nf; ++k) {
+    bem_freq_stats& s = sv[k];
+    float ms = 0;
+    cudaEventElapsedTime(&ms, rec[k].a0, rec[k].a1);
+    s.assemble_ms = ms;
+    cudaEventElapsedTime(&ms, rec[k].g0, rec[k].g1);
+    s.guess_ms = ms;
+    cudaEventElapsedTime(&ms, rec[k].s0, rec[k].s1);
+    s.solve_ms = ms;
+    s.sem_residual = rec[k].fit ? sem_h[2 * k] : 1.0;
+    s.aca_failures = fails_h[k];
+    if (stats) stats[k] = s;
   }
   if (stats && !ctx->far_h.empty()) {
     std::vector<int> rk(ctx->far_h.size());

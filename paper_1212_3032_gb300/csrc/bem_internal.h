@@ -157,11 +157,46 @@ template <typename T> struct DevBuf {
 bool count_if(bool c);
 long long launch_count();
 
+// Device-side state of one GMRES solve (restarted GMRES, right
+// preconditioning, Sec. 3.1). The kernels of an Arnoldi step, of the update
+// that closes a cycle and of the true-residual test read and advance it, so
+// that the host enqueues a solve's work without waiting on any step. The
+// kernels that change it also write a copy to mapped host memory, from which
+// the host learns, a few steps later, that a cycle or the solve has ended.
+constexpr int GM_MAX_CYCLES = 256;  // cycles whose step counts are recorded
+struct GmCtl {
+  int active;     // a cycle is under way: the step kernels do their work
+  int j;          // Arnoldi steps taken in the current cycle
+  int update;     // the cycle has ended; the update of x is pending
+  int live;       // the solve has not finished
+  int its;        // Arnoldi steps over all cycles
+  int cycles;     // cycles started
+  int converged;  // the true residual met the tolerance
+  int arrive;     // blocks of the residual test that have read the state
+  double bnorm, rel, guess_rel, target;
+  int jdone[GM_MAX_CYCLES];  // steps taken by each cycle
+};
+// What the device-driven kernels share (passed by value).
+struct GmDev {
+  GmCtl* ctl;          // device state
+  GmCtl* mirror;       // its mapped host copy (device address)
+  c128* R;             // rotated Hessenberg columns: column j at R + j (m + 1)
+  c128* g;             // m + 1: rotated right-hand side of the small least-squares problem
+  c128* cs;            // m: Givens rotations (cosines)
+  c128* sn;            // m: (sines)
+  c128* hcol;          // the steps' Hessenberg column slots, slot_len apart
+  long long slot_len;
+  int m, max_iters;
+  double tol;          // on ||r|| / ||b||
+  double floor;        // inner target relative to the cycle's first residual
+};
+
 struct MlpState;  // learned initial guess (bem_mlp.cu)
 
 // The storage of one assembled operator and its right-hand side. A sweep
-// keeps two: frequency k + 1 is assembled into one while GMRES runs on the
-// other (the context's fields hold the set in use; swap_ops exchanges them).
+// keeps up to three: frequencies k + 1 and k + 2 are assembled into the
+// others while GMRES runs on the set of frequency k (the context's fields
+// hold the set in use; swap_ops exchanges it with one of the others).
 struct OpSet {
   DevBuf<c64> near32, u32, v32, prec_inv32, minv32;
   DevBuf<c128> near64, u64, v64, prec_inv, b64, minv64;
@@ -266,13 +301,13 @@ struct bem_ctx {
   cudaStream_t aux_stream = nullptr;  // the far-field assembly runs here, joined back to stream
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t asm_stream = nullptr;  // a sweep assembles frequency k + 1 here while GMRES(k) runs
-  cudaEvent_t ev_asm_done = nullptr;
+  cudaEvent_t ev_asm_ring[3] = {};    // a sweep's assembly of frequency f has completed (slot f mod depth)
   // a sweep runs the caller's part of its work (guess, GMRES, IDFT) on this
   // stream of the device's greatest priority, so that blocks of the
   // overlapped assembly (least priority) do not delay it; joined to `stream`
   cudaStream_t solve_stream = nullptr;
   cudaEvent_t ev_solve_in = nullptr, ev_solve_out = nullptr;
-  bem::OpSet back;                    // the operator set not in use (see swap_ops)
+  bem::OpSet back[2];                 // the operator sets not in use (see swap_ops)
   bem::DevBuf<int> leaf_cnt;          // per leaf: tasks completed in the current product (reset to 0 after it)
   bem::DevBuf<int> task_ptr;          // CSR of tasks over leaves
   bem::DevBuf<double> part;           // partial sums (sized for 4 rhs of complex FP64)
@@ -346,6 +381,15 @@ struct bem_ctx {
   double* host_cols = nullptr;         // pinned Hessenberg column slots of GMRES
   size_t host_cols_n = 0;              // complex values it holds
   std::vector<cudaEvent_t> col_events; // one per Arnoldi step of a cycle
+  bem::DevBuf<bem::GmCtl> gm_ctl;      // device-driven GMRES: state
+  bem::GmCtl* gm_mirror = nullptr;     // its mapped host copy (host address)
+  bem::GmCtl* gm_mirror_dev = nullptr; // (device address)
+  bem::DevBuf<bem::c128> gm_work;      // rotated columns, g, cs, sn
+  bem::DevBuf<bem::c64> gm_w32, gm_z32;   // product output and preconditioned input of a step
+  bem::DevBuf<bem::c128> gm_w64, gm_z64;
+  cudaEvent_t ev_free_ring[3] = {};   // a sweep's solve of frequency f has completed (its set is free)
+  double* sweep_pin = nullptr;         // pinned per-frequency results of a sweep (extrapolation residuals,
+  size_t sweep_pin_n = 0;              // ACA failure counts), read after it
 
   // event timing (bem_set_profiling)
   bool profiling = false;

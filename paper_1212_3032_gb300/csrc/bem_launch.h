@@ -69,18 +69,21 @@ void launch_far_pack(const FarBlk* blks, int b0, int nblk, const int* rank, cons
 // H-matrix product y = A x for nrhs right-hand sides (x, y: nrhs vectors of
 // length N, stride N). Op: operator storage; X: input vectors; Y: output;
 // accumulation in Acc (float or double).
+// run (optional): the launch does nothing unless *run is nonzero.
 template <typename Op, typename X, typename Y, typename Acc>
 void launch_hmatvec(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V, cplx<Acc>* t,
-                    const X* x, Y* y, int nrhs, cudaStream_t st);
+                    const X* x, Y* y, int nrhs, cudaStream_t st, const int* run = nullptr);
 
 // y = A x (c64 operator, FP32 accumulation, one right-hand side) with
 // caller-provided scratch: t (t_entries values) and part (part_rows values).
 void launch_hmatvec_scratch_c64(const bem_ctx* ctx, const c64* near, const c64* U, const c64* V, cplx<float>* t,
                                 cplx<float>* part, const c64* x, c64* y, cudaStream_t st);
 
-// z = M^{-1} v per element (3x3 inverse diagonal blocks)
+// z = M^{-1} v per element (3x3 inverse diagonal blocks); run (optional): the
+// launch does nothing unless *run; joff (optional): v taken at v + (*joff) ldv
 template <typename Pm, typename V, typename Z>
-void launch_precond(const Pm* pinv, const V* v, Z* z, int ne, cudaStream_t st);
+void launch_precond(const Pm* pinv, const V* v, Z* z, int ne, cudaStream_t st, const int* run = nullptr,
+                    const int* joff = nullptr, long long ldv = 0);
 
 // Partial dot products part[l * nblk + blk] of conj(V_l) . w, l < nvec (FP64)
 template <typename Vb, typename W>
@@ -89,9 +92,20 @@ int launch_dots(const Vb* V, long long ldv, int nvec, const W* w, long long n, c
 // V_{j+1} = w / ||w||) in a single cooperative launch; hcol receives
 // [h1 (m+1) | h2 (m+1) | ||w||^2]; part needs (2 (j+1) + 1) x
 // arnoldi_orth_max_blocks() complex values.
+// With gm (the device-driven solver): j and the column slot come from its
+// state, the launch does nothing outside a cycle, and the step's Givens
+// rotation and convergence test are taken on the device (bem_solve.cu).
 template <typename Vb>
 cudaError_t launch_arnoldi_orth(Vb* V, long long ldv, int j, Vb* w, long long n, c128* part, c128* hcol, int m,
-                                cudaStream_t st);
+                                cudaStream_t st, const GmDev* gm = nullptr);
+// Device-driven GMRES: start of a solve (bb: ||b||^2 on the device), the
+// true-residual test that ends the solve or starts a cycle (rr: ||r||^2;
+// V0 = r / ||r||), and the update out = V R^{-1} g that closes a cycle.
+void launch_gm_init(const GmDev& d, const c128* bb, cudaStream_t st);
+template <typename Vb>
+void launch_gm_begin(const GmDev& d, const c128* rr, const c128* r, Vb* V0, c128* x, long long n, cudaStream_t st);
+template <typename Vb>
+void launch_gm_combine(const Vb* V, long long ldv, const GmDev& d, c128* out, long long n, cudaStream_t st);
 int arnoldi_orth_max_blocks();
 // Solution extrapolation fit (Sec. 4.2) after Y = A X (C columns of n, c128):
 // CGS2 QR, s = R^{-1} Q^H b, a0 = X s, and the residual estimates res[0..1]
@@ -114,7 +128,7 @@ void launch_residual(const c128* b, const c128* y, c128* r, long long n, cudaStr
 template <typename Vb>
 void launch_combine(const Vb* V, long long ldv, int nvec, const c128* y, c128* out, long long n,
                     cudaStream_t st);
-void launch_axpy(c128 a, const c128* x, c128* y, long long n, cudaStream_t st);
+void launch_axpy(c128 a, const c128* x, c128* y, long long n, cudaStream_t st, const int* run = nullptr);
 void launch_copy_cast(const c128* x, c64* y, long long n, double scale, cudaStream_t st);
 void launch_copy_cast(const c128* x, c128* y, long long n, double scale, cudaStream_t st);
 
@@ -144,6 +158,7 @@ cudaError_t launch_leaf_inverse(const LeafPre* leaves, int nleaves, const cplx<R
                                 cplx<R>* out, cudaStream_t st);
 // z = M^-1 v with the leaf inverses (tree order vectors)
 template <typename Pm, typename V, typename Z>
-void launch_leaf_apply(const LeafPre* leaves, int nleaves, const Pm* minv, const V* v, Z* z, cudaStream_t st);
+void launch_leaf_apply(const LeafPre* leaves, int nleaves, const Pm* minv, const V* v, Z* z, cudaStream_t st,
+                       const int* run = nullptr, const int* joff = nullptr, long long ldv = 0);
 
 }  // namespace bem

@@ -199,12 +199,17 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(LI_THREADS) k_leaf_i
   }
 }
 
-// z[rows of leaf] = M_leaf^-1 v[rows of leaf] (column-major inverse, ldo even)
+// z[rows of leaf] = M_leaf^-1 v[rows of leaf] (column-major inverse, ldo even);
+// run / joff as for the 3 x 3 blocks (a launch that does nothing unless *run,
+// v read from v + (*joff) ldv)
 constexpr int LA_THREADS = 256;
 template <typename Pm, typename V, typename Z>
 __global__ void __launch_bounds__(LA_THREADS) k_leaf_apply(const LeafPre* __restrict__ leaves,
                                                            const Pm* __restrict__ minv, const V* __restrict__ v,
-                                                           Z* __restrict__ z) {
+                                                           Z* __restrict__ z, const int* __restrict__ run,
+                                                           const int* __restrict__ joff, long long ldv) {
+  if (run && !*run) return;
+  if (joff) v += (long long)(*joff) * ldv;
   using Acc = std::conditional_t<(sizeof(Pm) == 16 || sizeof(V) == 16), double, float>;
   __shared__ cplx<Acc> red[LA_THREADS];
   const LeafPre L = leaves[blockIdx.x];
@@ -286,18 +291,21 @@ cudaError_t launch_leaf_inverse(const LeafPre* leaves, int nleaves, const cplx<R
 }
 
 template <typename Pm, typename V, typename Z>
-void launch_leaf_apply(const LeafPre* leaves, int nleaves, const Pm* minv, const V* v, Z* z, cudaStream_t st) {
+void launch_leaf_apply(const LeafPre* leaves, int nleaves, const Pm* minv, const V* v, Z* z, cudaStream_t st,
+                       const int* run, const int* joff, long long ldv) {
   if (!count_if(nleaves > 0)) return;
-  k_leaf_apply<Pm, V, Z><<<nleaves, LA_THREADS, 0, st>>>(leaves, minv, v, z);
+  k_leaf_apply<Pm, V, Z><<<nleaves, LA_THREADS, 0, st>>>(leaves, minv, v, z, run, joff, ldv);
 }
 
 template cudaError_t launch_leaf_inverse<float>(const LeafPre*, int, const cplx<float>*, const c128*, cplx<float>*,
                                                cudaStream_t);
 template cudaError_t launch_leaf_inverse<double>(const LeafPre*, int, const cplx<double>*, const c128*,
                                                 cplx<double>*, cudaStream_t);
-template void launch_leaf_apply<c64, c64, c64>(const LeafPre*, int, const c64*, const c64*, c64*, cudaStream_t);
-template void launch_leaf_apply<c64, c128, c128>(const LeafPre*, int, const c64*, const c128*, c128*, cudaStream_t);
+template void launch_leaf_apply<c64, c64, c64>(const LeafPre*, int, const c64*, const c64*, c64*, cudaStream_t,
+                                               const int*, const int*, long long);
+template void launch_leaf_apply<c64, c128, c128>(const LeafPre*, int, const c64*, const c128*, c128*, cudaStream_t,
+                                                 const int*, const int*, long long);
 template void launch_leaf_apply<c128, c128, c128>(const LeafPre*, int, const c128*, const c128*, c128*,
-                                                  cudaStream_t);
+                                                  cudaStream_t, const int*, const int*, long long);
 
 }  // namespace bem

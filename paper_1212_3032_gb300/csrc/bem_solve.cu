@@ -523,7 +523,9 @@ __global__ void __launch_bounds__(HF_THREADS, (NRHS == 1 && sizeof(Acc) == 4) ? 
     const int* __restrict__ rank, const long long* __restrict__ fbase, const Op* __restrict__ near,
     const Op* __restrict__ U, const Op* __restrict__ V, const X* __restrict__ x, long long N, int tsn,
     cplx<Acc>* __restrict__ part, long long pstride, const int* __restrict__ hc_ptr,
-    const long long* __restrict__ hc_off, int* __restrict__ leaf_cnt, Y* __restrict__ y) {
+    const long long* __restrict__ hc_off, int* __restrict__ leaf_cnt, Y* __restrict__ y,
+    const int* __restrict__ run) {
+  if (run && !*run) return;  // every CTA of the launch reads the same flag
   extern __shared__ unsigned char smem_raw[];
   cplx<Acc>* ts = reinterpret_cast<cplx<Acc>*>(smem_raw);  // NRHS x tsn: the items' V^T x values
   cplx<Acc>* red = ts + NRHS * tsn;                        // NRHS x HF_THREADS x E
@@ -613,7 +615,7 @@ __global__ void __launch_bounds__(HF_THREADS, (NRHS == 1 && sizeof(Acc) == 4) ? 
 
 template <typename Op, typename X, typename Y, typename Acc, int NRHS>
 static void hmv_impl(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V, cplx<Acc>* t,
-                     const X* x, Y* y, cudaStream_t st) {
+                     const X* x, Y* y, cudaStream_t st, const int* run) {
   (void)t;
   if (!ctx->nhitems) return;
   constexpr int E = 16 / (int)sizeof(Op);
@@ -637,17 +639,17 @@ static void hmv_impl(const bem_ctx* ctx, const Op* near, const Op* U, const Op* 
   k_hmv_fused<Op, X, Y, Acc, NRHS><<<ctx->nhitems, HF_THREADS, sm, st>>>(
       ctx->hitems.p, ctx->hfar_list.p, ctx->leaf_r0.p, ctx->leaf_nr.p, ctx->panels.p, ctx->far_d.p, ctx->rank.p,
       ctx->fbase.p, near, U, V, x, ctx->N, tsn, part, ctx->hpart_rows, ctx->hc_ptr.p, ctx->hc_off.p,
-      ctx->leaf_cnt.p, y);
+      ctx->leaf_cnt.p, y, run);
 }
 
 template <typename Op, typename X, typename Y, typename Acc>
 void launch_hmatvec(const bem_ctx* ctx, const Op* near, const Op* U, const Op* V, cplx<Acc>* t, const X* x,
-                    Y* y, int nrhs, cudaStream_t st) {
+                    Y* y, int nrhs, cudaStream_t st, const int* run) {
   switch (nrhs) {
-    case 1: hmv_impl<Op, X, Y, Acc, 1>(ctx, near, U, V, t, x, y, st); break;
-    case 2: hmv_impl<Op, X, Y, Acc, 2>(ctx, near, U, V, t, x, y, st); break;
-    case 3: hmv_impl<Op, X, Y, Acc, 3>(ctx, near, U, V, t, x, y, st); break;
-    default: hmv_impl<Op, X, Y, Acc, 4>(ctx, near, U, V, t, x, y, st); break;
+    case 1: hmv_impl<Op, X, Y, Acc, 1>(ctx, near, U, V, t, x, y, st, run); break;
+    case 2: hmv_impl<Op, X, Y, Acc, 2>(ctx, near, U, V, t, x, y, st, run); break;
+    case 3: hmv_impl<Op, X, Y, Acc, 3>(ctx, near, U, V, t, x, y, st, run); break;
+    default: hmv_impl<Op, X, Y, Acc, 4>(ctx, near, U, V, t, x, y, st, run); break;
   }
 }
 
@@ -671,20 +673,28 @@ void launch_hmatvec_scratch_c64(const bem_ctx* ctx, const c64* near, const c64* 
 }
 
 template void launch_hmatvec<c64, c64, c64, float>(const bem_ctx*, const c64*, const c64*, const c64*,
-                                                   cplx<float>*, const c64*, c64*, int, cudaStream_t);
+                                                   cplx<float>*, const c64*, c64*, int, cudaStream_t, const int*);
 template void launch_hmatvec<c64, c64, c128, float>(const bem_ctx*, const c64*, const c64*, const c64*,
-                                                    cplx<float>*, const c64*, c128*, int, cudaStream_t);
+                                                    cplx<float>*, const c64*, c128*, int, cudaStream_t,
+                                                    const int*);
 template void launch_hmatvec<c64, c128, c128, double>(const bem_ctx*, const c64*, const c64*, const c64*,
-                                                      cplx<double>*, const c128*, c128*, int, cudaStream_t);
+                                                      cplx<double>*, const c128*, c128*, int, cudaStream_t,
+                                                      const int*);
 template void launch_hmatvec<c128, c128, c128, double>(const bem_ctx*, const c128*, const c128*,
                                                        const c128*, cplx<double>*, const c128*, c128*, int,
-                                                       cudaStream_t);
+                                                       cudaStream_t, const int*);
 
 // ---------------------------------------------------------------------------
 // block-Jacobi preconditioner
 // ---------------------------------------------------------------------------
+// run (optional): the launch does nothing unless *run is nonzero; joff
+// (optional): v is read from v + (*joff) ldv (the device-driven solver's
+// basis vector V_j).
 template <typename Pm, typename V, typename Z>
-__global__ void k_precond(const Pm* __restrict__ pinv, const V* __restrict__ v, Z* __restrict__ z, int ne) {
+__global__ void k_precond(const Pm* __restrict__ pinv, const V* __restrict__ v, Z* __restrict__ z, int ne,
+                          const int* __restrict__ run, const int* __restrict__ joff, long long ldv) {
+  if (run && !*run) return;
+  if (joff) v += (long long)(*joff) * ldv;
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   using Acc = typename Promote<decltype(Pm{}.re), decltype(V{}.re)>::type;
@@ -700,13 +710,17 @@ __global__ void k_precond(const Pm* __restrict__ pinv, const V* __restrict__ v, 
   }
 }
 template <typename Pm, typename V, typename Z>
-void launch_precond(const Pm* pinv, const V* v, Z* z, int ne, cudaStream_t st) {
+void launch_precond(const Pm* pinv, const V* v, Z* z, int ne, cudaStream_t st, const int* run, const int* joff,
+                    long long ldv) {
   count_if(true);
-  k_precond<Pm, V, Z><<<(ne + 127) / 128, 128, 0, st>>>(pinv, v, z, ne);
+  k_precond<Pm, V, Z><<<(ne + 127) / 128, 128, 0, st>>>(pinv, v, z, ne, run, joff, ldv);
 }
-template void launch_precond<c64, c64, c64>(const c64*, const c64*, c64*, int, cudaStream_t);
-template void launch_precond<c128, c128, c128>(const c128*, const c128*, c128*, int, cudaStream_t);
-template void launch_precond<c128, c128, c64>(const c128*, const c128*, c64*, int, cudaStream_t);
+template void launch_precond<c64, c64, c64>(const c64*, const c64*, c64*, int, cudaStream_t, const int*,
+                                            const int*, long long);
+template void launch_precond<c128, c128, c128>(const c128*, const c128*, c128*, int, cudaStream_t, const int*,
+                                               const int*, long long);
+template void launch_precond<c128, c128, c64>(const c128*, const c128*, c64*, int, cudaStream_t, const int*,
+                                              const int*, long long);
 
 // ---------------------------------------------------------------------------
 // Arnoldi pieces (FP64 accumulation)
@@ -901,12 +915,83 @@ __device__ __forceinline__ void orth_update(const Vb* __restrict__ V, long long 
 constexpr int ORTH_THREADS = 256;
 constexpr int ORTH_MAXVEC = 513;  // shared-memory coefficient slots (restart + 1 <= 512)
 
+// The host copy of the solver state (the fields the host reads).
+__device__ __forceinline__ void gm_publish(const GmCtl* c, GmCtl* mirror) {
+  volatile GmCtl* h = mirror;
+  h->active = c->active;
+  h->j = c->j;
+  h->update = c->update;
+  h->live = c->live;
+  h->its = c->its;
+  h->cycles = c->cycles;
+  h->converged = c->converged;
+  h->bnorm = c->bnorm;
+  h->rel = c->rel;
+  h->guess_rel = c->guess_rel;
+  h->target = c->target;
+}
+
+// Step j of the cycle on the host's behalf (one thread): column j of the
+// Hessenberg matrix (the two projections summed, ||w|| below them), the
+// rotations of the earlier steps applied to it, the rotation that zeroes its
+// subdiagonal, and the residual estimate |g_{j+1}|. The cycle ends when that
+// estimate meets the inner target, on breakdown (||w|| = 0), after m steps or
+// at the step limit.
+__device__ void gm_givens(const GmDev& d, int j, const c128* __restrict__ hcol, double nrm2) {
+  GmCtl* c = d.ctl;
+  const int m = d.m;
+  c128* Rj = d.R + (long long)j * (m + 1);
+  for (int i = 0; i <= j; ++i) Rj[i] = c128{hcol[i].re + hcol[m + 1 + i].re, hcol[i].im + hcol[m + 1 + i].im};
+  const double hn = sqrt(fmax(0.0, nrm2));
+  c128 b = Rj[0];
+  for (int i = 0; i < j; ++i) {
+    // G_i = [[conj c, conj s], [-s, c]] on rows i, i + 1
+    const c128 a = b, nx = Rj[i + 1], ci = d.cs[i], si = d.sn[i];
+    Rj[i] = c128{ci.re * a.re + ci.im * a.im + si.re * nx.re + si.im * nx.im,
+                 ci.re * a.im - ci.im * a.re + si.re * nx.im - si.im * nx.re};
+    b = c128{-(si.re * a.re - si.im * a.im) + (ci.re * nx.re - ci.im * nx.im),
+             -(si.re * a.im + si.im * a.re) + (ci.re * nx.im + ci.im * nx.re)};
+  }
+  const double den = sqrt(b.re * b.re + b.im * b.im + hn * hn);
+  const c128 cj = den > 0 ? c128{b.re / den, b.im / den} : c128{1.0, 0.0};
+  const c128 sj = den > 0 ? c128{hn / den, 0.0} : c128{0.0, 0.0};
+  d.cs[j] = cj;
+  d.sn[j] = sj;
+  Rj[j] = c128{den, 0.0};
+  const c128 gj = d.g[j];
+  d.g[j + 1] = c128{-(sj.re * gj.re - sj.im * gj.im), -(sj.re * gj.im + sj.im * gj.re)};
+  d.g[j] = c128{cj.re * gj.re + cj.im * gj.im, cj.re * gj.im - cj.im * gj.re};
+  const int its = c->its + 1, jn = j + 1;
+  const double gcur = sqrt(d.g[jn].re * d.g[jn].re + d.g[jn].im * d.g[jn].im);
+  c->its = its;
+  c->j = jn;
+  if (gcur <= c->target || its >= d.max_iters || hn == 0.0 || jn == m) {
+    c->active = 0;
+    c->update = 1;
+    const int cy = c->cycles - 1;
+    if (cy >= 0 && cy < GM_MAX_CYCLES) {
+      c->jdone[cy] = jn;
+      reinterpret_cast<volatile int*>(d.mirror->jdone)[cy] = jn;
+    }
+  }
+  gm_publish(c, d.mirror);
+}
+
+// With gm.ctl set (the device-driven solver) the step index j and the column
+// slot come from the solver state, the launch does nothing outside a cycle,
+// and block 0 takes the step's Givens rotation after the last grid barrier
+// (every block has read the state before the first one).
 template <typename Vb>
 __global__ void __launch_bounds__(ORTH_THREADS) k_arnoldi_orth(Vb* __restrict__ V, long long ldv, int j,
                                                                Vb* __restrict__ w, long long n,
                                                                c128* __restrict__ part, c128* __restrict__ hcol,
-                                                               int m) {
+                                                               int m, GmDev gm) {
   using T = decltype(Vb{}.re);
+  if (gm.ctl) {
+    if (!gm.ctl->active) return;  // the same in every block: no grid barrier is reached
+    j = gm.ctl->j;
+    hcol = gm.hcol + (long long)j * gm.slot_len;
+  }
   cg::grid_group grid = cg::this_grid();
   __shared__ c128 h[ORTH_MAXVEC];
   __shared__ cplx<T> hT[ORTH_MAXVEC];
@@ -964,6 +1049,10 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_arnoldi_orth(Vb* __restrict__ 
     o.im = a.im * sc;
     vn[i] = o;
   }
+  if (gm.ctl && blockIdx.x == 0) {
+    __syncthreads();  // block 0's column writes are visible to its thread 0
+    if (threadIdx.x == 0) gm_givens(gm, j, hcol, nrm2);
+  }
 }
 
 template <typename Vb>
@@ -983,17 +1072,155 @@ int orth_grid(long long n) {
 
 template <typename Vb>
 cudaError_t launch_arnoldi_orth(Vb* V, long long ldv, int j, Vb* w, long long n, c128* part, c128* hcol, int m,
-                                cudaStream_t st) {
-  if (j + 1 > ORTH_MAXVEC) return cudaErrorInvalidValue;
+                                cudaStream_t st, const GmDev* gm) {
+  if (j + 1 > ORTH_MAXVEC || m + 1 > ORTH_MAXVEC) return cudaErrorInvalidValue;
   const int nb = orth_grid<Vb>(n);
-  void* args[] = {&V, &ldv, &j, &w, &n, &part, &hcol, &m};
+  GmDev g{};
+  if (gm) g = *gm;
+  void* args[] = {&V, &ldv, &j, &w, &n, &part, &hcol, &m, &g};
   count_if(true);
   return cudaLaunchCooperativeKernel((const void*)k_arnoldi_orth<Vb>, dim3(nb), dim3(ORTH_THREADS), args, 0, st);
 }
 template cudaError_t launch_arnoldi_orth<c64>(c64*, long long, int, c64*, long long, c128*, c128*, int,
-                                              cudaStream_t);
+                                              cudaStream_t, const GmDev*);
 template cudaError_t launch_arnoldi_orth<c128>(c128*, long long, int, c128*, long long, c128*, c128*, int,
-                                               cudaStream_t);
+                                               cudaStream_t, const GmDev*);
+
+// ---------------------------------------------------------------------------
+// The rest of the device-driven GMRES control
+// ---------------------------------------------------------------------------
+// Start of a solve: ||b|| from its squared norm (bb, device), counters reset.
+__global__ void k_gm_init(GmDev d, const c128* __restrict__ bb) {
+  GmCtl* c = d.ctl;
+  c->active = 0;
+  c->j = 0;
+  c->update = 0;
+  c->live = 1;
+  c->its = 0;
+  c->cycles = 0;
+  c->converged = 0;
+  c->arrive = 0;
+  c->bnorm = sqrt(fmax(0.0, bb->re));
+  c->rel = 1.0;
+  c->guess_rel = 1.0;
+  c->target = 0.0;
+  gm_publish(c, d.mirror);
+}
+void launch_gm_init(const GmDev& d, const c128* bb, cudaStream_t st) {
+  count_if(true);
+  k_gm_init<<<1, 1, 0, st>>>(d, bb);
+}
+
+// The true-residual test after r = b - A x (rr = ||r||^2 on the device):
+// the solve ends if ||r|| <= tol ||b|| (or r = 0) or the step limit is
+// reached; otherwise a cycle starts from V_0 = r / ||r|| with g = (||r||, 0,
+// ...) and the inner target max(0.9 tol ||b||, floor ||r||). A zero
+// right-hand side gives x = 0. The blocks read the state first; the last
+// block to arrive writes it, so that no block sees a half-updated state.
+template <typename Vb>
+__global__ void k_gm_begin(GmDev d, const c128* __restrict__ rr, const c128* __restrict__ r, Vb* __restrict__ V0,
+                           c128* __restrict__ x, long long n) {
+  GmCtl* c = d.ctl;
+  const int live = c->live, its = c->its, cycles = c->cycles;
+  const double bnorm = c->bnorm;
+  const double rnorm = sqrt(fmax(0.0, rr->re));
+  const double rel = bnorm > 0 ? rnorm / bnorm : 0.0;
+  const bool conv = rel <= d.tol || rnorm == 0.0;
+  const bool start = live && !conv && its < d.max_iters;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) {
+    if (live && bnorm == 0.0) x[i] = c128{0.0, 0.0};
+    if (start) {
+      const double sc = 1.0 / rnorm;
+      Vb o;
+      o.re = decltype(o.re)(r[i].re * sc);
+      o.im = decltype(o.im)(r[i].im * sc);
+      V0[i] = o;
+    }
+  }
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&c->arrive, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  c->arrive = 0;
+  if (!live) return;
+  c->update = 0;
+  c->rel = rel;
+  if (cycles == 0) c->guess_rel = rel;
+  if (!start) {
+    c->live = 0;
+    c->active = 0;
+    c->converged = conv ? 1 : 0;
+  } else {
+    c->active = 1;
+    c->j = 0;
+    c->cycles = cycles + 1;
+    d.g[0] = c128{rnorm, 0.0};
+    c->target = fmax(0.9 * d.tol * bnorm, d.floor * rnorm);
+  }
+  gm_publish(c, d.mirror);
+}
+template <typename Vb>
+void launch_gm_begin(const GmDev& d, const c128* rr, const c128* r, Vb* V0, c128* x, long long n, cudaStream_t st) {
+  count_if(true);
+  k_gm_begin<Vb><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, rr, r, V0, x, n);
+}
+template void launch_gm_begin<c64>(const GmDev&, const c128*, const c128*, c64*, c128*, long long, cudaStream_t);
+template void launch_gm_begin<c128>(const GmDev&, const c128*, const c128*, c128*, c128*, long long,
+                                    cudaStream_t);
+
+// The update that closes a cycle (only when one has ended): y = R^{-1} g
+// over the cycle's steps (back substitution by one warp, in every block),
+// then out = V y.
+template <typename Vb>
+__global__ void k_gm_combine(const Vb* __restrict__ V, long long ldv, GmDev d, c128* __restrict__ out,
+                             long long n) {
+  if (!d.ctl->update) return;
+  const int jd = d.ctl->j, m = d.m;
+  __shared__ c128 y[ORTH_MAXVEC];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i = jd - 1; i >= 0; --i) {
+      double sre = 0, sim = 0;
+      for (int k = i + 1 + lane; k < jd; k += 32) {
+        const c128 a = d.R[(long long)k * (m + 1) + i], b = y[k];
+        sre = fma(a.re, b.re, fma(-a.im, b.im, sre));
+        sim = fma(a.re, b.im, fma(a.im, b.re, sim));
+      }
+      sre = wsum(sre);
+      sim = wsum(sim);
+      if (lane == 0) {
+        const c128 gi = d.g[i], a = d.R[(long long)i * (m + 1) + i];
+        const double tr = gi.re - sre, ti = gi.im - sim, den = a.re * a.re + a.im * a.im;
+        y[i] = den > 0 ? c128{(tr * a.re + ti * a.im) / den, (ti * a.re - tr * a.im) / den} : c128{0.0, 0.0};
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double re = 0, im = 0;
+  for (int l = 0; l < jd; ++l) {
+    const Vb a = V[l * ldv + i];
+    const c128 c = y[l];
+    re = fma((double)a.re, c.re, fma(-(double)a.im, c.im, re));
+    im = fma((double)a.re, c.im, fma((double)a.im, c.re, im));
+  }
+  out[i] = c128{re, im};
+}
+template <typename Vb>
+void launch_gm_combine(const Vb* V, long long ldv, const GmDev& d, c128* out, long long n, cudaStream_t st) {
+  count_if(true);
+  k_gm_combine<Vb><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, ldv, d, out, n);
+}
+template void launch_gm_combine<c64>(const c64*, long long, const GmDev&, c128*, long long, cudaStream_t);
+template void launch_gm_combine<c128>(const c128*, long long, const GmDev&, c128*, long long, cudaStream_t);
 int arnoldi_orth_max_blocks() { return std::max(orth_grid<c64>(1LL << 40), orth_grid<c128>(1LL << 40)); }
 
 // ---------------------------------------------------------------------------
@@ -1170,15 +1397,17 @@ void launch_combine(const Vb* V, long long ldv, int nvec, const c128* y, c128* o
 template void launch_combine<c64>(const c64*, long long, int, const c128*, c128*, long long, cudaStream_t);
 template void launch_combine<c128>(const c128*, long long, int, const c128*, c128*, long long, cudaStream_t);
 
-__global__ void k_axpy(c128 a, const c128* __restrict__ x, c128* __restrict__ y, long long n) {
+__global__ void k_axpy(c128 a, const c128* __restrict__ x, c128* __restrict__ y, long long n,
+                       const int* __restrict__ run) {
+  if (run && !*run) return;
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   c128 v = x[i];
   y[i] = c128{y[i].re + a.re * v.re - a.im * v.im, y[i].im + a.re * v.im + a.im * v.re};
 }
-void launch_axpy(c128 a, const c128* x, c128* y, long long n, cudaStream_t st) {
+void launch_axpy(c128 a, const c128* x, c128* y, long long n, cudaStream_t st, const int* run) {
   count_if(true);
-  k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, x, y, n);
+  k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, x, y, n, run);
 }
 
 template <typename O>
