@@ -54,7 +54,7 @@ MAT = dict(E=1.0, nu=0.25, rho=1.0)
 
 # DRAM read + write of one H-matrix product (k_hmv_fused) at k = n_omega / 4
 # of cavity5120, from the ncu capture of `bench.py --profile-case`
-# (profiles/k_hmv_fused_cavity5120.md: 888.1 MB read, 3.8 MB written); the
+# (profiles/k_hmv_fused_cavity5120.md: 888.0 MB read, 3.9 MB written); the
 # same product's algorithmic bytes are 887.3 MB (counted by the library), so
 # the kernel streams every operator entry once.
 HMV_TRAFFIC_K64 = 891_946_752
