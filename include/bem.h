@@ -76,8 +76,9 @@ extern "C" {
                              most a quarter of the device memory, else compact */
 #define BEM_FAR_FULL 1    /* every block's U, V at its rank cap, ACA writes in place */
 #define BEM_FAR_COMPACT 2 /* ACA in a workspace batch by batch, factors packed at
-                             their actual ranks; one operator set (no overlap of
-                             the next frequency's assembly with the solve) */
+                             their actual ranks; a sweep keeps a second operator
+                             set (the next frequency assembled during the solve)
+                             only where it fits in a fifth of the free memory */
 
 /* block-diagonal preconditioner of GMRES (Sec. 3.1, Sec. 5: "block diagonal",
  * block size not stated) */
@@ -168,6 +169,10 @@ int bem_set_window(bem_ctx* ctx, double eta, int window);
  * DFT-MFT. bc_pattern: ne x 3 (traction on Gamma_sigma elements,
  * displacement on Gamma_u elements). stats (optional): n_omega/2 + 1
  * entries. n_omega must be even and >= 2.
+ * The assemblies of the next frequencies overlap the solve of frequency k
+ * (up to two ahead with full far-field storage, in operator sets of their
+ * own); GMRES is driven by the device (its rotations, convergence test and
+ * restarts run in kernels); the call returns once the whole sweep is done.
  * Errors: NO_MESH, STATE (material not set), INVALID_ARG, NOT_CONVERGED
  * (every frequency is still solved as far as max_iters allows and stored). */
 int bem_solve_sweep(bem_ctx* ctx, double T, int32_t n_omega, const double* load_hist,

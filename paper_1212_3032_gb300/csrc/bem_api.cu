@@ -216,22 +216,6 @@ int set_device(bem_ctx* ctx) {
   return BEM_OK;
 }
 
-// Reduce sum conj(a).b over FP64 into host value (synchronises).
-template <typename A, typename B>
-int dot_host(bem_ctx* ctx, const A* a, const B* b, long long n, std::complex<double>& out) {
-  BEM_CUDA_TRY(ctx->red.ensure(64 * 8));
-  c128* part = reinterpret_cast<c128*>(ctx->red.p);
-  int nblk = launch_dots<A, B>(a, n, 1, b, n, part, ctx->stream);
-  launch_dots_final(part, nblk, 1, reinterpret_cast<c128*>(ctx->red.p) + 64 * 2, ctx->stream);
-  CK("dot");
-  c128 h;
-  BEM_CUDA_TRY(cudaMemcpyAsync(&h, reinterpret_cast<c128*>(ctx->red.p) + 64 * 2, sizeof(c128),
-                               cudaMemcpyDeviceToHost, ctx->stream));
-  BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  out = {h.re, h.im};
-  return BEM_OK;
-}
-
 int ensure_static(bem_ctx* ctx, bool need_fp64);
 
 bool is_mixed(const bem_ctx* ctx) { return ctx->prec == BEM_PREC_C64_MIXED; }
@@ -452,7 +436,6 @@ extern "C" void bem_destroy(bem_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->host_red) cudaFreeHost(ctx->host_red);
-  if (ctx->host_cols) cudaFreeHost(ctx->host_cols);
   for (cudaEvent_t e : ctx->col_events) cudaEventDestroy(e);
   if (ctx->aux_stream) {
     cudaStreamSynchronize(ctx->aux_stream);
@@ -1510,14 +1493,7 @@ template <> const c64* basis_pinv<c64>(bem_ctx* ctx) { return ctx->prec_inv32.p;
 template <> const c128* basis_pinv<c128>(bem_ctx* ctx) { return ctx->prec_inv.p; }
 
 // Pinned host slots for ncomplex values and nev timing-free events.
-int ensure_host_cols(bem_ctx* ctx, long long ncomplex, int nev) {
-  if ((size_t)ncomplex > ctx->host_cols_n) {
-    if (ctx->host_cols) cudaFreeHost(ctx->host_cols);
-    ctx->host_cols = nullptr;
-    ctx->host_cols_n = 0;
-    BEM_CUDA_TRY(cudaMallocHost(&ctx->host_cols, ncomplex * 2 * sizeof(double)));
-    ctx->host_cols_n = ncomplex;
-  }
+int ensure_col_events(bem_ctx* ctx, int nev) {
   while ((int)ctx->col_events.size() < nev) {
     cudaEvent_t e;
     BEM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -1584,7 +1560,7 @@ int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq
   BEM_CUDA_TRY(ctx->orth_part.ensure((size_t)(2 * (m + 1) + 2) * arnoldi_orth_max_blocks()));
   BEM_CUDA_TRY(ctx->gm_ctl.ensure(1));
   BEM_CUDA_TRY(ctx->gm_work.ensure((size_t)(m + 1) * m + 3 * (size_t)m + 1));
-  TRY(ensure_host_cols(ctx, 1, m + 1));
+  TRY(ensure_col_events(ctx, m + 1));
   GmDev d{};
   d.ctl = ctx->gm_ctl.p;
   d.mirror = ctx->gm_mirror_dev;

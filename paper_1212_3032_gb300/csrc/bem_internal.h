@@ -378,9 +378,7 @@ struct bem_ctx {
   bem::DevBuf<bem::c128> orth_part;    // partial sums of the Arnoldi orthogonalisation step
   bem::DevBuf<double> pattern;         // tree order ne x 3
   double* host_red = nullptr;          // pinned
-  double* host_cols = nullptr;         // pinned Hessenberg column slots of GMRES
-  size_t host_cols_n = 0;              // complex values it holds
-  std::vector<cudaEvent_t> col_events; // one per Arnoldi step of a cycle
+  std::vector<cudaEvent_t> col_events; // one per Arnoldi step of a cycle (the host reads the solver state after them)
   bem::DevBuf<bem::GmCtl> gm_ctl;      // device-driven GMRES: state
   bem::GmCtl* gm_mirror = nullptr;     // its mapped host copy (host address)
   bem::GmCtl* gm_mirror_dev = nullptr; // (device address)

@@ -116,18 +116,8 @@ cudaError_t launch_sem_fit(const c128* const* X, int C, int K, const c128* Y, co
                            c128* a0, double* res, long long n, cudaStream_t st);
 // out[l] = sum_blk part[l * nblk + blk]
 void launch_dots_final(const c128* part, int nblk, int nvec, c128* out, cudaStream_t st);
-// w -= sum_l V_l h_l
-template <typename Vb, typename W>
-void launch_update(const Vb* V, long long ldv, int nvec, const c128* h, W* w, long long n, cudaStream_t st);
-// v = w * scale (complex scale given on device as 1/||w|| in h[0].re)
-template <typename W, typename Vb>
-void launch_scale(const W* w, Vb* v, long long n, const double* inv_norm, cudaStream_t st);
 // r = b - y ; both c128
 void launch_residual(const c128* b, const c128* y, c128* r, long long n, cudaStream_t st);
-// x += sum_l V_l y_l (x c128) after preconditioning: caller passes z = M^{-1} V y
-template <typename Vb>
-void launch_combine(const Vb* V, long long ldv, int nvec, const c128* y, c128* out, long long n,
-                    cudaStream_t st);
 void launch_axpy(c128 a, const c128* x, c128* y, long long n, cudaStream_t st, const int* run = nullptr);
 void launch_copy_cast(const c128* x, c64* y, long long n, double scale, cudaStream_t st);
 void launch_copy_cast(const c128* x, c128* y, long long n, double scale, cudaStream_t st);

@@ -784,50 +784,7 @@ void launch_dots_final(const c128* part, int nblk, int nvec, c128* out, cudaStre
   k_dots_final<<<nvec, 32, 0, st>>>(part, nblk, out);
 }
 
-template <typename Vb, typename W>
-__global__ void k_update(const Vb* __restrict__ V, long long ldv, int nvec, const c128* __restrict__ h,
-                         W* __restrict__ w, long long n) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double re = 0, im = 0;
-  for (int l = 0; l < nvec; ++l) {
-    Vb a = V[l * ldv + i];
-    c128 c = h[l];
-    re = fma((double)a.re, c.re, fma(-(double)a.im, c.im, re));
-    im = fma((double)a.re, c.im, fma((double)a.im, c.re, im));
-  }
-  W o = w[i];
-  o.re = decltype(o.re)((double)o.re - re);
-  o.im = decltype(o.im)((double)o.im - im);
-  w[i] = o;
-}
-template <typename Vb, typename W>
-void launch_update(const Vb* V, long long ldv, int nvec, const c128* h, W* w, long long n, cudaStream_t st) {
-  count_if(true);
-  k_update<Vb, W><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, ldv, nvec, h, w, n);
-}
-template void launch_update<c64, c64>(const c64*, long long, int, const c128*, c64*, long long, cudaStream_t);
-template void launch_update<c128, c128>(const c128*, long long, int, const c128*, c128*, long long,
-                                        cudaStream_t);
 
-template <typename W, typename Vb>
-__global__ void k_scale(const W* __restrict__ w, Vb* __restrict__ v, long long n, const double* __restrict__ nrm2) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double s = nrm2[0] > 0 ? 1.0 / sqrt(nrm2[0]) : 0.0;
-  W a = w[i];
-  Vb o;
-  o.re = decltype(o.re)(a.re * s);
-  o.im = decltype(o.im)(a.im * s);
-  v[i] = o;
-}
-template <typename W, typename Vb>
-void launch_scale(const W* w, Vb* v, long long n, const double* nrm2, cudaStream_t st) {
-  count_if(true);
-  k_scale<W, Vb><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w, v, n, nrm2);
-}
-template void launch_scale<c64, c64>(const c64*, c64*, long long, const double*, cudaStream_t);
-template void launch_scale<c128, c128>(const c128*, c128*, long long, const double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // One Arnoldi orthogonalisation step in one cooperative launch: classical
@@ -1375,27 +1332,6 @@ void launch_residual(const c128* b, const c128* y, c128* r, long long n, cudaStr
   k_residual<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b, y, r, n);
 }
 
-template <typename Vb>
-__global__ void k_combine(const Vb* __restrict__ V, long long ldv, int nvec, const c128* __restrict__ y,
-                          c128* __restrict__ out, long long n) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double re = 0, im = 0;
-  for (int l = 0; l < nvec; ++l) {
-    Vb a = V[l * ldv + i];
-    c128 c = y[l];
-    re = fma((double)a.re, c.re, fma(-(double)a.im, c.im, re));
-    im = fma((double)a.re, c.im, fma((double)a.im, c.re, im));
-  }
-  out[i] = c128{re, im};
-}
-template <typename Vb>
-void launch_combine(const Vb* V, long long ldv, int nvec, const c128* y, c128* out, long long n, cudaStream_t st) {
-  count_if(true);
-  k_combine<Vb><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, ldv, nvec, y, out, n);
-}
-template void launch_combine<c64>(const c64*, long long, int, const c128*, c128*, long long, cudaStream_t);
-template void launch_combine<c128>(const c128*, long long, int, const c128*, c128*, long long, cudaStream_t);
 
 __global__ void k_axpy(c128 a, const c128* __restrict__ x, c128* __restrict__ y, long long n,
                        const int* __restrict__ run) {
