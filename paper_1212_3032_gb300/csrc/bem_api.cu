@@ -1523,7 +1523,7 @@ int ensure_col_events(bem_ctx* ctx, int nev) {
 // steps once the cycle has ended, then enqueues the update and the next test.
 // The steps enqueued past the end of a cycle or of the solve return at once.
 // ---------------------------------------------------------------------------
-constexpr int GM_LAG = 2;
+constexpr int GM_LAG = 1;
 
 template <typename Vb, typename Pm, typename Acc>
 int gmres_impl(bem_ctx* ctx, const c128* b, c128* x, const bem_opts& o, bem_freq_stats* stats) {
